@@ -1,0 +1,161 @@
+/*
+ * dist.h -- C ABI of libdist: exact symplectic minimum distance on one GB300.
+ *
+ * Problem (Section 2, definitions of wt_s and wt_s(C)): for an F2-linear code
+ * C in F2^{2n} given by generator rows (x | z),
+ *     d = min { wt_s(c) : c in C, c != 0 },   wt_s(x, z) = popcount(x OR z).
+ * An F4-linear code of length n (Section 2.3) is the same problem: its F4
+ * Hamming weight equals wt_s of the 2-bit-plane image a + alpha b -> (a | b).
+ *
+ * Method (Section 2.1, Brouwer-Zimmermann with the packages of Sections 2.2
+ * and 2.3): the code is put into systematic generator matrices Gamma_1..m on
+ * disjoint qubit sets; for r = 1, 2, ... every combination of r units
+ * (packages of rows sharing a pivot qubit, or free rows) of every included
+ * matrix is enumerated on the GPU; the smallest weight seen is the upper
+ * bound U, and the lower bound L = sum_j max(0, r + 1 - f_j) (f_j = free rows
+ * of Gamma_j; Section 2.3's bound for two matrices, generalised) rises after
+ * every round; d = U once L >= U.
+ *
+ * Conventions:
+ *   - Every function returns DIST_OK (0) or a negative DIST_E* code; nothing
+ *     throws across the ABI.  dist_strerror() names a code.
+ *   - Inputs are plain host pointers and are copied; the caller keeps them.
+ *   - Outputs go into caller-allocated structs.
+ *   - A dist_code is used by one host thread at a time.
+ *   - The library needs a CUDA device (sm_103a build).  Without one, calls
+ *     that touch the device return DIST_ECUDA; there is no CPU fallback.
+ *   - cuda_stream arguments are cudaStream_t values passed as void*; NULL
+ *     selects a stream owned by the dist_code.
+ */
+#ifndef DIST_H
+#define DIST_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { DIST_F2 = 2, DIST_F4 = 4 };
+
+enum {
+    DIST_OK = 0,
+    DIST_EINVAL = -1,      /* bad argument or input outside the limits below */
+    DIST_ENOMEM = -2,      /* host or device allocation failed */
+    DIST_ECUDA = -3,       /* CUDA error, or no usable device */
+    DIST_ETIMEOUT = -4,    /* a bounded wait ran out */
+    DIST_EINCOMPLETE = -5, /* time limit reached: lower <= d <= upper in the result */
+    DIST_EZERO = -6,       /* the code (or C minus S) has no nonzero codeword */
+    DIST_EBUSY = -7,       /* batch ticket not finished yet */
+    DIST_EINTERNAL = -8,   /* a self-check of the library failed */
+    DIST_ERANGE = -9       /* distance needs combinations beyond the device walk (r > 32) */
+};
+
+#define DIST_MAX_N 128     /* qubits */
+#define DIST_MAX_K 256     /* F2 rows (an F4 input counts twice) */
+
+typedef struct dist_code dist_code;
+
+/*
+ * dist_init -- ingest and diagonalize a code (steps S1-S2; Section 2.2,
+ * Diagonalization_over_F2, and Section 2.3, Diagonalization_over_F4), and
+ * upload its generator matrices to the current CUDA device.
+ *   generator: field DIST_F2 -> K rows x 2n bytes in {0,1}, row-major, each
+ *              row x_0..x_{n-1} | z_0..z_{n-1}.
+ *              field DIST_F4 -> K rows x n bytes in {0,1,2,3}; v = a + 2b
+ *              means a + alpha b with alpha^2 = alpha + 1 (x-plane a,
+ *              z-plane b).  The code is the F4-span of the rows.
+ *   1 <= n <= 128; 1 <= K; K <= 256 (F2) or 2K <= 256 (F4).
+ *   Rank-deficient input is reduced (k_eff in the result); rank 0 gives
+ *   DIST_EZERO.  On success *out owns host and device memory until
+ *   dist_free.
+ */
+int dist_init(dist_code **out, const uint8_t *generator, int n, int K, int field);
+
+/*
+ * dist_set_exclude -- take the minimum over C minus S, S = span of the first
+ * n_stab input rows (F4: their F4-span).  With a normalizer matrix whose
+ * first rows generate the stabilizer this is d(Q) = wt_s(N \ S), the check of
+ * the modified Brouwer-Zimmermann algorithm (Section 2.1).  n_stab = 0
+ * restores the plain minimum.  DIST_EZERO if S = C.
+ */
+int dist_set_exclude(dist_code *c, int n_stab);
+
+typedef struct {
+    int32_t d;            /* certified distance (upper bound U if incomplete) */
+    int32_t lower;        /* lower bound on d (= d when certified) */
+    int32_t rounds;       /* last combination size r enumerated */
+    int32_t k_eff;        /* rank of the input (F4: over F4) */
+    int32_t n_gamma;      /* generator matrices enumerated */
+    int32_t status;       /* DIST_OK, DIST_EINCOMPLETE, ... (same as return) */
+    uint64_t codewords;   /* (subset, representative) combinations evaluated */
+    double seconds;       /* host wall time of the call */
+    uint8_t witness[256]; /* a codeword of weight d: F2 2n bytes (x | z), F4 n symbols */
+    uint8_t coeffs[256];  /* its coefficients over the input rows: F2 bits, F4 symbols */
+    double gpu_seconds;   /* summed CUDA-event time of the enumeration kernels */
+    uint64_t launches;    /* enumeration kernels launched */
+} dist_result;
+
+/*
+ * dist_solve -- steps S3-S6: enumerate rounds until L >= U and return the
+ * certified d with a witness.  Work is ordered on cuda_stream; the call
+ * returns after the result is on the host.
+ */
+int dist_solve(dist_code *c, dist_result *out, void *cuda_stream);
+
+/*
+ * dist_solve_bounded -- as dist_solve, but stops after about time_limit_s
+ * seconds (checked between launches and by the kernels themselves) and then
+ * returns DIST_EINCOMPLETE with lower <= d <= upper (out->d = upper).
+ */
+int dist_solve_bounded(dist_code *c, dist_result *out, void *cuda_stream, double time_limit_s);
+
+/* dist_free -- releases a dist_code (NULL is accepted). */
+int dist_free(dist_code *c);
+
+/*
+ * dist_plan_info -- host-only view of the plan step S2-S3 built for an input
+ * (no CUDA call).  For each generator matrix j < n_gamma_built: a[j] units
+ * with three representatives, b[j] with one, f[j] free rows; order[0..n_used)
+ * lists the matrices that are enumerated.  d_est is the random-code estimate
+ * used to choose them; u0 the lightest representative.
+ */
+typedef struct {
+    int32_t n_gamma_built, n_gamma_used, k_eff, s_rank, d_est, u0;
+    int32_t order[16];
+    int32_t a[16], b[16], f[16];
+} dist_plan_info;
+int dist_plan_info_get(const uint8_t *generator, int n, int K, int field, int n_stab,
+                       dist_plan_info *info);
+
+/*
+ * dist_plan_unit -- host-only: representative `rep` of unit `unit` of
+ * generator matrix `gamma` (units 0..a-1 first, then the b single-
+ * representative ones) as 2n bytes (x | z) in the input's qubit order, with
+ * its pivot qubit (-1 for a free row) and kind (0 rank-2 package or F4 row,
+ * 1 rank-1 package, 2 free row).  For tests of the diagonalization.
+ */
+int dist_plan_unit(const uint8_t *generator, int n, int K, int field, int gamma, int unit,
+                   int rep, uint8_t *vec_out, int *qubit, int *kind);
+
+/*
+ * dist_intpeak -- integer issue microbenchmark used as the roofline
+ * denominator.  Runs a loop of `iters` iterations of the enumeration's
+ * per-codeword instruction mix (2 LOP3, 1 POPC, 1 min) on every SM and
+ * reports codewords per second (mix_per_s) plus the rates of POPC alone
+ * and LOP3 alone (operations per second) and the SM clock seen (MHz).
+ */
+typedef struct {
+    double mix_per_s, popc_per_s, lop3_per_s, sm_mhz;
+    int32_t sms, blocks;
+} dist_intpeak_result;
+int dist_intpeak(dist_intpeak_result *out, int iters, void *cuda_stream);
+
+/* Library version string and device info (name, SM count) of the current device. */
+const char *dist_version(void);
+const char *dist_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

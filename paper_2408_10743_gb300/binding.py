@@ -1,0 +1,238 @@
+"""ctypes binding of libdist (include/dist.h): the same entry points, argument
+marshalling only.  All computation happens inside the library; there is no
+Python or CPU fallback -- if libdist.so cannot be built or loaded, or no CUDA
+device is present, the calls raise.
+
+Streams: pass a ``torch.cuda.Stream`` (or its integer handle) as ``stream``;
+None selects the stream owned by the code object.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DIST_F2, DIST_F4 = 2, 4
+DIST_OK = 0
+DIST_EINVAL, DIST_ENOMEM, DIST_ECUDA, DIST_ETIMEOUT = -1, -2, -3, -4
+DIST_EINCOMPLETE, DIST_EZERO, DIST_EBUSY, DIST_EINTERNAL, DIST_ERANGE = -5, -6, -7, -8, -9
+
+
+class DistResult(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("lower", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("k_eff", ctypes.c_int32), ("n_gamma", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("codewords", ctypes.c_uint64),
+                ("seconds", ctypes.c_double), ("witness", ctypes.c_uint8 * 256),
+                ("coeffs", ctypes.c_uint8 * 256), ("gpu_seconds", ctypes.c_double),
+                ("launches", ctypes.c_uint64)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_gamma_built", ctypes.c_int32), ("n_gamma_used", ctypes.c_int32),
+                ("k_eff", ctypes.c_int32), ("s_rank", ctypes.c_int32),
+                ("d_est", ctypes.c_int32), ("u0", ctypes.c_int32),
+                ("order", ctypes.c_int32 * 16), ("a", ctypes.c_int32 * 16),
+                ("b", ctypes.c_int32 * 16), ("f", ctypes.c_int32 * 16)]
+
+
+class IntpeakResult(ctypes.Structure):
+    _fields_ = [("mix_per_s", ctypes.c_double), ("popc_per_s", ctypes.c_double),
+                ("lop3_per_s", ctypes.c_double), ("sm_mhz", ctypes.c_double),
+                ("sms", ctypes.c_int32), ("blocks", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes); mirrors include/dist.h
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+_VP = ctypes.c_void_p
+SIGNATURES = {
+    "dist_init": (ctypes.c_int, [ctypes.POINTER(_VP), _U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "dist_set_exclude": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "dist_solve": (ctypes.c_int, [_VP, ctypes.POINTER(DistResult), _VP]),
+    "dist_solve_bounded": (ctypes.c_int, [_VP, ctypes.POINTER(DistResult), _VP, ctypes.c_double]),
+    "dist_free": (ctypes.c_int, [_VP]),
+    "dist_plan_info_get": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.POINTER(PlanInfo)]),
+    "dist_plan_unit": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "dist_intpeak": (ctypes.c_int, [ctypes.POINTER(IntpeakResult), ctypes.c_int, _VP]),
+    "dist_version": (ctypes.c_char_p, []),
+    "dist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libdist.so (compiling it first if the sources changed)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libdist.so is missing: the CUDA library did not build")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+class DistError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = lib().dist_strerror(code).decode()
+        super().__init__("%s: %s (%d)" % (what, msg, code))
+        self.code = code
+
+
+def _check(code: int, what: str, ok=(DIST_OK,)) -> int:
+    if code not in ok:
+        raise DistError(code, what)
+    return code
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _as_gen(generator, field):
+    g = np.ascontiguousarray(np.asarray(generator, dtype=np.uint8))
+    if g.ndim != 2:
+        raise ValueError("generator must be a 2-D array")
+    K = g.shape[0]
+    n = g.shape[1] // 2 if field == DIST_F2 else g.shape[1]
+    return g, n, K
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_U8P)
+
+
+# --- entry points with the C names --------------------------------------------------
+
+def dist_init(generator, n, K, field):
+    h = _VP()
+    g = np.ascontiguousarray(np.asarray(generator, dtype=np.uint8))
+    _check(lib().dist_init(ctypes.byref(h), _ptr(g), n, K, field), "dist_init")
+    return h
+
+
+def dist_set_exclude(handle, n_stab):
+    return _check(lib().dist_set_exclude(handle, n_stab), "dist_set_exclude")
+
+
+def dist_solve(handle, stream=None, ok=(DIST_OK,)):
+    r = DistResult()
+    _check(lib().dist_solve(handle, ctypes.byref(r), _stream_handle(stream)), "dist_solve", ok)
+    return r
+
+
+def dist_solve_bounded(handle, time_limit_s, stream=None):
+    r = DistResult()
+    _check(lib().dist_solve_bounded(handle, ctypes.byref(r), _stream_handle(stream),
+                                    float(time_limit_s)),
+           "dist_solve_bounded", ok=(DIST_OK, DIST_EINCOMPLETE))
+    return r
+
+
+def dist_free(handle):
+    return _check(lib().dist_free(handle), "dist_free")
+
+
+def dist_plan_info_get(generator, field=DIST_F2, n_stab=0) -> PlanInfo:
+    g, n, K = _as_gen(generator, field)
+    info = PlanInfo()
+    _check(lib().dist_plan_info_get(_ptr(g), n, K, field, n_stab, ctypes.byref(info)),
+           "dist_plan_info_get")
+    return info
+
+
+def dist_plan_unit(generator, gamma, unit, rep, field=DIST_F2):
+    g, n, K = _as_gen(generator, field)
+    out = np.zeros(2 * n, dtype=np.uint8)
+    q = ctypes.c_int(0)
+    kind = ctypes.c_int(0)
+    _check(lib().dist_plan_unit(_ptr(g), n, K, field, gamma, unit, rep, _ptr(out),
+                                ctypes.byref(q), ctypes.byref(kind)), "dist_plan_unit")
+    return out, q.value, kind.value
+
+
+def dist_intpeak(iters=4096, stream=None) -> IntpeakResult:
+    r = IntpeakResult()
+    _check(lib().dist_intpeak(ctypes.byref(r), iters, _stream_handle(stream)), "dist_intpeak")
+    return r
+
+
+def dist_version() -> str:
+    return lib().dist_version().decode()
+
+
+def dist_strerror(code: int) -> str:
+    return lib().dist_strerror(code).decode()
+
+
+# --- convenience wrapper ---------------------------------------------------------------
+
+def result_dict(r: DistResult, n: int, K: int, field: int) -> dict:
+    wlen = 2 * n if field == DIST_F2 else n
+    return {"d": r.d, "lower": r.lower, "rounds": r.rounds, "k_eff": r.k_eff,
+            "n_gamma": r.n_gamma, "status": r.status, "codewords": int(r.codewords),
+            "seconds": r.seconds, "gpu_seconds": r.gpu_seconds, "launches": int(r.launches),
+            "witness": np.frombuffer(bytes(r.witness), dtype=np.uint8)[:wlen].copy(),
+            "coeffs": np.frombuffer(bytes(r.coeffs), dtype=np.uint8)[:K].copy()}
+
+
+class Code:
+    """One code on the current CUDA device (owns a dist_code)."""
+
+    def __init__(self, generator, field=DIST_F2):
+        g, n, K = _as_gen(generator, field)
+        self.n, self.K, self.field = n, K, field
+        self._h = dist_init(g, n, K, field)
+
+    def set_exclude(self, n_stab: int):
+        dist_set_exclude(self._h, n_stab)
+
+    def solve(self, stream=None, time_limit_s: float = 0.0) -> dict:
+        if time_limit_s > 0:
+            r = dist_solve_bounded(self._h, time_limit_s, stream)
+        else:
+            r = dist_solve(self._h, stream)
+        return result_dict(r, self.n, self.K, self.field)
+
+    def close(self):
+        if self._h:
+            dist_free(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def distance(generator, field=DIST_F2, n_stab=0, stream=None) -> dict:
+    """Certified symplectic minimum distance of one code (convenience)."""
+    with Code(generator, field) as c:
+        if n_stab:
+            c.set_exclude(n_stab)
+        return c.solve(stream)

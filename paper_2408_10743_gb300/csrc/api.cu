@@ -1,0 +1,331 @@
+// api.cu -- the C ABI of libdist (declared in include/dist.h).
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/dist.h"
+#include "plan.h"
+#include "solve.h"
+
+namespace dist {
+cudaError_t enum_launch(const EnumParams& P, int max_blocks, cudaStream_t st);
+size_t enum_smem_bytes(const EnumParams& P);
+int enum_blocks_per_sm(size_t smem);
+struct IntpeakRaw {
+    double mix_s, popc_s, lop3_s;
+    double sm_mhz;
+    int sms, blocks, threads;
+};
+cudaError_t intpeak_run(int iters, cudaStream_t st, IntpeakRaw* r);
+}  // namespace dist
+
+using namespace dist;
+
+namespace {
+
+// Per-device constants: the binomial table the kernels unrank with.
+struct DeviceCtx {
+    int device = -1;
+    int sms = 0;
+    int blocks_per_sm = 0;
+    unsigned long long* d_binom = nullptr;
+};
+
+std::mutex g_dev_mu;
+DeviceCtx g_dev[64];
+
+int map_plan_rc(int rc) {
+    switch (rc) {
+        case P_OK: return DIST_OK;
+        case P_EZERO: return DIST_EZERO;
+        case P_ENOMEM: return DIST_ENOMEM;
+        case P_ERANGE: return DIST_ERANGE;
+        default: return DIST_EINVAL;
+    }
+}
+
+int device_ctx(DeviceCtx** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DIST_ECUDA;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceCtx& d = g_dev[dev];
+    if (d.device < 0) {
+        int major = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess)
+            return DIST_ECUDA;
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return DIST_ECUDA;
+        std::vector<unsigned long long> tab((DIST_MAXU + 1) * (DIST_MAXR + 1));
+        binom_table(tab.data());
+        if (cudaMalloc(&d.d_binom, tab.size() * sizeof(unsigned long long)) != cudaSuccess)
+            return DIST_ENOMEM;
+        if (cudaMemcpy(d.d_binom, tab.data(), tab.size() * sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return DIST_ECUDA;
+        // occupancy at the largest shared-memory footprint a code can need
+        EnumParams big;
+        memset(&big, 0, sizeof big);
+        big.a = 128;
+        big.b = 128;
+        big.W = DIST_MAXW;
+        d.blocks_per_sm = enum_blocks_per_sm(enum_smem_bytes(big));
+        if (d.blocks_per_sm < 1) return DIST_ECUDA;
+        d.device = dev;
+    }
+    *out = &d;
+    return DIST_OK;
+}
+
+}  // namespace
+
+struct dist_code {
+    Plan plan;
+    DeviceCtx* dev = nullptr;
+    uint32_t* d_tables = nullptr;
+    std::vector<size_t> rep_off, coef_off;   // word offsets per generator matrix
+    Scratch* d_scr = nullptr;
+    Scratch* h_scr = nullptr;                 // pinned mirror for read-back
+    cudaStream_t stream = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+namespace {
+
+void release(dist_code* c) {
+    if (!c) return;
+    if (c->d_tables) cudaFree(c->d_tables);
+    if (c->d_scr) cudaFree(c->d_scr);
+    if (c->h_scr) cudaFreeHost(c->h_scr);
+    if (c->e0) cudaEventDestroy(c->e0);
+    if (c->e1) cudaEventDestroy(c->e1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// Runs one enumeration step per call on the GPU (the executor of solve_loop).
+struct GpuExec {
+    dist_code* c;
+    cudaStream_t st;
+    double gpu_s = 0.0;
+    unsigned long long nl = 0;
+    int reset() {
+        if (cudaMemsetAsync(c->d_scr, 0, sizeof(Scratch), st) != cudaSuccess) return DIST_ECUDA;
+        // U = DIST_WINF (0x0000FFFF, little-endian)
+        if (cudaMemsetAsync(c->d_scr, 0xFF, 2, st) != cudaSuccess) return DIST_ECUDA;
+        return DIST_OK;
+    }
+    int target_warps() const { return c->dev->sms * c->dev->blocks_per_sm * 8; }
+    double gpu_seconds() const { return gpu_s; }
+    unsigned long long launches() const { return nl; }
+    int run(EnumParams& ep, double deadline_wall, StepResult* out) {
+        ep.reps = c->d_tables + c->rep_off[ep.gamma];
+        ep.coefs = c->d_tables + c->coef_off[ep.gamma];
+        ep.binom = c->dev->d_binom;
+        ep.scr = c->d_scr;
+        ep.budget_ns = 0;
+        if (deadline_wall > 0) {
+            double left = deadline_wall - wall_now();
+            ep.budget_ns = left > 1e-3 ? (unsigned long long)(left * 1e9) : 1000000ull;
+        }
+        if (cudaMemsetAsync(&c->d_scr->next_chunk, 0, sizeof(unsigned long long), st) != cudaSuccess)
+            return DIST_ECUDA;
+        cudaEventRecord(c->e0, st);
+        if (enum_launch(ep, c->dev->sms * c->dev->blocks_per_sm, st) != cudaSuccess) return DIST_ECUDA;
+        cudaEventRecord(c->e1, st);
+        nl++;
+        if (cudaMemcpyAsync(c->h_scr, c->d_scr, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return DIST_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return DIST_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->e0, c->e1);
+        gpu_s += ms * 1e-3;
+        out->U = c->h_scr->U;
+        out->status = c->h_scr->status;
+        out->codewords = c->h_scr->codewords;
+        return DIST_OK;
+    }
+    int read_slot(uint32_t w, WitnessSlot* s) {
+        if (w > DIST_MAXN) return DIST_EINTERNAL;
+        if (cudaMemcpyAsync(&c->h_scr->slot[w], &c->d_scr->slot[w], sizeof(WitnessSlot),
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return DIST_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return DIST_ECUDA;
+        *s = c->h_scr->slot[w];
+        return DIST_OK;
+    }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int dist_init(dist_code** out, const uint8_t* generator, int n, int K, int field) {
+    if (!out || !generator) return DIST_EINVAL;
+    *out = nullptr;
+    dist_code* c = new (std::nothrow) dist_code();
+    if (!c) return DIST_ENOMEM;
+    int rc = map_plan_rc(plan_build(generator, n, K, field, &c->plan));
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    rc = device_ctx(&c->dev);
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    size_t words = 0;
+    for (const Gamma& G : c->plan.gammas) {
+        c->rep_off.push_back(words);
+        words += G.dev_reps.size();
+        c->coef_off.push_back(words);
+        words += G.dev_coefs.size();
+        words = (words + 3) & ~(size_t)3;
+    }
+    std::vector<uint32_t> host(words, 0);
+    for (size_t g = 0; g < c->plan.gammas.size(); g++) {
+        const Gamma& G = c->plan.gammas[g];
+        memcpy(&host[c->rep_off[g]], G.dev_reps.data(), G.dev_reps.size() * 4);
+        memcpy(&host[c->coef_off[g]], G.dev_coefs.data(), G.dev_coefs.size() * 4);
+    }
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&c->e0) != cudaSuccess || cudaEventCreate(&c->e1) != cudaSuccess) {
+        release(c);
+        return DIST_ECUDA;
+    }
+    if (cudaMalloc(&c->d_tables, words * 4) != cudaSuccess ||
+        cudaMalloc(&c->d_scr, sizeof(Scratch)) != cudaSuccess ||
+        cudaMallocHost(&c->h_scr, sizeof(Scratch)) != cudaSuccess) {
+        release(c);
+        return DIST_ENOMEM;
+    }
+    if (cudaMemcpyAsync(c->d_tables, host.data(), words * 4, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        release(c);
+        return DIST_ECUDA;
+    }
+    *out = c;
+    return DIST_OK;
+}
+
+int dist_set_exclude(dist_code* c, int n_stab) {
+    if (!c) return DIST_EINVAL;
+    return map_plan_rc(plan_set_exclude(&c->plan, n_stab));
+}
+
+int dist_solve_bounded(dist_code* c, dist_result* out, void* cuda_stream, double time_limit_s) {
+    if (!c || !out) return DIST_EINVAL;
+    if (c->plan.n_stab > 0 && c->plan.s_rank == c->plan.k_eff) return DIST_EZERO;
+    DeviceGuard guard(c->dev->device);
+    GpuExec ex{c, cuda_stream ? (cudaStream_t)cuda_stream : c->stream};
+    return solve_loop(c->plan, ex, time_limit_s, out);
+}
+
+int dist_solve(dist_code* c, dist_result* out, void* cuda_stream) {
+    return dist_solve_bounded(c, out, cuda_stream, 0.0);
+}
+
+int dist_free(dist_code* c) {
+    if (!c) return DIST_OK;
+    DeviceGuard guard(c->dev ? c->dev->device : 0);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    release(c);
+    return DIST_OK;
+}
+
+int dist_plan_info_get(const uint8_t* generator, int n, int K, int field, int n_stab,
+                       dist_plan_info* info) {
+    if (!info) return DIST_EINVAL;
+    memset(info, 0, sizeof *info);
+    Plan p;
+    int rc = map_plan_rc(plan_build(generator, n, K, field, &p));
+    if (rc) return rc;
+    if (n_stab) {
+        rc = map_plan_rc(plan_set_exclude(&p, n_stab));
+        if (rc) return rc;
+    }
+    info->n_gamma_built = (int)p.gammas.size();
+    info->n_gamma_used = (int)p.J.size();
+    info->k_eff = p.k_eff;
+    info->s_rank = p.s_rank;
+    info->d_est = p.d_est;
+    info->u0 = p.u0;
+    for (size_t t = 0; t < p.J.size() && t < 16; t++) info->order[t] = p.J[t];
+    for (size_t g = 0; g < p.gammas.size() && g < 16; g++) {
+        info->a[g] = (int)p.gammas[g].A.size();
+        info->b[g] = (int)p.gammas[g].B.size();
+        info->f[g] = p.gammas[g].f;
+    }
+    return DIST_OK;
+}
+
+int dist_plan_unit(const uint8_t* generator, int n, int K, int field, int gamma, int unit, int rep,
+                   uint8_t* vec_out, int* qubit, int* kind) {
+    if (!vec_out) return DIST_EINVAL;
+    Plan p;
+    int rc = map_plan_rc(plan_build(generator, n, K, field, &p));
+    if (rc) return rc;
+    if (gamma < 0 || gamma >= (int)p.gammas.size()) return DIST_EINVAL;
+    const Gamma& G = p.gammas[gamma];
+    if (unit < 0 || unit >= G.units()) return DIST_EINVAL;
+    const Unit& x = unit < (int)G.A.size() ? G.A[unit] : G.B[unit - G.A.size()];
+    if (rep < 0 || rep >= x.nrep) return DIST_EINVAL;
+    for (int i = 0; i < n; i++) {
+        vec_out[i] = (uint8_t)((x.rep[rep].x[i >> 5] >> (i & 31)) & 1u);
+        vec_out[n + i] = (uint8_t)((x.rep[rep].z[i >> 5] >> (i & 31)) & 1u);
+    }
+    if (qubit) *qubit = x.qubit;
+    if (kind) *kind = x.kind;
+    return DIST_OK;
+}
+
+int dist_intpeak(dist_intpeak_result* out, int iters, void* cuda_stream) {
+    if (!out || iters < 1) return DIST_EINVAL;
+    memset(out, 0, sizeof *out);
+    IntpeakRaw r;
+    if (intpeak_run(iters, (cudaStream_t)cuda_stream, &r) != cudaSuccess) return DIST_ECUDA;
+    const double threads = (double)r.blocks * r.threads;
+    out->mix_per_s = threads * (double)iters * 27.0 / r.mix_s;
+    out->popc_per_s = threads * (double)iters * 8.0 / r.popc_s;
+    out->lop3_per_s = threads * (double)iters * 8.0 / r.lop3_s;
+    out->sm_mhz = r.sm_mhz;
+    out->sms = r.sms;
+    out->blocks = r.blocks;
+    return DIST_OK;
+}
+
+const char* dist_version(void) { return "libdist 0.1 (sm_103a)"; }
+
+const char* dist_strerror(int code) {
+    switch (code) {
+        case DIST_OK: return "ok";
+        case DIST_EINVAL: return "invalid argument";
+        case DIST_ENOMEM: return "out of memory";
+        case DIST_ECUDA: return "CUDA error or no usable device";
+        case DIST_ETIMEOUT: return "bounded wait timed out";
+        case DIST_EINCOMPLETE: return "time limit reached before d was certified";
+        case DIST_EZERO: return "no nonzero codeword (outside the excluded span)";
+        case DIST_EBUSY: return "not finished yet";
+        case DIST_EINTERNAL: return "internal self-check failed";
+        case DIST_ERANGE: return "distance needs combinations beyond the device walk";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

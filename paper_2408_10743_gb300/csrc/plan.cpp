@@ -1,0 +1,616 @@
+// plan.cpp -- host planner: ingest, package diagonalization, bound schedule,
+// work description per launch, witness decoding.  Plain C++, no CUDA.
+#include "plan.h"
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+namespace dist {
+
+// ---------------------------------------------------------------------------
+// Bit-plane helpers.
+// ---------------------------------------------------------------------------
+static inline int bit(const uint32_t* v, int i) { return (int)((v[i >> 5] >> (i & 31)) & 1u); }
+static inline void setb(uint32_t* v, int i) { v[i >> 5] |= 1u << (i & 31); }
+
+static inline void vxor(Vec& a, const Vec& b) {
+    for (int w = 0; w < DIST_MAXW; w++) {
+        a.x[w] ^= b.x[w];
+        a.z[w] ^= b.z[w];
+    }
+}
+static inline void cxor(Coef& a, const Coef& b) {
+    for (int q = 0; q < 2; q++)
+        for (int w = 0; w < DIST_MAXCW; w++) a.p[q][w] ^= b.p[q][w];
+}
+static inline bool vzero(const Vec& a) {
+    for (int w = 0; w < DIST_MAXW; w++)
+        if (a.x[w] | a.z[w]) return false;
+    return true;
+}
+
+int vec_weight(const Vec& v, int W) {
+    int s = 0;
+    for (int w = 0; w < W; w++) s += __builtin_popcount(v.x[w] | v.z[w]);
+    return s;
+}
+
+// Value of coordinate q as 0..3 = x_q + 2 z_q: the projection of a row onto
+// qubit q (F2^2), or its F4 symbol.
+static inline int proj(const Vec& v, int q) { return bit(v.x, q) | (bit(v.z, q) << 1); }
+
+// F4 scalar c (1 = 1, 2 = alpha, 3 = alpha^2) times a plane pair (x, z) that
+// encodes x + alpha z:  alpha (x + alpha z) = z + alpha (x + z).
+static inline void f4_scale_planes(uint32_t* x, uint32_t* z, int nw, int c) {
+    for (int w = 0; w < nw; w++) {
+        uint32_t a = x[w], b = z[w];
+        if (c == 2) {
+            x[w] = b;
+            z[w] = a ^ b;
+        } else if (c == 3) {
+            x[w] = a ^ b;
+            z[w] = a;
+        }
+    }
+}
+static inline Vec vscale(const Vec& v, int c) {
+    Vec r = v;
+    f4_scale_planes(r.x, r.z, DIST_MAXW, c);
+    return r;
+}
+static inline Coef cscale(const Coef& v, int c) {
+    Coef r = v;
+    f4_scale_planes(r.p[0], r.p[1], DIST_MAXCW, c);
+    return r;
+}
+static inline int f4_inv(int c) { return c == 1 ? 1 : (c == 2 ? 3 : 2); }
+
+// ---------------------------------------------------------------------------
+// Binomials.
+// ---------------------------------------------------------------------------
+void binom_table(unsigned long long* tab) {
+    const unsigned long long SAT = ~0ull;
+    for (int n = 0; n <= DIST_MAXU; n++)
+        for (int k = 0; k <= DIST_MAXR; k++) {
+            unsigned long long v;
+            if (k == 0) v = 1;
+            else if (n == 0) v = 0;
+            else {
+                unsigned long long a = tab[(n - 1) * (DIST_MAXR + 1) + k - 1];
+                unsigned long long b = tab[(n - 1) * (DIST_MAXR + 1) + k];
+                v = (a == SAT || b == SAT || a + b < a) ? SAT : a + b;
+            }
+            tab[n * (DIST_MAXR + 1) + k] = v;
+        }
+}
+
+static double dbinom(int n, int k) {
+    if (k < 0 || k > n) return 0.0;
+    return exp(lgamma(n + 1.0) - lgamma(k + 1.0) - lgamma(n - k + 1.0));
+}
+
+static unsigned long long ubinom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    unsigned __int128 v = 1;
+    for (int i = 1; i <= k; i++) {
+        v = v * (unsigned)(n - k + i) / (unsigned)i;
+        if (v > ((unsigned __int128)1 << 63)) return ~0ull;
+    }
+    return (unsigned long long)v;
+}
+
+static unsigned long long upow3(int e) {
+    unsigned long long v = 1;
+    for (int i = 0; i < e; i++) {
+        if (v > (1ull << 62) / 3) return ~0ull;
+        v *= 3;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// S1: ingest and rank reduction.
+// ---------------------------------------------------------------------------
+static int load_input(const uint8_t* gen, int n, int K, int field, Plan* p) {
+    p->input.assign(K, Vec());
+    for (int r = 0; r < K; r++) {
+        Vec& v = p->input[r];
+        memset(&v, 0, sizeof v);
+        for (int i = 0; i < n; i++) {
+            int a, b;
+            if (field == 2) {
+                a = gen[(size_t)r * 2 * n + i];
+                b = gen[(size_t)r * 2 * n + n + i];
+                if (a > 1 || b > 1) return P_EINVAL;
+            } else {
+                int s = gen[(size_t)r * n + i];
+                if (s > 3) return P_EINVAL;
+                a = s & 1;
+                b = s >> 1;
+            }
+            if (a) setb(v.x, i);
+            if (b) setb(v.z, i);
+        }
+    }
+    return P_OK;
+}
+
+// Keeps, in input order, the rows independent of the ones kept before them
+// (over F2 for field 2, over F4 for field 4).
+static void reduce_rank(Plan* p) {
+    p->kept.clear();
+    p->basis.clear();
+    std::vector<Vec> ech;
+    std::vector<int> piv;  // F2: bit index in [0, 2n) ; F4: coordinate
+    for (int r = 0; r < p->K_in; r++) {
+        Vec t = p->input[r];
+        for (size_t e = 0; e < ech.size(); e++) {
+            if (p->field == 2) {
+                int q = piv[e];
+                int b = q < p->n ? bit(t.x, q) : bit(t.z, q - p->n);
+                if (b) vxor(t, ech[e]);
+            } else {
+                int c = proj(t, piv[e]);
+                if (c) vxor(t, vscale(ech[e], c));  // ech rows have symbol 1 at their pivot
+            }
+        }
+        if (vzero(t)) continue;
+        int q = -1;
+        if (p->field == 2) {
+            for (int i = 0; i < 2 * p->n && q < 0; i++)
+                if (i < p->n ? bit(t.x, i) : bit(t.z, i - p->n)) q = i;
+        } else {
+            for (int i = 0; i < p->n && q < 0; i++)
+                if (proj(t, i)) q = i;
+            t = vscale(t, f4_inv(proj(t, q)));
+        }
+        ech.push_back(t);
+        piv.push_back(q);
+        p->kept.push_back(r);
+        p->basis.push_back(p->input[r]);
+    }
+    p->k_eff = (int)p->basis.size();
+}
+
+// ---------------------------------------------------------------------------
+// S2: package diagonalization.
+// ---------------------------------------------------------------------------
+
+// F2 (Sections 2.2-2.3 in F2 language).  Works on the qubits not used by an
+// earlier matrix.  At each step it takes the unused qubit whose projections,
+// over the rows not pivoted yet, span the most (rank 2 first, then rank 1,
+// lowest index on ties):
+//  * rank 2: two rows g, h with independent projections become a package
+//    {g, h, g+h}; every other row gets the combination of g and h that clears
+//    the qubit, so any sum that contains a package member is nonzero there.
+//  * rank 1 (projections in {0, v}): a row g with projection v becomes a
+//    one-element package.  Other rows may carry any projection; fix a nonzero
+//    w != v and add g to every row whose projection is v or v+w.  Afterwards
+//    all other rows lie in {0, w}, whose span never contains v or v+w, so any
+//    sum containing g is nonzero at the qubit.
+// Rows left without a pivot are free.  A later pivot only adds rows whose
+// projection on earlier pivot qubits is already 0, so earlier packages keep
+// their property.
+static void diag_f2(const Plan& p, std::vector<char>& used, Gamma& G) {
+    const int k = p.k_eff, n = p.n;
+    std::vector<Vec> R = p.basis;
+    std::vector<Coef> C(k);
+    for (int i = 0; i < k; i++) {
+        memset(&C[i], 0, sizeof(Coef));
+        setb(C[i].p[0], i);
+    }
+    std::vector<char> piv(k, 0);
+    struct U { int kind, q, g, h; };
+    std::vector<U> units;
+    for (;;) {
+        int best_q = -1, best_rank = 0;
+        for (int q = 0; q < n; q++) {
+            if (used[q]) continue;
+            int seen = 0;
+            for (int i = 0; i < k; i++)
+                if (!piv[i]) seen |= 1 << proj(R[i], q);
+            int nz = __builtin_popcount(seen & 0xE);
+            int rank = nz >= 2 ? 2 : nz;
+            if (rank > best_rank) {
+                best_rank = rank;
+                best_q = q;
+                if (rank == 2) break;
+            }
+        }
+        if (best_rank == 0) break;
+        const int q = best_q;
+        if (best_rank == 2) {
+            int g = -1, h = -1;
+            for (int i = 0; i < k && g < 0; i++)
+                if (!piv[i] && proj(R[i], q)) g = i;
+            int vg = proj(R[g], q);
+            for (int i = 0; i < k && h < 0; i++)
+                if (!piv[i] && proj(R[i], q) && proj(R[i], q) != vg) h = i;
+            int vh = proj(R[h], q);
+            for (int i = 0; i < k; i++) {
+                if (i == g || i == h) continue;
+                int v = proj(R[i], q);
+                if (v == vg) {
+                    vxor(R[i], R[g]); cxor(C[i], C[g]);
+                } else if (v == vh) {
+                    vxor(R[i], R[h]); cxor(C[i], C[h]);
+                } else if (v == (vg ^ vh)) {
+                    vxor(R[i], R[g]); cxor(C[i], C[g]);
+                    vxor(R[i], R[h]); cxor(C[i], C[h]);
+                }
+            }
+            piv[g] = piv[h] = 1;
+            units.push_back({UNIT_PACKAGE2, q, g, h});
+        } else {
+            int g = -1;
+            for (int i = 0; i < k && g < 0; i++)
+                if (!piv[i] && proj(R[i], q)) g = i;
+            int v = proj(R[g], q);
+            int w = (v == 1) ? 2 : 1;  // smallest nonzero value other than v
+            for (int i = 0; i < k; i++) {
+                if (i == g) continue;
+                int pv = proj(R[i], q);
+                if (pv == v || pv == (v ^ w)) {
+                    vxor(R[i], R[g]); cxor(C[i], C[g]);
+                }
+            }
+            piv[g] = 1;
+            units.push_back({UNIT_PACKAGE1, q, g, -1});
+        }
+        used[q] = 1;
+        G.pivots.push_back(q);
+    }
+    for (int i = 0; i < k; i++)
+        if (!piv[i]) units.push_back({UNIT_FREE, -1, i, -1});
+    G.A.clear();
+    G.B.clear();
+    G.f = 0;
+    G.npack = 0;
+    for (const U& u : units) {
+        Unit x;
+        memset(&x, 0, sizeof x);
+        x.kind = u.kind;
+        x.qubit = u.q;
+        x.rep[0] = R[u.g];
+        x.coef[0] = C[u.g];
+        if (u.kind == UNIT_PACKAGE2) {
+            x.nrep = 3;
+            x.rep[1] = R[u.h];
+            x.coef[1] = C[u.h];
+            x.rep[2] = R[u.g];
+            vxor(x.rep[2], R[u.h]);
+            x.coef[2] = C[u.g];
+            cxor(x.coef[2], C[u.h]);
+            G.A.push_back(x);
+        } else {
+            x.nrep = 1;
+            G.B.push_back(x);
+        }
+        if (u.kind == UNIT_FREE) G.f++;
+        else G.npack++;
+    }
+}
+
+// F4-linear codes (Section 2.3): reduced echelon form over F4 on the unused
+// coordinates, lowest coordinate first.  Every row becomes a unit with the
+// representatives g, alpha g, alpha^2 g; pivot rows are packages (weight >= 1
+// on their pivot coordinate in any combination that uses them), the rest free.
+static void diag_f4(const Plan& p, std::vector<char>& used, Gamma& G) {
+    const int k = p.k_eff, n = p.n;
+    std::vector<Vec> R = p.basis;
+    std::vector<Coef> C(k);
+    for (int i = 0; i < k; i++) {
+        memset(&C[i], 0, sizeof(Coef));
+        setb(C[i].p[0], i);  // scalar 1 on basis row i
+    }
+    std::vector<char> piv(k, 0);
+    std::vector<std::pair<int, int>> order;  // (row, qubit)
+    int npiv = 0;
+    for (int q = 0; q < n && npiv < k; q++) {
+        if (used[q]) continue;
+        int g = -1;
+        for (int i = 0; i < k && g < 0; i++)
+            if (!piv[i] && proj(R[i], q)) g = i;
+        if (g < 0) continue;
+        int inv = f4_inv(proj(R[g], q));
+        R[g] = vscale(R[g], inv);
+        C[g] = cscale(C[g], inv);
+        for (int i = 0; i < k; i++) {
+            if (i == g) continue;
+            int c = proj(R[i], q);
+            if (c) {
+                vxor(R[i], vscale(R[g], c));
+                cxor(C[i], cscale(C[g], c));
+            }
+        }
+        piv[g] = 1;
+        npiv++;
+        used[q] = 1;
+        G.pivots.push_back(q);
+        order.push_back({g, q});
+    }
+    for (int i = 0; i < k; i++)
+        if (!piv[i]) order.push_back({i, -1});
+    G.A.clear();
+    G.B.clear();
+    G.f = 0;
+    G.npack = 0;
+    for (auto& o : order) {
+        Unit x;
+        memset(&x, 0, sizeof x);
+        x.kind = o.second >= 0 ? UNIT_PACKAGE2 : UNIT_FREE;
+        x.qubit = o.second;
+        x.nrep = 3;
+        for (int e = 0; e < 3; e++) {
+            x.rep[e] = vscale(R[o.first], e + 1);
+            x.coef[e] = cscale(C[o.first], e + 1);
+        }
+        G.A.push_back(x);
+        if (o.second >= 0) G.npack++;
+        else G.f++;
+    }
+}
+
+// Device tables of one matrix: qubits reordered so that the qubits that are
+// NOT pivots of this matrix come first (they fill word 0 of each plane, the
+// word the enumeration filters on), pivots after them.
+static void build_device_tables(const Plan& p, Gamma& G) {
+    std::vector<char> isp(p.n, 0);
+    for (int q : G.pivots) isp[q] = 1;
+    G.perm.clear();
+    for (int q = 0; q < p.n; q++)
+        if (!isp[q]) G.perm.push_back(q);
+    for (int q : G.pivots) G.perm.push_back(q);
+    const int u = G.units(), W = p.W, CW = p.CW;
+    G.dev_reps.assign((size_t)u * 3 * 2 * W, 0);
+    G.dev_coefs.assign((size_t)u * 3 * 2 * CW, 0);
+    for (int t = 0; t < u; t++) {
+        const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
+        for (int e = 0; e < x.nrep; e++) {
+            uint32_t* dx = &G.dev_reps[(((size_t)t * 3 + e) * 2 + 0) * W];
+            uint32_t* dz = &G.dev_reps[(((size_t)t * 3 + e) * 2 + 1) * W];
+            for (int pos = 0; pos < p.n; pos++) {
+                int q = G.perm[pos];
+                if (bit(x.rep[e].x, q)) setb(dx, pos);
+                if (bit(x.rep[e].z, q)) setb(dz, pos);
+            }
+            for (int c = 0; c < 2; c++)
+                for (int w = 0; w < CW; w++)
+                    G.dev_coefs[(((size_t)t * 3 + e) * 2 + c) * CW + w] = x.coef[e].p[c][w];
+        }
+    }
+}
+
+static bool coef_outside(const Plan& p, const Coef& c) {
+    if (p.n_stab == 0) return true;
+    for (int w = 0; w < p.CW; w++)
+        if ((c.p[0][w] | c.p[1][w]) & p.outside[w]) return true;
+    return false;
+}
+
+// Number of codewords in round r of matrix g (F4: projective, first scalar 1).
+double plan_round_count(const Plan& p, int g, int r) {
+    const Gamma& G = p.gammas[g];
+    const int a = (int)G.A.size(), b = (int)G.B.size();
+    if (p.field == 4) return r >= 1 ? dbinom(a, r) * pow(3.0, r - 1) : 0.0;
+    double s = 0;
+    for (int i = std::max(0, r - b); i <= std::min(r, a); i++)
+        s += dbinom(a, i) * pow(3.0, i) * dbinom(b, r - i);
+    return s;
+}
+
+static int bound_for(const Plan& p, const std::vector<int>& J, int r, int jpos) {
+    long L = 0;
+    for (size_t t = 0; t < J.size(); t++) {
+        const Gamma& G = p.gammas[J[t]];
+        int rr = (int)t <= jpos ? r : r - 1;
+        if (rr >= G.units()) return DIST_WINF;
+        L += std::max(0, rr + 1 - G.f);
+    }
+    return (int)std::min<long>(L, DIST_WINF - 1);
+}
+
+int plan_lower_bound(const Plan& p, int r, int jpos) { return bound_for(p, p.J, r, jpos); }
+
+int plan_initial_bound(const Plan& p) { return std::max(1, bound_for(p, p.J, 0, (int)p.J.size())); }
+
+// Choice of J: among the matrices sorted by free rows, the prefix whose
+// estimated work to lift the bound to d_est is smallest.  Any nonempty J is
+// correct; this only decides speed.
+static void choose_J(Plan* p) {
+    std::vector<int> cand;
+    for (size_t g = 0; g < p->gammas.size(); g++) cand.push_back((int)g);
+    std::stable_sort(cand.begin(), cand.end(),
+                     [&](int a, int b) { return p->gammas[a].f < p->gammas[b].f; });
+    double best = INFINITY;
+    std::vector<int> bestJ;
+    for (size_t m = 1; m <= cand.size(); m++) {
+        std::vector<int> J(cand.begin(), cand.begin() + m);
+        double work = 0;
+        for (int r = 1; r <= DIST_MAXU; r++) {
+            for (size_t t = 0; t < J.size(); t++) {
+                work += plan_round_count(*p, J[t], r);
+                if (bound_for(*p, J, r, (int)t) >= p->d_est) goto done;
+            }
+        }
+    done:
+        if (work < best) {
+            best = work;
+            bestJ = J;
+        }
+    }
+    p->J = bestJ;
+}
+
+int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
+    if (!gen || n < 1 || n > DIST_MAXN || K < 1) return P_EINVAL;
+    if (field != 2 && field != 4) return P_EINVAL;
+    if ((field == 2 ? K : 2 * K) > DIST_MAXK) return P_EINVAL;
+    if (field == 2 && K > 2 * n) { /* dependent by counting; allowed, reduced below */ }
+    *p = Plan();
+    p->n = n;
+    p->field = field;
+    p->K_in = K;
+    p->W = (n + 31) / 32;
+    int rc = load_input(gen, n, K, field, p);
+    if (rc) return rc;
+    reduce_rank(p);
+    if (p->k_eff == 0) return P_EZERO;
+    p->CW = (p->k_eff + 31) / 32;
+
+    std::vector<char> used(n, 0);
+    for (int j = 0; j < DIST_MAXGAMMA; j++) {
+        Gamma G;
+        std::vector<char> u2 = used;
+        if (field == 2) diag_f2(*p, u2, G);
+        else diag_f4(*p, u2, G);
+        if (G.npack == 0) break;
+        if (G.A.size() > 255 || G.units() > DIST_MAXU) return P_ERANGE;
+        used = u2;
+        build_device_tables(*p, G);
+        p->gammas.push_back(std::move(G));
+    }
+    if (p->gammas.empty()) return P_EZERO;
+
+    p->u0 = DIST_WINF;
+    for (const Gamma& G : p->gammas) {
+        for (const Unit& x : G.A)
+            for (int e = 0; e < x.nrep; e++) p->u0 = std::min(p->u0, vec_weight(x.rep[e], p->W));
+        for (const Unit& x : G.B) p->u0 = std::min(p->u0, vec_weight(x.rep[0], p->W));
+    }
+    // Expected number of nonzero codewords of weight <= w in a random code of
+    // the same size: 2^(K2 - 2n) * sum_v C(n, v) 3^v.  d_est = first w where it
+    // reaches 1, capped by the lightest representative.
+    const int K2 = field == 2 ? p->k_eff : 2 * p->k_eff;
+    double acc = 0;
+    p->d_est = n;
+    for (int w = 1; w <= n; w++) {
+        acc += dbinom(n, w) * pow(3.0, w);
+        if (log2(acc) + K2 - 2.0 * n >= 0) {
+            p->d_est = w;
+            break;
+        }
+    }
+    p->d_est = std::max(1, std::min(p->d_est, p->u0));
+    choose_J(p);
+    return P_OK;
+}
+
+int plan_set_exclude(Plan* p, int n_stab) {
+    if (n_stab < 0 || n_stab > p->K_in) return P_EINVAL;
+    p->n_stab = n_stab;
+    p->s_rank = 0;
+    for (int r : p->kept)
+        if (r < n_stab) p->s_rank++;
+    memset(p->outside, 0, sizeof p->outside);
+    if (n_stab > 0)
+        for (int i = p->s_rank; i < p->k_eff; i++) setb(p->outside, i);
+    if (n_stab > 0 && p->s_rank == p->k_eff) return P_EZERO;
+    return P_OK;
+}
+
+int plan_step(const Plan& p, int jpos, int r, int L_prev, int target_warps, EnumParams* ep,
+              unsigned long long* codewords) {
+    if (r < 1 || r > DIST_MAXR) return P_ERANGE;
+    const int g = p.J[jpos];
+    const Gamma& G = p.gammas[g];
+    memset(ep, 0, sizeof *ep);
+    ep->a = (int)G.A.size();
+    ep->b = (int)G.B.size();
+    ep->W = p.W;
+    ep->CW = p.CW;
+    ep->r = r;
+    ep->gamma = g;
+    ep->proj = p.field == 4 ? 1 : 0;
+    ep->exclude = p.n_stab > 0 ? 1 : 0;
+    for (int w = 0; w < DIST_MAXCW; w++) ep->outside[w] = p.outside[w];
+    ep->L_prev = L_prev;
+    const int a = ep->a, b = ep->b;
+    unsigned long long total = 0, chunks = 0;
+    double dtotal = 0;
+    int imin = std::max(0, r - b), imax = std::min(r, a);
+    if (ep->proj) imin = std::max(imin, 1);
+    for (int i = imin; i <= imax; i++) {
+        unsigned long long NA = ubinom(a, i), NB = ubinom(b, r - i);
+        unsigned long long codes = ep->proj ? upow3(i - 1) : upow3(i);
+        if (NA == 0 || NB == 0) continue;
+        if (NA == ~0ull || NB == ~0ull || codes == ~0ull) return P_ERANGE;
+        unsigned __int128 subsets = (unsigned __int128)NA * NB;
+        if (subsets >> 62) return P_ERANGE;
+        dtotal += (double)subsets * (double)codes;
+    }
+    // Subsets per lane: about six warp-chunks per resident warp, a lane chunk
+    // of at most ~2^21 codewords so that a stop request is seen quickly.
+    double per_lane = dtotal / (32.0 * std::max(1, target_warps) * 6.0);
+    per_lane = std::min(per_lane, (double)(1u << 21));
+    for (int i = imin; i <= imax; i++) {
+        unsigned long long NA = ubinom(a, i), NB = ubinom(b, r - i);
+        if (NA == 0 || NB == 0) continue;
+        unsigned long long codes = ep->proj ? upow3(i - 1) : upow3(i);
+        unsigned long long subsets = NA * NB;
+        double spl_d = per_lane / (double)codes;
+        unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
+        if (spl > (1ull << 30)) spl = 1ull << 30;
+        SegDesc& s = ep->seg[ep->nseg++];
+        s.NA = NA;
+        s.NB = NB;
+        s.codes = codes;
+        s.i = (uint32_t)i;
+        s.spl = (uint32_t)spl;
+        s.chunk_base = chunks;
+        chunks += (subsets + 32 * spl - 1) / (32 * spl);
+        total += subsets * codes;
+    }
+    ep->nchunks = chunks;
+    if (codewords) *codewords = total;
+    return P_OK;
+}
+
+int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* coeffs) {
+    if (s.gamma >= p.gammas.size() || s.count == 0 || s.count > DIST_MAXR) return P_EINVAL;
+    const Gamma& G = p.gammas[s.gamma];
+    Vec c;
+    Coef k;
+    memset(&c, 0, sizeof c);
+    memset(&k, 0, sizeof k);
+    for (uint32_t t = 0; t < s.count; t++) {
+        int u = s.unit[t], e = s.digit[t];
+        const Unit* x = u < (int)G.A.size() ? &G.A[u]
+                        : (u - (int)G.A.size() < (int)G.B.size() ? &G.B[u - G.A.size()] : nullptr);
+        if (!x || e >= x->nrep) return P_EINVAL;
+        vxor(c, x->rep[e]);
+        cxor(k, x->coef[e]);
+    }
+    if ((int)s.weight != vec_weight(c, p.W)) return P_EINVAL;
+    if (!coef_outside(p, k)) return P_EINVAL;
+    // The coefficients must rebuild the codeword from the input rows.
+    Vec chk;
+    memset(&chk, 0, sizeof chk);
+    for (int i = 0; i < p.k_eff; i++) {
+        int sym = bit(k.p[0], i) | (bit(k.p[1], i) << 1);
+        if (sym) vxor(chk, p.field == 2 ? p.input[p.kept[i]] : vscale(p.input[p.kept[i]], sym));
+    }
+    for (int w = 0; w < DIST_MAXW; w++)
+        if (chk.x[w] != c.x[w] || chk.z[w] != c.z[w]) return P_EINVAL;
+    if (witness) {
+        for (int i = 0; i < p.n; i++) {
+            if (p.field == 2) {
+                witness[i] = (uint8_t)bit(c.x, i);
+                witness[p.n + i] = (uint8_t)bit(c.z, i);
+            } else {
+                witness[i] = (uint8_t)proj(c, i);
+            }
+        }
+    }
+    if (coeffs) {
+        memset(coeffs, 0, (size_t)p.K_in);
+        for (int i = 0; i < p.k_eff; i++)
+            coeffs[p.kept[i]] = (uint8_t)(bit(k.p[0], i) | (bit(k.p[1], i) << 1));
+    }
+    return P_OK;
+}
+
+}  // namespace dist

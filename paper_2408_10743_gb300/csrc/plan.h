@@ -1,0 +1,100 @@
+// plan.h -- host side of the distance computation (no CUDA calls):
+//   S1 ingest + rank reduction, S2 package diagonalization into generator
+//   matrices Gamma_1..Gamma_m on disjoint qubit sets, S3 the lower-bound
+//   schedule, the per-launch work description, and S6 witness decoding.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "dist_types.h"
+
+namespace dist {
+
+// A vector of F2^{2n} as two bit-planes; for F4 inputs the same planes hold
+// a + alpha b (x = coefficient of 1, z = coefficient of alpha).
+struct Vec {
+    uint32_t x[DIST_MAXW];
+    uint32_t z[DIST_MAXW];
+};
+
+// Coefficient vector over the kept basis rows.  F2: plane 0 holds one bit per
+// row.  F4: planes 0/1 hold the F4 scalar a + alpha b of each row.
+struct Coef {
+    uint32_t p[2][DIST_MAXCW];
+};
+
+enum UnitKind { UNIT_PACKAGE2 = 0, UNIT_PACKAGE1 = 1, UNIT_FREE = 2 };
+
+// One element of an enumeration: a package of rows sharing a pivot qubit, or a
+// free row.  A-units carry three representatives with rep[0]^rep[1]^rep[2]=0
+// (rank-2 package {g, h, g+h}, or an F4 row {g, alpha g, alpha^2 g});
+// B-units carry one.
+struct Unit {
+    int kind;
+    int qubit;   // pivot qubit, -1 for a free row
+    int nrep;    // 1 or 3
+    Vec rep[3];  // original qubit order
+    Coef coef[3];
+};
+
+struct Gamma {
+    std::vector<Unit> A, B;
+    int f = 0;                    // free rows (no pivot qubit)
+    int npack = 0;                // units with a pivot qubit
+    std::vector<int> pivots;      // pivot qubits, in pivot order
+    std::vector<int> perm;        // device position p -> original qubit
+    std::vector<uint32_t> dev_reps;   // [u][3][2][W], device qubit order
+    std::vector<uint32_t> dev_coefs;  // [u][3][2][CW]
+    int units() const { return (int)(A.size() + B.size()); }
+};
+
+struct Plan {
+    int n = 0, field = 2, W = 1, CW = 1;
+    int K_in = 0;                 // input rows
+    int k_eff = 0;                // rank: F2 rows (field 2) or F4 rows (field 4)
+    std::vector<Vec> input;       // input rows as planes
+    std::vector<int> kept;        // input row index of every basis row
+    std::vector<Vec> basis;
+    int n_stab = 0, s_rank = 0;   // exclusion: S = span(first n_stab input rows)
+    uint32_t outside[DIST_MAXCW] = {0};
+    std::vector<Gamma> gammas;    // every matrix built
+    std::vector<int> J;           // matrices enumerated, in order
+    int u0 = 0;                   // smallest weight among all representatives
+    int d_est = 0;                // random-code estimate used to choose J
+};
+
+enum { P_OK = 0, P_EINVAL = -1, P_ENOMEM = -2, P_EZERO = -6, P_ERANGE = -9 };
+
+// S1 + S2 + choice of J.  gen layout: field 2 -> K x 2n bytes {0,1} (x | z);
+// field 4 -> K x n bytes {0..3}, v = a + 2b for a + alpha b.
+int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p);
+
+// Minimum over C minus span(first n_stab input rows); 0 switches it off.
+int plan_set_exclude(Plan* p, int n_stab);
+
+// Lower bound on every codeword not yet enumerated once J[0..jpos] have
+// finished round r and J[jpos+1..] round r-1.  Returns DIST_WINF when some
+// matrix has enumerated all of its combinations (nothing left unseen).
+int plan_lower_bound(const Plan& p, int r, int jpos);
+int plan_initial_bound(const Plan& p);
+
+// Codewords (subset x representative choices) of round r of matrix g.
+double plan_round_count(const Plan& p, int g, int r);
+
+// Work description of round r of J[jpos] for a device with target_warps
+// resident warps.  Returns P_ERANGE if r is beyond the device walk's limits.
+int plan_step(const Plan& p, int jpos, int r, int L_prev, int target_warps,
+              EnumParams* ep, unsigned long long* codewords);
+
+// Rebuilds the codeword recorded in a witness slot.  witness: 2n bytes (F2)
+// or n bytes (F4); coeffs: K_in bytes over the input rows (F2 bits or F4
+// symbols).  Checks the weight and that the coefficients reproduce it.
+int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* coeffs);
+
+// Saturating binomial table [(DIST_MAXU+1) x (DIST_MAXR+1)].
+void binom_table(unsigned long long* tab);
+
+int vec_weight(const Vec& v, int W);
+
+}  // namespace dist

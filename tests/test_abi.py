@@ -1,0 +1,59 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function the
+public header declares (no device calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2408_10743_gb300 as dist
+from paper_2408_10743_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dist.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(dist_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("dist_init", "dist_solve", "dist_solve_bounded", "dist_free", "dist_set_exclude",
+                 "dist_strerror", "dist_intpeak"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(dist.library_path() if os.path.exists(dist.library_path()) else dist.lib()._name)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    # the binding wraps every declared function with the same name
+    assert set(declared_functions()) <= set(binding.SIGNATURES)
+
+
+def test_library_is_in_tree_and_built_for_sm103a():
+    path = dist.library_path()
+    dist.lib()
+    assert os.path.exists(path)
+    assert os.path.dirname(path).startswith(ROOT)
+    log = open(os.path.join(os.path.dirname(path), "_build", "compile.log")).read()
+    assert "arch=compute_103a,code=sm_103a" in log
+
+
+def test_strerror_and_version():
+    assert "sm_103a" in dist.dist_version()
+    assert dist.dist_strerror(-6).startswith("no nonzero")
+    assert dist.dist_strerror(12345) == "unknown error"
+
+
+def test_invalid_arguments_rejected_without_device():
+    import numpy as np
+    with pytest.raises(dist.DistError) as e:
+        dist.dist_plan_info_get(np.array([[2, 0]], dtype=np.uint8))
+    assert e.value.code == -1
+    with pytest.raises(dist.DistError) as e:
+        dist.dist_plan_info_get(np.zeros((2, 6), dtype=np.uint8))
+    assert e.value.code == -6

@@ -1,0 +1,183 @@
+"""The enumeration kernel's lane code (walk.cuh), the planner and the round
+loop, run on the CPU by a test-only harness (tests/hostwalk), against the
+oracle.  This checks the enumeration logic -- segments, revolving-door order,
+the 27-entry table with its Gray walk, the word-0 filter and slow path, the
+bounds -- without a GPU.  The GPU parity tests run the same code on device."""
+import ctypes
+import os
+import subprocess
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_10743_gb300 import synth
+from paper_2408_10743_gb300.binding import DistResult
+from codes import (f4_linear_f2_view, five_qubit, py_bruteforce, steane, sym_weight_bits,
+                   tiny_random_code, toric, f2_rank)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HW_DIR = os.path.join(ROOT, "tests", "hostwalk")
+CSRC = os.path.join(ROOT, "paper_2408_10743_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def hw():
+    out = os.path.join(HW_DIR, "libhostwalk.so")
+    srcs = [os.path.join(HW_DIR, "hostwalk.cpp"), os.path.join(CSRC, "plan.cpp")]
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    if not os.path.exists(out) or os.path.getmtime(out) < max(os.path.getmtime(p) for p in srcs + hdrs):
+        tmp = out + ".tmp.%d" % os.getpid()
+        subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-Wno-unknown-pragmas",
+                        "-I", CSRC, "-o", tmp] + srcs, check=True)
+        os.replace(tmp, out)
+    L = ctypes.CDLL(out)
+    L.hw_solve.restype = ctypes.c_int
+    L.hw_solve.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_int, ctypes.c_int, ctypes.POINTER(DistResult)]
+    L.hw_rd_walk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_uint8)]
+    return L
+
+
+def solve(L, g, field=2, n_stab=0, warps=4):
+    g = np.ascontiguousarray(g, dtype=np.uint8)
+    n = g.shape[1] // 2 if field == 2 else g.shape[1]
+    r = DistResult()
+    rc = L.hw_solve(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n, g.shape[0], field, n_stab,
+                    warps, ctypes.byref(r))
+    return rc, r
+
+
+def check_witness(g, r, field=2):
+    n = g.shape[1] // 2 if field == 2 else g.shape[1]
+    K = g.shape[0]
+    coeffs = np.frombuffer(bytes(r.coeffs), dtype=np.uint8)[:K]
+    if field == 2:
+        w = np.frombuffer(bytes(r.witness), dtype=np.uint8)[:2 * n]
+        assert sym_weight_bits(w, n) == r.d
+        rebuilt = np.bitwise_xor.reduce(g[coeffs.astype(bool)], axis=0)
+        assert np.array_equal(rebuilt, w)
+    else:
+        w = np.frombuffer(bytes(r.witness), dtype=np.uint8)[:n]
+        assert int(np.count_nonzero(w)) == r.d
+
+
+def rd_list(n, t):
+    """Revolving-door order by its recursive definition."""
+    if t == 0:
+        return [()]
+    if t == n:
+        return [tuple(range(n))]
+    if t > n:
+        return []
+    return rd_list(n - 1, t) + [s + (n - 1,) for s in reversed(rd_list(n - 1, t - 1))]
+
+
+def test_revolving_door_order(hw):
+    for n in range(1, 12):
+        for t in range(1, n + 1):
+            ref = rd_list(n, t)
+            total = comb(n, t)
+            assert len(ref) == total
+            for start in sorted({0, total // 3, total - 1}):
+                cnt = total - start
+                buf = (ctypes.c_uint8 * (cnt * t))()
+                hw.hw_rd_walk(n, t, start, cnt, buf)
+                got = [tuple(buf[i * t:(i + 1) * t]) for i in range(cnt)]
+                assert got == ref[start:], (n, t, start)
+            for a, b in zip(ref, ref[1:]):
+                assert len(set(a) ^ set(b)) == 2  # one unit out, one in
+
+
+@pytest.mark.parametrize("kind", ["iid", "css", "yheavy", "sparse"])
+def test_tiny_vs_oracle(hw, kind):
+    rng = np.random.default_rng({"iid": 31, "css": 32, "yheavy": 33, "sparse": 34}[kind])
+    for _ in range(150):
+        n = int(rng.integers(1, 9))
+        K = int(rng.integers(1, min(2 * n, 12) + 1))
+        g = tiny_random_code(rng, n, K, kind)
+        if not g.any():
+            continue
+        rc, r = solve(hw, g, warps=int(rng.integers(1, 4)))
+        assert rc == 0
+        assert r.d == oracle.bz(g)["d"]
+        check_witness(g, r)
+
+
+def test_medium_vs_oracle(hw):
+    """n up to 48 (two words per plane): fast path, word-0 filter, slow path."""
+    for t in range(30):
+        rng = synth.Xoshiro256ss(5000 + t)
+        n = 16 + rng.below(33)
+        K = (n + 1) // 2 + rng.below(n - (n + 1) // 2 + 1)
+        g = synth.random_f2_code(n, K, rng)
+        rc, r = solve(hw, g)
+        assert rc == 0
+        assert r.d == oracle.bz(g)["d"], (n, K)
+        check_witness(g, r)
+
+
+def test_workload0_and_1(hw):
+    g0 = synth.single_f2()
+    rc, r = solve(hw, g0)
+    assert rc == 0 and r.d == oracle.bruteforce(g0)[0]
+    check_witness(g0, r)
+    g1 = synth.single_f4()
+    rc, r = solve(hw, g1, field=4)
+    d1 = oracle.bz(g1, field=4)["d"]
+    assert rc == 0 and r.d == d1
+    check_witness(g1, r, field=4)
+    # the same code as an additive F2 code (rows g and alpha g)
+    rc, r2 = solve(hw, f4_linear_f2_view(g1))
+    assert rc == 0 and r2.d == d1
+
+
+def test_exclusion_known_codes(hw):
+    N, s = five_qubit()
+    assert solve(hw, N, n_stab=s)[1].d == 3
+    N, s = steane()
+    assert solve(hw, N, n_stab=s)[1].d == 3
+    for L in (2, 3, 4, 5):
+        N, s = toric(L)
+        rc, r = solve(hw, N)
+        assert rc == 0 and r.d == min(L, 4)
+        rc, r = solve(hw, N, n_stab=s)
+        assert rc == 0 and r.d == L
+        check_witness(N, r)
+
+
+def test_exclusion_random(hw):
+    rng = np.random.default_rng(35)
+    for t in range(120):
+        n = int(rng.integers(2, 7))
+        K = int(rng.integers(2, min(2 * n, 10) + 1))
+        g = tiny_random_code(rng, n, K, ["iid", "css", "yheavy"][t % 3])
+        s = int(rng.integers(1, K))
+        ref = py_bruteforce(g, n, n_stab=s)
+        rc, r = solve(hw, g, n_stab=s)
+        if ref is None:
+            assert rc == -6
+        else:
+            assert rc == 0 and r.d == ref
+
+
+def test_codeword_count_full_round(hw):
+    """A code whose distance forces complete rounds: the evaluated count equals
+    the sum over rounds and matrices of C(a,i) 3^i C(b, r-i)."""
+    import paper_2408_10743_gb300 as dist
+    g = synth.random_f2_code(20, 12, synth.Xoshiro256ss(77))
+    rc, r = solve(hw, g)
+    assert rc == 0
+    info = dist.dist_plan_info_get(g)
+    J = list(info.order[:info.n_gamma_used])
+    total = 0
+    for rr in range(1, r.rounds + 1):
+        for j in J:
+            a, b = info.a[j], info.b[j]
+            total += sum(comb(a, i) * 3 ** i * comb(b, rr - i) for i in range(0, rr + 1))
+    # the last round may stop early once U <= L; all earlier rounds are complete
+    last = sum(sum(comb(info.a[j], i) * 3 ** i * comb(info.b[j], r.rounds - i)
+                   for i in range(0, r.rounds + 1)) for j in J)
+    assert total - last <= r.codewords <= total

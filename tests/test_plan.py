@@ -1,0 +1,162 @@
+"""Host-side planner (steps S1-S3) checked on the CPU: the generator matrices
+built by the package diagonalization (Sections 2.2-2.3) are checked here
+with independent Python code, including the lemma behind the lower bound."""
+import itertools
+
+import numpy as np
+import pytest
+
+import paper_2408_10743_gb300 as dist
+from paper_2408_10743_gb300 import synth
+from codes import f2_rank, f4_mul, tiny_random_code, toric
+
+
+def proj(v, n, q):
+    return int(v[q]) | (int(v[n + q]) << 1)
+
+
+def load_gammas(g, field=2):
+    info = dist.dist_plan_info_get(g, field=field)
+    n = g.shape[1] // 2 if field == 2 else g.shape[1]
+    out = []
+    for j in range(info.n_gamma_built):
+        units = []
+        for u in range(info.a[j] + info.b[j]):
+            nrep = 3 if u < info.a[j] else 1
+            reps = []
+            q = kind = None
+            for e in range(nrep):
+                v, q, kind = dist.dist_plan_unit(g, j, u, e, field=field)
+                reps.append(v)
+            units.append({"reps": reps, "q": q, "kind": kind})
+        out.append({"units": units, "a": info.a[j], "b": info.b[j], "f": info.f[j]})
+    return info, n, out
+
+
+def f2_image(g, field):
+    if field == 2:
+        return g
+    from codes import f4_linear_f2_view
+    return f4_linear_f2_view(g)
+
+
+def check_structure(g, field=2):
+    info, n, gammas = load_gammas(g, field)
+    G2 = f2_image(g, field)
+    rank = f2_rank(G2)
+    used = set()
+    for gm in gammas:
+        reps_all = [r for u in gm["units"] for r in u["reps"]]
+        # every representative is a codeword
+        for r in reps_all:
+            assert f2_rank(np.vstack([G2, r])) == rank
+        # the units' independent representatives form a basis of the code
+        basis = []
+        for u in gm["units"]:
+            basis.append(u["reps"][0])
+            if len(u["reps"]) == 3:
+                basis.append(u["reps"][1])
+                assert np.array_equal(u["reps"][0] ^ u["reps"][1], u["reps"][2])
+        assert len(basis) == rank and f2_rank(np.array(basis)) == rank
+        assert gm["f"] == sum(1 for u in gm["units"] if u["kind"] == 2)
+        qs = [u["q"] for u in gm["units"] if u["q"] >= 0]
+        assert len(qs) == len(set(qs))
+        assert not (set(qs) & used)
+        used |= set(qs)
+        # package property: the unit's value at its pivot is never cancelled
+        for t, u in enumerate(gm["units"]):
+            if u["q"] < 0:
+                continue
+            q = u["q"]
+            mine = {proj(r, n, q) for r in u["reps"]}
+            assert 0 not in mine
+            others = [proj(r, n, q) for s, v in enumerate(gm["units"]) if s != t for r in v["reps"]]
+            span = {0}
+            for o in others:
+                span |= {x ^ o for x in span}
+            assert not (mine & span), (t, q, mine, span)
+    return info, gammas
+
+
+@pytest.mark.parametrize("kind", ["iid", "css", "yheavy", "sparse"])
+def test_package_structure_random(kind):
+    rng = np.random.default_rng({"iid": 21, "css": 22, "yheavy": 23, "sparse": 24}[kind])
+    for _ in range(25):
+        n = int(rng.integers(2, 9))
+        K = int(rng.integers(1, min(2 * n, 12) + 1))
+        g = tiny_random_code(rng, n, K, kind)
+        if not g.any():
+            continue
+        check_structure(g)
+
+
+def test_package_structure_f4():
+    rng = np.random.default_rng(25)
+    for _ in range(15):
+        n = int(rng.integers(3, 10))
+        k = int(rng.integers(1, min(n, 5) + 1))
+        g4 = rng.integers(0, 4, size=(k, n), dtype=np.uint8)
+        if not g4.any():
+            continue
+        info, gammas = check_structure(g4, field=4)
+        for gm in gammas:
+            for u in gm["units"]:
+                # representatives are g, alpha g, alpha^2 g
+                r0, r1 = u["reps"][0], u["reps"][1]
+                nn = len(r0) // 2
+                sym0 = r0[:nn] | (r0[nn:] << 1)
+                sym1 = r1[:nn] | (r1[nn:] << 1)
+                assert all(f4_mul(2, int(a)) == int(b) for a, b in zip(sym0, sym1))
+
+
+def test_structure_workloads():
+    check_structure(synth.single_f2())
+    info, _ = check_structure(synth.single_f4(), field=4)
+    assert info.n_gamma_used >= 1
+
+
+def test_qc72_plan_shape():
+    info = dist.dist_plan_info_get(synth.single_qc())
+    assert info.k_eff == 72 and info.n_gamma_built >= 2
+    assert info.a[0] + info.b[0] <= 72
+    assert info.f[0] == 0
+
+
+def test_bound_lemma_bruteforce():
+    """Every codeword, written in a generator matrix's units, weighs at least
+    (number of units used) - (free rows used) on that matrix's pivot qubits."""
+    rng = np.random.default_rng(26)
+    for trial in range(40):
+        n = int(rng.integers(2, 6))
+        K = int(rng.integers(1, min(2 * n, 8) + 1))
+        g = tiny_random_code(rng, n, K, ["iid", "css", "yheavy"][trial % 3])
+        if not g.any():
+            continue
+        info, n, gammas = load_gammas(g)
+        for gm in gammas:
+            units = gm["units"]
+            pivots = [u["q"] for u in units if u["q"] >= 0]
+            choices = [[None] + list(range(len(u["reps"]))) for u in units]
+            for pick in itertools.product(*choices):
+                v = np.zeros(2 * n, dtype=np.uint8)
+                used = free = 0
+                for u, e in zip(units, pick):
+                    if e is None:
+                        continue
+                    v ^= u["reps"][e]
+                    used += 1
+                    free += u["kind"] == 2
+                if used == 0:
+                    continue
+                wpiv = sum(1 for q in pivots if v[q] | v[n + q])
+                assert wpiv >= used - free
+                assert v.any()  # distinct unit choices never cancel
+
+
+def test_exclusion_rank():
+    N, s = toric(3)
+    info = dist.dist_plan_info_get(N, n_stab=s)
+    assert info.s_rank == s
+    with pytest.raises(dist.DistError) as e:
+        dist.dist_plan_info_get(N, n_stab=N.shape[0])
+    assert e.value.code == -6

@@ -141,7 +141,7 @@ int dist_plan_unit(const uint8_t *generator, int n, int K, int field, int gamma,
 /*
  * dist_intpeak -- integer issue microbenchmark used as the roofline
  * denominator.  Runs a loop of `iters` iterations of the enumeration's
- * per-codeword instruction mix (2 LOP3, 1 POPC, 1 min) on every SM and
+ * per-codeword instruction mix (2 LOP3, 1 POPC, half a 3-way min) on every SM and
  * reports codewords per second (mix_per_s) plus the rates of POPC alone
  * and LOP3 alone (operations per second) and the SM clock seen (MHz).
  */

@@ -11,9 +11,10 @@
 #include "solve.h"
 
 namespace dist {
-cudaError_t enum_launch(const EnumParams& P, int max_blocks, cudaStream_t st);
+cudaError_t enum_launch(const EnumParams& P, int grid, cudaStream_t st);
 size_t enum_smem_bytes(const EnumParams& P);
 int enum_blocks_per_sm(size_t smem);
+cudaError_t enum_set_max_smem(size_t bytes);
 struct IntpeakRaw {
     double mix_s, popc_s, lop3_s;
     double sm_mhz;
@@ -30,7 +31,8 @@ namespace {
 struct DeviceCtx {
     int device = -1;
     int sms = 0;
-    int blocks_per_sm = 0;
+    int blocks_per_sm = 0;          // at a small shared-memory footprint
+    size_t smem_optin = 0;          // largest dynamic shared memory per block
     unsigned long long* d_binom = nullptr;
 };
 
@@ -65,13 +67,12 @@ int device_ctx(DeviceCtx** out) {
         if (cudaMemcpy(d.d_binom, tab.data(), tab.size() * sizeof(unsigned long long),
                        cudaMemcpyHostToDevice) != cudaSuccess)
             return DIST_ECUDA;
-        // occupancy at the largest shared-memory footprint a code can need
-        EnumParams big;
-        memset(&big, 0, sizeof big);
-        big.a = 128;
-        big.b = 128;
-        big.W = DIST_MAXW;
-        d.blocks_per_sm = enum_blocks_per_sm(enum_smem_bytes(big));
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            return DIST_ECUDA;
+        d.smem_optin = (size_t)optin;
+        if (enum_set_max_smem(d.smem_optin) != cudaSuccess) return DIST_ECUDA;
+        d.blocks_per_sm = enum_blocks_per_sm(16 * 1024);
         if (d.blocks_per_sm < 1) return DIST_ECUDA;
         d.device = dev;
     }
@@ -84,8 +85,9 @@ int device_ctx(DeviceCtx** out) {
 struct dist_code {
     Plan plan;
     DeviceCtx* dev = nullptr;
-    uint32_t* d_tables = nullptr;
-    std::vector<size_t> rep_off, coef_off;   // word offsets per generator matrix
+    uint32_t* d_tables = nullptr;             // Plan::tables on the device
+    SegDesc* d_segs = nullptr;                // segment table of the current launch
+    SegDesc* h_segs = nullptr;                // pinned staging copy
     Scratch* d_scr = nullptr;
     Scratch* h_scr = nullptr;                 // pinned mirror for read-back
     cudaStream_t stream = nullptr;
@@ -97,6 +99,8 @@ namespace {
 void release(dist_code* c) {
     if (!c) return;
     if (c->d_tables) cudaFree(c->d_tables);
+    if (c->d_segs) cudaFree(c->d_segs);
+    if (c->h_segs) cudaFreeHost(c->h_segs);
     if (c->d_scr) cudaFree(c->d_scr);
     if (c->h_scr) cudaFreeHost(c->h_scr);
     if (c->e0) cudaEventDestroy(c->e0);
@@ -117,12 +121,24 @@ struct GpuExec {
         if (cudaMemsetAsync(c->d_scr, 0xFF, 2, st) != cudaSuccess) return DIST_ECUDA;
         return DIST_OK;
     }
+    int seed(uint32_t U0, const WitnessSlot& s) {
+        c->h_scr->U = U0;
+        c->h_scr->slot[U0] = s;
+        if (cudaMemcpyAsync(&c->d_scr->U, &c->h_scr->U, sizeof(uint32_t), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&c->d_scr->slot[U0], &c->h_scr->slot[U0], sizeof(WitnessSlot),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return DIST_ECUDA;
+        return DIST_OK;
+    }
     int target_warps() const { return c->dev->sms * c->dev->blocks_per_sm * 8; }
     double gpu_seconds() const { return gpu_s; }
     unsigned long long launches() const { return nl; }
-    int run(EnumParams& ep, double deadline_wall, StepResult* out) {
-        ep.reps = c->d_tables + c->rep_off[ep.gamma];
-        ep.coefs = c->d_tables + c->coef_off[ep.gamma];
+    int run(const LaunchPlan& lp, double deadline_wall, StepResult* out) {
+        EnumParams ep;
+        plan_params(c->plan, lp, &ep);
+        ep.tables = c->d_tables;
+        ep.segs = c->d_segs;
         ep.binom = c->dev->d_binom;
         ep.scr = c->d_scr;
         ep.budget_ns = 0;
@@ -130,10 +146,22 @@ struct GpuExec {
             double left = deadline_wall - wall_now();
             ep.budget_ns = left > 1e-3 ? (unsigned long long)(left * 1e9) : 1000000ull;
         }
+        const size_t smem = enum_smem_bytes(ep);
+        if (smem > c->dev->smem_optin) return DIST_ERANGE;
+        int bps = enum_blocks_per_sm(smem);
+        if (bps < 1) return DIST_ECUDA;
+        unsigned long long want = (lp.nchunks + 7) / 8;  // eight warps per block
+        if (want < 1) want = 1;
+        const unsigned long long cap = (unsigned long long)c->dev->sms * (unsigned long long)bps;
+        const int grid = (int)(want < cap ? want : cap);
+        memcpy(c->h_segs, lp.segs.data(), lp.segs.size() * sizeof(SegDesc));
+        if (cudaMemcpyAsync(c->d_segs, c->h_segs, lp.segs.size() * sizeof(SegDesc),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return DIST_ECUDA;
         if (cudaMemsetAsync(&c->d_scr->next_chunk, 0, sizeof(unsigned long long), st) != cudaSuccess)
             return DIST_ECUDA;
         cudaEventRecord(c->e0, st);
-        if (enum_launch(ep, c->dev->sms * c->dev->blocks_per_sm, st) != cudaSuccess) return DIST_ECUDA;
+        if (enum_launch(ep, grid, st) != cudaSuccess) return DIST_ECUDA;
         cudaEventRecord(c->e1, st);
         nl++;
         if (cudaMemcpyAsync(c->h_scr, c->d_scr, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -189,32 +217,21 @@ int dist_init(dist_code** out, const uint8_t* generator, int n, int K, int field
         delete c;
         return rc;
     }
-    size_t words = 0;
-    for (const Gamma& G : c->plan.gammas) {
-        c->rep_off.push_back(words);
-        words += G.dev_reps.size();
-        c->coef_off.push_back(words);
-        words += G.dev_coefs.size();
-        words = (words + 3) & ~(size_t)3;
-    }
-    std::vector<uint32_t> host(words, 0);
-    for (size_t g = 0; g < c->plan.gammas.size(); g++) {
-        const Gamma& G = c->plan.gammas[g];
-        memcpy(&host[c->rep_off[g]], G.dev_reps.data(), G.dev_reps.size() * 4);
-        memcpy(&host[c->coef_off[g]], G.dev_coefs.data(), G.dev_coefs.size() * 4);
-    }
+    const size_t words = c->plan.tables.size();
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&c->e0) != cudaSuccess || cudaEventCreate(&c->e1) != cudaSuccess) {
         release(c);
         return DIST_ECUDA;
     }
     if (cudaMalloc(&c->d_tables, words * 4) != cudaSuccess ||
+        cudaMalloc(&c->d_segs, DIST_MAXSEG * sizeof(SegDesc)) != cudaSuccess ||
+        cudaMallocHost(&c->h_segs, DIST_MAXSEG * sizeof(SegDesc)) != cudaSuccess ||
         cudaMalloc(&c->d_scr, sizeof(Scratch)) != cudaSuccess ||
         cudaMallocHost(&c->h_scr, sizeof(Scratch)) != cudaSuccess) {
         release(c);
         return DIST_ENOMEM;
     }
-    if (cudaMemcpyAsync(c->d_tables, host.data(), words * 4, cudaMemcpyHostToDevice, c->stream) !=
+    if (cudaMemcpyAsync(c->d_tables, c->plan.tables.data(), words * 4, cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
         release(c);
@@ -301,7 +318,7 @@ int dist_intpeak(dist_intpeak_result* out, int iters, void* cuda_stream) {
     IntpeakRaw r;
     if (intpeak_run(iters, (cudaStream_t)cuda_stream, &r) != cudaSuccess) return DIST_ECUDA;
     const double threads = (double)r.blocks * r.threads;
-    out->mix_per_s = threads * (double)iters * 27.0 / r.mix_s;
+    out->mix_per_s = threads * (double)iters * 81.0 / r.mix_s;
     out->popc_per_s = threads * (double)iters * 8.0 / r.popc_s;
     out->lop3_per_s = threads * (double)iters * 8.0 / r.lop3_s;
     out->sm_mhz = r.sm_mhz;

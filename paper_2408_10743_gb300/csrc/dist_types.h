@@ -15,17 +15,17 @@
 #define DIST_MAXCW 8           // 32-bit words of a coefficient plane (K <= 256)
 #define DIST_MAXU 256          // enumeration units of one generator matrix
 #define DIST_MAXR 32           // largest combination size walked on the device
-#define DIST_MAXSEG (DIST_MAXR + 2)
 #define DIST_MAXGAMMA 16
+#define DIST_MAXSEG 256        // segments in one launch
 #define DIST_WINF 0xFFFFu      // "no codeword yet" weight
-#define DIST_FAST_MAX_OUTER 20 // 3^20 < 2^32: outer Gray counter fits in 32 bits
+#define DIST_FAST_MAX_DYN 20   // 3^20 < 2^32: the dynamic Gray counter fits in 32 bits
 
 // One claimable record per weight value: the first thread that finds a
 // codeword of weight w (that passes the optional exclusion) writes how to
 // rebuild it -- generator matrix, chosen units and the representative of each.
 struct WitnessSlot {
     uint32_t claim;               // 0 = free
-    uint32_t gamma;               // generator matrix index (position in the plan)
+    uint32_t gamma;               // generator matrix index (in the plan)
     uint32_t count;               // number of chosen units
     uint32_t weight;
     uint8_t unit[DIST_MAXR];      // unit indices: A-units 0..a-1, B-units a..a+b-1
@@ -36,16 +36,29 @@ struct WitnessSlot {
 // next_chunk the work counter of the current launch.
 struct Scratch {
     uint32_t U;
-    uint32_t status;              // bit 0: stopped because U <= L, bit 1: deadline
+    uint32_t status;              // bit 1: time budget spent
     unsigned long long next_chunk;
     unsigned long long codewords; // (subset, representative) combinations evaluated
     unsigned long long pad;
     WitnessSlot slot[DIST_MAXN + 1];
 };
 
-// A segment of one enumeration step: the combinations with exactly i units
-// taken from the A-units (three representatives each) and r-i from the
-// B-units (one representative each).
+// A generator matrix as one launch sees it.
+struct GammaDesc {
+    uint32_t rep_off;     // word offset of its representatives in the global table buffer
+    uint32_t coef_off;    // word offset of its coefficient planes
+    uint32_t flag_off;    // word offset of its per-unit pivot flags
+    uint32_t s_rep;       // word offset of its representatives in shared memory
+    uint32_t s_r0;        // word offset of its word-0 table (U2 pairs) in shared memory
+    uint32_t s_flag;      // word offset of its pivot flags in shared memory
+    uint16_t a, b;        // A-units (three representatives), B-units (one)
+    int32_t gamma;        // index in the plan (witness decoding)
+};
+
+// A segment: within one step (round r of one generator matrix), the
+// combinations with exactly i A-units and r-i B-units.  L_before is the lower
+// bound that holds once every earlier step is complete: if U <= L_before the
+// segment (and everything after it) is not needed.
 struct SegDesc {
     unsigned long long NA;          // C(a, i): A-subsets
     unsigned long long NB;          // C(b, r - i): B-subsets
@@ -53,19 +66,23 @@ struct SegDesc {
     unsigned long long codes;       // representative choices per subset
     uint32_t i;
     uint32_t spl;                   // subsets per lane in one warp chunk
+    uint16_t g;                     // GammaDesc index
+    uint16_t r;
+    int32_t L_before;
 };
 
-// Everything one launch needs: one generator matrix, one round r.
+// Everything one launch needs.
 struct EnumParams {
-    const uint32_t* reps;         // [u][3][2][W] words, u = a + b, Gamma qubit order
-    const uint32_t* coefs;        // [u][3][2][CW] coefficient planes (exclusion)
-    const unsigned long long* binom;  // [DIST_MAXU + 1][DIST_MAXR + 1], saturating
+    const uint32_t* tables;             // all matrices: [u][3][2][W] reps, [u][3][2][CW] coefs
+    const SegDesc* segs;                // nseg segments (copied to shared memory)
+    const unsigned long long* binom;    // global [DIST_MAXU + 1][DIST_MAXR + 1], saturating
     Scratch* scr;
-    uint32_t outside[DIST_MAXCW]; // coefficient bits of rows outside S
-    int a, b, W, CW, r, gamma, proj, exclude;
-    int L_prev;                   // stop as soon as U <= L_prev
-    int nseg;
+    uint32_t outside[DIST_MAXCW];       // coefficient bits of rows outside S
+    int W, CW, proj, exclude;
+    int ng, nseg;
+    int brows, bcols;                   // shared binomial table shape
+    uint32_t s_binom, s_segs, s_words;  // shared-memory layout (32-bit word offsets, total)
     unsigned long long nchunks;
-    unsigned long long budget_ns;     // stop after this long (per block, %globaltimer); 0 = none
-    SegDesc seg[DIST_MAXSEG];
+    unsigned long long budget_ns;       // stop after this long (per block, %globaltimer); 0 = none
+    GammaDesc g[DIST_MAXGAMMA];
 };

@@ -1,16 +1,19 @@
 // enum.cu -- the enumeration kernel (steps S4-S5) for sm_103a.
 //
-// One launch = one round r of one generator matrix.  The matrix's
-// representatives (a few KB) are staged once per block into shared memory;
-// after that the kernel reads nothing from HBM except the running upper bound
-// U.  Warps pull chunks of combination ranks from a global counter
-// (persistent grid, one block per resident slot), every lane walks its
-// ranks with walk_range(), warps sum their codeword counts with shuffles, and
-// a lane that finds a lighter codeword publishes it with atomicMin on U and
-// claims the witness slot of that weight.  Every lane re-reads U once per
-// subset, so the whole grid stops shortly after U drops to the bound already
-// in force.  There is no spin-wait anywhere: the kernel ends when the chunks
-// run out, when U <= L, or when its time budget is spent.
+// One launch runs a run of consecutive enumeration steps (round r of one
+// generator matrix each), described by a segment table.  Every block stages
+// the representatives of the matrices involved, their word-0 tables, the
+// binomials the unranking needs and the segment table into shared memory
+// (tens of KB at most); after that the kernel reads nothing from HBM except
+// the running upper bound U.  Warps pull chunks of combination ranks from a
+// global counter (persistent grid); every lane walks its ranks with
+// walk_range(); warps sum their codeword counts with shuffles; a lane that
+// finds a lighter codeword publishes it with atomicMin on U and claims the
+// witness slot of that weight.  A chunk whose segment has L_before >= U is
+// not needed, and neither is anything after it (L_before only grows), so the
+// warp that sees it pushes the counter to the end and the grid drains.
+// There is no spin-wait: the kernel ends when the chunks run out or its time
+// budget is spent.
 #include <cuda_runtime.h>
 
 #include "walk.cuh"
@@ -19,14 +22,14 @@ namespace dist {
 
 struct DevSink {
     Scratch* scr;
-    int L_prev;
-    __device__ __forceinline__ bool poll(uint32_t& thr) {
+    __device__ __forceinline__ bool poll(uint32_t& thr, int L_before) {
         const uint32_t u = *reinterpret_cast<volatile uint32_t*>(&scr->U);
         thr = u < thr ? u : thr;
-        return (int)u <= L_prev;
+        return (int)u <= L_before;
     }
     __device__ __noinline__ void record(uint32_t w, int gamma, int count, const uint8_t* units,
                                         const uint8_t* digits) {
+        if (w >= *reinterpret_cast<volatile uint32_t*>(&scr->U)) return;  // not lighter than known
         atomicMin(&scr->U, w);
         WitnessSlot* s = &scr->slot[w];
         if (atomicCAS(&s->claim, 0u, 1u) == 0u) {
@@ -50,34 +53,40 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 extern __shared__ __align__(16) uint32_t g_enum_smem[];
 
-__global__ void __launch_bounds__(256, 2) enum_kernel(const __grid_constant__ EnumParams P) {
-    const int u = P.a + P.b;
-    const int nrep = u * 3 * 2 * P.W;
-    uint32_t* s_reps = g_enum_smem;
-    U2* s_r0 = reinterpret_cast<U2*>(g_enum_smem + ((nrep + 1) & ~1));
-    for (int t = threadIdx.x; t < nrep; t += blockDim.x) s_reps[t] = P.reps[t];
-    for (int t = threadIdx.x; t < P.a * 3; t += blockDim.x) {
-        s_r0[t].x = P.reps[(t * 2 + 0) * P.W];
-        s_r0[t].z = P.reps[(t * 2 + 1) * P.W];
+#ifndef DIST_ENUM_MINB
+#define DIST_ENUM_MINB 2
+#endif
+
+__global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_kernel(const __grid_constant__ EnumParams P) {
+    uint32_t* sm = g_enum_smem;
+    // stage: representatives and word-0 tables of every matrix in the launch
+    for (int gi = 0; gi < P.ng; gi++) {
+        const GammaDesc& g = P.g[gi];
+        const uint32_t* src = P.tables + g.rep_off;
+        const int nw = (g.a + g.b) * 6 * P.W;
+        for (int t = threadIdx.x; t < nw; t += blockDim.x) sm[g.s_rep + t] = src[t];
+        U2* r0 = reinterpret_cast<U2*>(sm + g.s_r0);
+        for (int t = threadIdx.x; t < g.a * 3; t += blockDim.x) {
+            r0[t].x = src[(t * 2 + 0) * P.W];
+            r0[t].z = src[(t * 2 + 1) * P.W];
+        }
+        for (int t = threadIdx.x; t < g.a + g.b; t += blockDim.x) sm[g.s_flag + t] = P.tables[g.flag_off + t];
+    }
+    unsigned long long* sbin = reinterpret_cast<unsigned long long*>(sm + P.s_binom);
+    for (int t = threadIdx.x; t < P.brows * P.bcols; t += blockDim.x) {
+        const int n = t / P.bcols, k = t - n * P.bcols;
+        sbin[t] = P.binom[n * (DIST_MAXR + 1) + k];
+    }
+    SegDesc* ssegs = reinterpret_cast<SegDesc*>(sm + P.s_segs);
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(P.segs);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(ssegs);
+        const int nw = P.nseg * (int)(sizeof(SegDesc) / 4);
+        for (int t = threadIdx.x; t < nw; t += blockDim.x) dst[t] = src[t];
     }
     __syncthreads();
 
-    LaneCtx C;
-    C.reps = s_reps;
-    C.r0 = s_r0;
-    C.coefs = P.coefs;
-    C.binom = P.binom;
-    C.outside = P.outside;
-    C.a = P.a;
-    C.b = P.b;
-    C.W = P.W;
-    C.CW = P.CW;
-    C.r = P.r;
-    C.gamma = P.gamma;
-    C.proj = P.proj;
-    C.exclude = P.exclude;
-    DevSink sink{P.scr, P.L_prev};
-
+    DevSink sink{P.scr};
     const int lane = threadIdx.x & 31;
     const unsigned long long t_start = P.budget_ns ? global_ns() : 0ull;
     uint32_t thr = DIST_WINF;
@@ -86,9 +95,40 @@ __global__ void __launch_bounds__(256, 2) enum_kernel(const __grid_constant__ En
         if (lane == 0) chunk = atomicAdd(&P.scr->next_chunk, 1ull);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= P.nchunks) break;
-        int sgi = 0;
-        while (sgi + 1 < P.nseg && P.seg[sgi + 1].chunk_base <= chunk) ++sgi;
-        const SegDesc sg = P.seg[sgi];
+        int lo_s = 0, hi_s = P.nseg;  // last segment with chunk_base <= chunk
+        while (hi_s - lo_s > 1) {
+            const int mid = (lo_s + hi_s) >> 1;
+            if (ssegs[mid].chunk_base <= chunk) lo_s = mid;
+            else hi_s = mid;
+        }
+        const SegDesc sg = ssegs[lo_s];
+        int skip = 0;
+        if (lane == 0) {
+            const uint32_t u = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
+            if ((int)u <= sg.L_before) {
+                skip = 1;
+                atomicMax(&P.scr->next_chunk, P.nchunks);
+            }
+        }
+        if (__shfl_sync(0xffffffffu, skip, 0)) break;
+        const GammaDesc& g = P.g[sg.g];
+        LaneCtx C;
+        C.reps = sm + g.s_rep;
+        C.r0 = reinterpret_cast<const U2*>(sm + g.s_r0);
+        C.flags = sm + g.s_flag;
+        C.coefs = P.tables + g.coef_off;
+        C.binom = sbin;
+        C.bstride = P.bcols;
+        C.outside = P.outside;
+        C.a = g.a;
+        C.b = g.b;
+        C.W = P.W;
+        C.CW = P.CW;
+        C.r = sg.r;
+        C.gamma = g.gamma;
+        C.proj = P.proj;
+        C.exclude = P.exclude;
+        C.L_before = sg.L_before;
         const unsigned long long total = sg.NA * sg.NB;
         const unsigned long long lo =
             (chunk - sg.chunk_base) * 32ull * sg.spl + (unsigned long long)lane * sg.spl;
@@ -102,10 +142,9 @@ __global__ void __launch_bounds__(256, 2) enum_kernel(const __grid_constant__ En
         int stop = 0;
         if (lane == 0) {
             if (done) atomicAdd(&P.scr->codewords, done);
-            const uint32_t uu = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
-            stop = (int)uu <= P.L_prev;
-            if (!stop && P.budget_ns && global_ns() - t_start > P.budget_ns) {
+            if (P.budget_ns && global_ns() - t_start > P.budget_ns) {
                 atomicOr(&P.scr->status, 2u);
+                atomicMax(&P.scr->next_chunk, P.nchunks);
                 stop = 1;
             }
         }
@@ -113,10 +152,7 @@ __global__ void __launch_bounds__(256, 2) enum_kernel(const __grid_constant__ En
     }
 }
 
-size_t enum_smem_bytes(const EnumParams& P) {
-    const size_t nrep = (size_t)(P.a + P.b) * 3 * 2 * P.W;
-    return ((nrep + 1) & ~(size_t)1) * 4 + (size_t)P.a * 3 * sizeof(U2);
-}
+size_t enum_smem_bytes(const EnumParams& P) { return (size_t)P.s_words * 4; }
 
 int enum_blocks_per_sm(size_t smem) {
     int nb = 0;
@@ -125,12 +161,12 @@ int enum_blocks_per_sm(size_t smem) {
     return nb;
 }
 
-cudaError_t enum_launch(const EnumParams& P, int max_blocks, cudaStream_t st) {
-    const size_t smem = enum_smem_bytes(P);
-    unsigned long long want = (P.nchunks + 7) / 8;  // eight warps per block
-    if (want < 1) want = 1;
-    const int grid = (int)(want < (unsigned long long)max_blocks ? want : (unsigned long long)max_blocks);
-    enum_kernel<<<grid, 256, smem, st>>>(P);
+cudaError_t enum_set_max_smem(size_t bytes) {
+    return cudaFuncSetAttribute(enum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t enum_launch(const EnumParams& P, int grid, cudaStream_t st) {
+    enum_kernel<<<grid, 256, enum_smem_bytes(P), st>>>(P);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,11 @@
 // intpeak.cu -- integer-issue microbenchmark: the roofline denominator of the
 // enumeration kernel, measured on the device it runs on.
 //
-//  * mix:  the enumeration's inner block exactly -- a 27-entry register table,
-//          per codeword t = (bx ^ Tx) | (bz ^ Tz), c = popc(t), m = min(m, c)
-//          (two LOP3, one POPC, one min) -- plus one base update per 27.
-//          Result: codewords per second the instruction mix allows.
+//  * mix:  the enumeration's inner block exactly -- a 9-entry register table
+//          swept 9 times with 8 base steps in between (81 codewords); per
+//          codeword t = (bx ^ Tx) | (bz ^ Tz), c = popc(t), folded with 3-way
+//          mins (two LOP3, one POPC, half a min).  Result: codewords per second
+//          the instruction mix allows.
 //  * popc: eight independent chains of popc(a ^ k).
 //  * lop3: eight independent chains of three-input logic ops.
 // Every kernel stores a data-dependent value so nothing is dead code.
@@ -22,12 +23,14 @@ __device__ __forceinline__ unsigned long long ip_ns() {
 __global__ void __launch_bounds__(256, 2) intpeak_mix(int iters, const uint32_t* seed, uint32_t* out,
                                                     unsigned long long* clk) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t Tx[27], Tz[27];
+    uint32_t Tx[9], Tz[9], D[6];
 #pragma unroll
-    for (int j = 0; j < 27; j++) {  // loaded, so the compiler cannot fold them into immediates
+    for (int j = 0; j < 9; j++) {  // loaded, so the compiler cannot fold them into immediates
         Tx[j] = seed[(tid + 2 * j) & 1023];
         Tz[j] = seed[(tid + 2 * j + 1) & 1023];
     }
+#pragma unroll
+    for (int j = 0; j < 6; j++) D[j] = seed[(tid + 31 * j + 7) & 1023];
     uint32_t bx = tid, bz = ~tid, acc = 0;
     unsigned long long c0 = 0, g0 = 0;
     if (tid == 0) {
@@ -35,17 +38,21 @@ __global__ void __launch_bounds__(256, 2) intpeak_mix(int iters, const uint32_t*
         g0 = ip_ns();
     }
     for (int it = 0; it < iters; it++) {
-        uint32_t m0 = 0xFFFFu, m1 = 0xFFFFu;
+        uint32_t m = 0xFFFFu;
 #pragma unroll
-        for (int j = 0; j < 27; j++) {
-            const uint32_t t = (bx ^ Tx[j]) | (bz ^ Tz[j]);
-            const uint32_t c = (uint32_t)__popc(t);
-            if (j & 1) m1 = c < m1 ? c : m1;
-            else m0 = c < m0 ? c : m0;
+        for (int s = 0; s < 9; s++) {  // 9 sweeps of 9 codewords, 8 base steps: 81 codewords
+            uint32_t c[9];
+#pragma unroll
+            for (int j = 0; j < 9; j++) c[j] = (uint32_t)__popc((bx ^ Tx[j]) | (bz ^ Tz[j]));
+            m = __vimin3_u32(m, __vimin3_u32(c[0], c[1], c[2]), __vimin3_u32(c[3], c[4], c[5]));
+            m = __vimin3_u32(m, __vimin3_u32(c[6], c[7], c[8]), m);
+            if (s < 8) {
+                bx ^= D[s % 3];
+                bz ^= D[3 + s % 3];
+            }
         }
-        acc += m0 < m1 ? m0 : m1;
+        acc += m;
         bx += 0x9E3779B9u;
-        bz ^= bx;
     }
     if (tid == 0) {
         clk[0] = clock64() - c0;

@@ -367,6 +367,15 @@ static void build_device_tables(const Plan& p, Gamma& G) {
     const int u = G.units(), W = p.W, CW = p.CW;
     G.dev_reps.assign((size_t)u * 3 * 2 * W, 0);
     G.dev_coefs.assign((size_t)u * 3 * 2 * CW, 0);
+    // A package is nonzero at its pivot in every combination that uses it; if
+    // the pivot sits outside word 0 this adds one to the word-0 lower bound.
+    std::vector<int> pos_of(p.n, 0);
+    for (int pos = 0; pos < p.n; pos++) pos_of[G.perm[pos]] = pos;
+    G.dev_flags.assign((size_t)u, 0);
+    for (int t = 0; t < u; t++) {
+        const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
+        if (x.qubit >= 0 && pos_of[x.qubit] >= 32) G.dev_flags[t] = 1;
+    }
     for (int t = 0; t < u; t++) {
         const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
         for (int e = 0; e < x.nrep; e++) {
@@ -389,6 +398,33 @@ static bool coef_outside(const Plan& p, const Coef& c) {
     for (int w = 0; w < p.CW; w++)
         if ((c.p[0][w] | c.p[1][w]) & p.outside[w]) return true;
     return false;
+}
+
+// Lightest representative of any matrix (outside S if only_outside): its
+// weight and a witness slot naming it.
+static void lightest_rep(const Plan& p, bool only_outside, int* w_out, WitnessSlot* slot) {
+    int best = DIST_WINF;
+    memset(slot, 0, sizeof *slot);
+    for (size_t g = 0; g < p.gammas.size(); g++) {
+        const Gamma& G = p.gammas[g];
+        for (int t = 0; t < G.units(); t++) {
+            const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
+            for (int e = 0; e < x.nrep; e++) {
+                if (only_outside && !coef_outside(p, x.coef[e])) continue;
+                int w = vec_weight(x.rep[e], p.W);
+                if (w < best) {
+                    best = w;
+                    slot->claim = 1;
+                    slot->gamma = (uint32_t)g;
+                    slot->count = 1;
+                    slot->weight = (uint32_t)w;
+                    slot->unit[0] = (uint8_t)t;
+                    slot->digit[0] = (uint8_t)e;
+                }
+            }
+        }
+    }
+    *w_out = best;
 }
 
 // Number of codewords in round r of matrix g (F4: projective, first scalar 1).
@@ -475,12 +511,26 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
     }
     if (p->gammas.empty()) return P_EZERO;
 
-    p->u0 = DIST_WINF;
-    for (const Gamma& G : p->gammas) {
-        for (const Unit& x : G.A)
-            for (int e = 0; e < x.nrep; e++) p->u0 = std::min(p->u0, vec_weight(x.rep[e], p->W));
-        for (const Unit& x : G.B) p->u0 = std::min(p->u0, vec_weight(x.rep[0], p->W));
+    size_t off = 0;
+    for (Gamma& G : p->gammas) {
+        G.rep_off = (uint32_t)off;
+        off += G.dev_reps.size();
+        G.coef_off = (uint32_t)off;
+        off += G.dev_coefs.size();
+        G.flag_off = (uint32_t)off;
+        off += G.dev_flags.size();
+        off = (off + 3) & ~(size_t)3;
     }
+    p->tables.assign(off, 0);
+    for (const Gamma& G : p->gammas) {
+        std::copy(G.dev_reps.begin(), G.dev_reps.end(), p->tables.begin() + G.rep_off);
+        std::copy(G.dev_coefs.begin(), G.dev_coefs.end(), p->tables.begin() + G.coef_off);
+        std::copy(G.dev_flags.begin(), G.dev_flags.end(), p->tables.begin() + G.flag_off);
+    }
+
+    // The lightest representative is a codeword: it seeds the upper bound.
+    p->u0 = DIST_WINF;
+    lightest_rep(*p, false, &p->u0, &p->u0_slot);
     // Expected number of nonzero codewords of weight <= w in a random code of
     // the same size: 2^(K2 - 2n) * sum_v C(n, v) 3^v.  d_est = first w where it
     // reaches 1, capped by the lightest representative.
@@ -495,6 +545,8 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
         }
     }
     p->d_est = std::max(1, std::min(p->d_est, p->u0));
+    p->u0_excl = p->u0;
+    p->u0_excl_slot = p->u0_slot;
     choose_J(p);
     return P_OK;
 }
@@ -508,65 +560,149 @@ int plan_set_exclude(Plan* p, int n_stab) {
     memset(p->outside, 0, sizeof p->outside);
     if (n_stab > 0)
         for (int i = p->s_rank; i < p->k_eff; i++) setb(p->outside, i);
+    // lightest representative outside S: an upper bound on the excluded minimum
+    p->u0_excl = p->u0;
+    p->u0_excl_slot = p->u0_slot;
+    if (n_stab > 0) {
+        p->u0_excl = DIST_WINF;
+        lightest_rep(*p, true, &p->u0_excl, &p->u0_excl_slot);
+    }
     if (n_stab > 0 && p->s_rank == p->k_eff) return P_EZERO;
     return P_OK;
 }
 
-int plan_step(const Plan& p, int jpos, int r, int L_prev, int target_warps, EnumParams* ep,
-              unsigned long long* codewords) {
-    if (r < 1 || r > DIST_MAXR) return P_ERANGE;
-    const int g = p.J[jpos];
-    const Gamma& G = p.gammas[g];
-    memset(ep, 0, sizeof *ep);
-    ep->a = (int)G.A.size();
-    ep->b = (int)G.B.size();
-    ep->W = p.W;
-    ep->CW = p.CW;
-    ep->r = r;
-    ep->gamma = g;
-    ep->proj = p.field == 4 ? 1 : 0;
-    ep->exclude = p.n_stab > 0 ? 1 : 0;
-    for (int w = 0; w < DIST_MAXCW; w++) ep->outside[w] = p.outside[w];
-    ep->L_prev = L_prev;
-    const int a = ep->a, b = ep->b;
-    unsigned long long total = 0, chunks = 0;
-    double dtotal = 0;
-    int imin = std::max(0, r - b), imax = std::min(r, a);
-    if (ep->proj) imin = std::max(imin, 1);
-    for (int i = imin; i <= imax; i++) {
-        unsigned long long NA = ubinom(a, i), NB = ubinom(b, r - i);
-        unsigned long long codes = ep->proj ? upow3(i - 1) : upow3(i);
-        if (NA == 0 || NB == 0) continue;
-        if (NA == ~0ull || NB == ~0ull || codes == ~0ull) return P_ERANGE;
-        unsigned __int128 subsets = (unsigned __int128)NA * NB;
-        if (subsets >> 62) return P_ERANGE;
-        dtotal += (double)subsets * (double)codes;
+int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int target_warps,
+                double max_codewords, LaunchPlan* lp) {
+    *lp = LaunchPlan();
+    lp->W = p.W;
+    lp->CW = p.CW;
+    lp->proj = p.field == 4 ? 1 : 0;
+    lp->exclude = p.n_stab > 0 ? 1 : 0;
+    std::vector<int> gslot(p.gammas.size(), -1);
+    int L = L_prev, maxrow = 1, maxr = 1;
+    double total = 0;
+    std::vector<double> seg_cw;
+    for (;;) {
+        if (r > DIST_MAXR) {
+            if (lp->step_r.empty()) return P_ERANGE;
+            break;
+        }
+        if (!lp->step_r.empty() && (L >= U_bound || total >= max_codewords)) break;
+        const int g = p.J[jpos];
+        const Gamma& G = p.gammas[g];
+        const int a = (int)G.A.size(), b = (int)G.B.size();
+        int imin = std::max(0, r - b), imax = std::min(r, a);
+        if (lp->proj) imin = std::max(imin, 1);
+        if (imax >= imin && lp->segs.size() + (imax - imin + 1) > DIST_MAXSEG) {
+            if (lp->step_r.empty()) return P_ERANGE;
+            break;
+        }
+        if (gslot[g] < 0) {
+            gslot[g] = (int)lp->g.size();
+            GammaDesc d;
+            memset(&d, 0, sizeof d);
+            d.rep_off = G.rep_off;
+            d.coef_off = G.coef_off;
+            d.flag_off = G.flag_off;
+            d.a = (uint16_t)a;
+            d.b = (uint16_t)b;
+            d.gamma = g;
+            lp->g.push_back(d);
+        }
+        for (int i = imin; i <= imax; i++) {
+            unsigned long long NA = ubinom(a, i), NB = ubinom(b, r - i);
+            unsigned long long codes = lp->proj ? upow3(i - 1) : upow3(i);
+            if (NA == 0 || NB == 0) continue;
+            if (NA == ~0ull || NB == ~0ull || codes == ~0ull) return P_ERANGE;
+            if (((unsigned __int128)NA * NB) >> 62) return P_ERANGE;
+            SegDesc sd;
+            memset(&sd, 0, sizeof sd);
+            sd.NA = NA;
+            sd.NB = NB;
+            sd.codes = codes;
+            sd.i = (uint32_t)i;
+            sd.g = (uint16_t)gslot[g];
+            sd.r = (uint16_t)r;
+            sd.L_before = L;
+            lp->segs.push_back(sd);
+            const double cw = (double)NA * (double)NB * (double)codes;
+            seg_cw.push_back(cw);
+            total += cw;
+        }
+        lp->step_r.push_back(r);
+        lp->step_jpos.push_back(jpos);
+        lp->step_L_before.push_back(L);
+        maxrow = std::max(maxrow, std::max(a, b));
+        maxr = std::max(maxr, r);
+        L = plan_lower_bound(p, r, jpos);
+        if (++jpos == (int)p.J.size()) {
+            jpos = 0;
+            ++r;
+        }
+        if (L == (int)DIST_WINF) break;  // this step finished a complete enumeration
     }
-    // Subsets per lane: about six warp-chunks per resident warp, a lane chunk
-    // of at most ~2^21 codewords so that a stop request is seen quickly.
-    double per_lane = dtotal / (32.0 * std::max(1, target_warps) * 6.0);
-    per_lane = std::min(per_lane, (double)(1u << 21));
-    for (int i = imin; i <= imax; i++) {
-        unsigned long long NA = ubinom(a, i), NB = ubinom(b, r - i);
-        if (NA == 0 || NB == 0) continue;
-        unsigned long long codes = ep->proj ? upow3(i - 1) : upow3(i);
-        unsigned long long subsets = NA * NB;
-        double spl_d = per_lane / (double)codes;
+    lp->next_r = r;
+    lp->next_jpos = jpos;
+    lp->codewords = total;
+    // Chunks: each segment is cut into about six warp-chunks per resident warp
+    // (so that every segment spreads over the whole GPU); a lane chunk holds at
+    // most ~2^21 codewords so that stop requests are seen soon.
+    unsigned long long chunks = 0;
+    for (size_t t = 0; t < lp->segs.size(); t++) {
+        SegDesc& sd = lp->segs[t];
+        double per_lane = seg_cw[t] / (32.0 * std::max(1, target_warps) * 6.0);
+        per_lane = std::min(per_lane, (double)(1u << 21));
+        double spl_d = per_lane / (double)sd.codes;
         unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
         if (spl > (1ull << 30)) spl = 1ull << 30;
-        SegDesc& s = ep->seg[ep->nseg++];
-        s.NA = NA;
-        s.NB = NB;
-        s.codes = codes;
-        s.i = (uint32_t)i;
-        s.spl = (uint32_t)spl;
-        s.chunk_base = chunks;
-        chunks += (subsets + 32 * spl - 1) / (32 * spl);
-        total += subsets * codes;
+        sd.spl = (uint32_t)spl;
+        sd.chunk_base = chunks;
+        chunks += (sd.NA * sd.NB + 32 * spl - 1) / (32 * spl);
     }
-    ep->nchunks = chunks;
-    if (codewords) *codewords = total;
+    lp->nchunks = chunks;
+    // Shared memory (32-bit words): representatives of every matrix, their
+    // word-0 tables, the binomials the launch can need, the segment table.
+    uint32_t off = 0;
+    for (GammaDesc& d : lp->g) {
+        d.s_rep = off;
+        off += (uint32_t)(d.a + d.b) * 6u * (uint32_t)p.W;
+    }
+    for (GammaDesc& d : lp->g) {
+        off = (off + 1) & ~1u;
+        d.s_r0 = off;
+        off += (uint32_t)d.a * 6u;
+    }
+    for (GammaDesc& d : lp->g) {
+        d.s_flag = off;
+        off += (uint32_t)(d.a + d.b);
+    }
+    off = (off + 1) & ~1u;
+    lp->s_binom = off;
+    lp->brows = maxrow + 1;
+    lp->bcols = maxr + 1;
+    off += (uint32_t)(lp->brows * lp->bcols) * 2u;
+    lp->s_segs = off;
+    off += (uint32_t)(lp->segs.size() * sizeof(SegDesc) / 4);
+    lp->s_words = off;
     return P_OK;
+}
+
+void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep) {
+    memset(ep, 0, sizeof *ep);
+    for (int w = 0; w < DIST_MAXCW; w++) ep->outside[w] = p.outside[w];
+    ep->W = lp.W;
+    ep->CW = lp.CW;
+    ep->proj = lp.proj;
+    ep->exclude = lp.exclude;
+    ep->ng = (int)lp.g.size();
+    for (size_t t = 0; t < lp.g.size(); t++) ep->g[t] = lp.g[t];
+    ep->nseg = (int)lp.segs.size();
+    ep->brows = lp.brows;
+    ep->bcols = lp.bcols;
+    ep->s_binom = lp.s_binom;
+    ep->s_segs = lp.s_segs;
+    ep->s_words = lp.s_words;
+    ep->nchunks = lp.nchunks;
 }
 
 int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* coeffs) {

@@ -46,6 +46,8 @@ struct Gamma {
     std::vector<int> perm;        // device position p -> original qubit
     std::vector<uint32_t> dev_reps;   // [u][3][2][W], device qubit order
     std::vector<uint32_t> dev_coefs;  // [u][3][2][CW]
+    std::vector<uint32_t> dev_flags;  // [u]: 1 if a package whose pivot lies outside word 0
+    uint32_t rep_off = 0, coef_off = 0, flag_off = 0;  // word offsets in Plan::tables
     int units() const { return (int)(A.size() + B.size()); }
 };
 
@@ -60,8 +62,24 @@ struct Plan {
     uint32_t outside[DIST_MAXCW] = {0};
     std::vector<Gamma> gammas;    // every matrix built
     std::vector<int> J;           // matrices enumerated, in order
+    std::vector<uint32_t> tables; // every matrix's device tables, concatenated
     int u0 = 0;                   // smallest weight among all representatives
+    int u0_excl = 0;              // same, among representatives outside S (exclusion)
+    WitnessSlot u0_slot{}, u0_excl_slot{};  // which representative reaches them
     int d_est = 0;                // random-code estimate used to choose J
+};
+
+// Consecutive enumeration steps (round r of matrix J[jpos]) run by one launch.
+struct LaunchPlan {
+    std::vector<SegDesc> segs;
+    std::vector<GammaDesc> g;
+    std::vector<int> step_r, step_jpos, step_L_before;
+    int W = 1, CW = 1, proj = 0, exclude = 0;
+    int brows = 0, bcols = 0;
+    uint32_t s_binom = 0, s_segs = 0, s_words = 0;  // shared-memory layout
+    unsigned long long nchunks = 0;
+    double codewords = 0;         // if every step completes
+    int next_r = 0, next_jpos = 0;
 };
 
 enum { P_OK = 0, P_EINVAL = -1, P_ENOMEM = -2, P_EZERO = -6, P_ERANGE = -9 };
@@ -82,10 +100,16 @@ int plan_initial_bound(const Plan& p);
 // Codewords (subset x representative choices) of round r of matrix g.
 double plan_round_count(const Plan& p, int g, int r);
 
-// Work description of round r of J[jpos] for a device with target_warps
-// resident warps.  Returns P_ERANGE if r is beyond the device walk's limits.
-int plan_step(const Plan& p, int jpos, int r, int L_prev, int target_warps,
-              EnumParams* ep, unsigned long long* codewords);
+// Steps from (r, jpos) onward for one launch: at least one, then more while
+// the estimated work stays under max_codewords, the segment table fits, and
+// the bound in force before the next step is still below U_bound (a step
+// with L_before >= U can never be needed).  L_prev is the bound in force
+// before (r, jpos).  Returns P_ERANGE if r exceeds the device walk's limits.
+int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int target_warps,
+                double max_codewords, LaunchPlan* lp);
+
+// Fills the launch-independent part of EnumParams (pointers stay null).
+void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep);
 
 // Rebuilds the codeword recorded in a witness slot.  witness: 2n bytes (F2)
 // or n bytes (F4); coeffs: K_in bytes over the input rows (F2 bits or F4

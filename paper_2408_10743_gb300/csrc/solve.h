@@ -1,5 +1,5 @@
 // solve.h -- the round loop of Brouwer-Zimmermann (steps S3 and S6), generic
-// over the executor that runs one enumeration step.
+// over the executor that runs one launch of enumeration steps.
 //
 // Bounds (Section 2.1; Section 2.3 for the package argument and the bound of
 // the second matrix): a combination that uses g units of a matrix weighs at
@@ -8,8 +8,16 @@
 // of the others are finished, every codeword not yet seen has at least r+1
 // (resp. r) units in each matrix, so it weighs at least
 //     L = sum_{t <= jpos} max(0, r + 1 - f_t) + sum_{t > jpos} max(0, r - f_t).
-// The upper bound U is the lightest codeword found.  Stop when L >= U; the
-// kernels also stop early as soon as U <= the L already established.
+// The upper bound U is the lightest codeword found.
+//
+// One launch runs a run of consecutive steps; each segment carries L_before,
+// the bound that holds once every earlier step is complete, and the kernel
+// drops work of a segment as soon as U <= its L_before.  After the launch let
+// s be the first step with U <= L_before(s).  No chunk of a step before s was
+// dropped (a drop needs U <= L_before there, and U only decreases), so all
+// steps before s are complete, every unseen codeword weighs at least
+// L_before(s) >= U, and d = U.  If no such s exists nothing was dropped and
+// the bound after the launch's last step holds; d = U once it reaches U.
 #pragma once
 #include <string.h>
 #include <time.h>
@@ -33,9 +41,13 @@ static inline double wall_now() {
     return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
 }
 
+// Work allowed in one launch (codewords, ~ a few seconds of a GB300).
+static const double kLaunchCodewords = 2e13;
+
 // Exec must provide:
 //   int reset();                                   // U = DIST_WINF, counters and slots cleared
-//   int run(EnumParams& ep, double deadline_wall, StepResult* out);
+//   int seed(uint32_t U0, const WitnessSlot& s);   // U = U0 with s in slot[U0]
+//   int run(const LaunchPlan& lp, double deadline_wall, StepResult* out);
 //   int read_slot(uint32_t w, WitnessSlot* out);
 //   int target_warps() const;
 //   double gpu_seconds() const; unsigned long long launches() const;
@@ -52,44 +64,50 @@ int solve_loop(const Plan& p, Exec& ex, double time_limit_s, dist_result* out) {
     uint32_t U = DIST_WINF;
     StepResult sr{DIST_WINF, 0, 0};
     int status = DIST_OK;
-    bool done = false;
-    for (int r = 1; !done; r++) {
-        for (int jpos = 0; jpos < (int)p.J.size() && !done; jpos++) {
-            EnumParams ep;
-            unsigned long long cw = 0;
-            int prc = plan_step(p, jpos, r, L, ex.target_warps(), &ep, &cw);
-            if (prc) {
-                status = prc == P_ERANGE ? DIST_ERANGE : DIST_EINVAL;
-                done = true;
+    int r = 1, jpos = 0;
+    // The lightest representative is a codeword (outside S in exclusion
+    // mode): start from it, so that no lane ever filters against "infinity".
+    const int ubound0 = p.n_stab > 0 ? p.u0_excl : p.u0;
+    if (ubound0 < (int)DIST_WINF) {
+        rc = ex.seed((uint32_t)ubound0, p.n_stab > 0 ? p.u0_excl_slot : p.u0_slot);
+        if (rc) return rc;
+        U = (uint32_t)ubound0;
+        sr.U = U;
+    }
+    for (;;) {
+        LaunchPlan lp;
+        const int ub = std::min<int>((int)U, ubound0);
+        int prc = plan_launch(p, r, jpos, L, ub, ex.target_warps(), kLaunchCodewords, &lp);
+        if (prc) {
+            status = prc == P_ERANGE ? DIST_ERANGE : DIST_EINVAL;
+            break;
+        }
+        rc = ex.run(lp, deadline, &sr);
+        if (rc) return rc;
+        U = sr.U;
+        bool certified = false;
+        for (size_t s = 0; s < lp.step_r.size(); s++) {
+            if (U != DIST_WINF && (int)U <= lp.step_L_before[s]) {
+                certified = true;
+                L = lp.step_L_before[s];
                 break;
             }
-            out->rounds = r;
-            rc = ex.run(ep, deadline, &sr);
-            if (rc) return rc;
-            U = sr.U;
-            if (U != DIST_WINF && (int)U <= L) {  // certified by a bound already in force
-                done = true;
-                break;
-            }
-            if (sr.status & 2u) {                  // the kernel hit the deadline
-                status = DIST_EINCOMPLETE;
-                done = true;
-                break;
-            }
-            L = plan_lower_bound(p, r, jpos);
-            if (L == (int)DIST_WINF) {             // a matrix has been enumerated completely
-                done = true;
-                break;
-            }
-            if (U != DIST_WINF && L >= (int)U) {
-                done = true;
-                break;
-            }
-            if (deadline > 0 && wall_now() > deadline) {
-                status = DIST_EINCOMPLETE;
-                done = true;
-                break;
-            }
+            out->rounds = lp.step_r[s];  // last step known to be complete so far
+        }
+        if (certified) break;
+        if (sr.status & 2u) {  // the kernel spent its time budget
+            status = DIST_EINCOMPLETE;
+            L = lp.step_L_before[0];
+            break;
+        }
+        L = plan_lower_bound(p, lp.step_r.back(), lp.step_jpos.back());
+        if (L == (int)DIST_WINF) break;  // a matrix has been enumerated completely
+        if (U != DIST_WINF && L >= (int)U) break;
+        r = lp.next_r;
+        jpos = lp.next_jpos;
+        if (deadline > 0 && wall_now() > deadline) {
+            status = DIST_EINCOMPLETE;
+            break;
         }
     }
     out->codewords = sr.codewords;

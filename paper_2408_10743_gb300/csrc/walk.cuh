@@ -11,15 +11,21 @@
 // Consecutive subsets differ by one unit out and one unit in; a lane unranks
 // its first subset from the combinatorial number system and then steps.
 //
-// Order of representatives (the fast path): the three largest units of the
-// subset form a 27-entry table of word-0 partial sums held in registers; the
-// other units' digits advance by a modular ternary Gray code (step k changes
-// digit nu_3(k) by +1 mod 3, which XORs the unit's third representative,
-// since rep0 ^ rep1 ^ rep2 = 0).  Every codeword then costs two LOP3, one
-// POPC and one min on word 0 of each plane.  Word 0 holds the qubits that are
-// not pivots of this matrix, so popc(word 0) is a sharp lower bound on the
-// weight; only when it falls below the current upper bound is the full
-// weight computed (the slow path), which keeps the result exact.
+// Order of representatives (the fast path, i >= 4 varying units).  Sorted
+// positions of the subset play three roles:
+//   i-1, i-2  : a 9-entry register table T of word-0 partial sums;
+//   i-3, i-4  : two "register digits" B and A whose deltas sit in registers;
+//   the rest  : "dynamic digits", advanced by a modular ternary Gray code
+//               (step k changes digit nu_3(k) by +1 mod 3).
+// Changing a digit from e to e+1 XORs the unit's third representative
+// (rep0 ^ rep1 ^ rep2 = 0), so one block of 81 codewords is 9 table sweeps
+// separated by the 8 steps of a 2-digit ternary Gray code over A and B, and
+// a dynamic step follows every block.  A codeword costs two LOP3, one POPC
+// and about half a 3-way min on word 0 of each plane.  Word 0 holds qubits
+// that are not pivots of this generator matrix, so popc(word 0) is a sharp
+// lower bound on the weight; only when a block's minimum falls below the
+// current upper bound is it re-walked with full weights (the slow path), so
+// the result is exact.
 #pragma once
 #include "dist_types.h"
 
@@ -27,10 +33,14 @@ namespace dist {
 
 #if defined(__CUDACC__)
 #define DIST_HD_COLD __host__ __device__ __noinline__
-#define DIST_HD_HOT __host__ __device__ __noinline__
+#if defined(DIST_FAST_NOINLINE)
+#define DIST_HD_FAST __host__ __device__ __noinline__
+#else
+#define DIST_HD_FAST __host__ __device__ __forceinline__
+#endif
 #else
 #define DIST_HD_COLD inline
-#define DIST_HD_HOT inline
+#define DIST_HD_FAST inline
 #endif
 
 struct U2 {
@@ -45,22 +55,34 @@ DIST_HD int popc32(uint32_t v) {
 #endif
 }
 
-DIST_HD unsigned long long binom_at(const unsigned long long* B, int n, int k) {
-    if (k < 0 || n < k) return 0ull;
-    return B[n * (DIST_MAXR + 1) + k];
+DIST_HD uint32_t min3u(uint32_t a, uint32_t b, uint32_t c) {
+#if defined(__CUDA_ARCH__)
+    return __vimin3_u32(a, b, c);
+#else
+    uint32_t m = a < b ? a : b;
+    return m < c ? m : c;
+#endif
 }
 
-// Subset of revolving-door rank R, t elements, written ascending into s.
-DIST_HD void rd_unrank(const unsigned long long* B, unsigned long long R, int t, uint8_t* s) {
+DIST_HD unsigned long long binom_at(const unsigned long long* B, int stride, int n, int k) {
+    if (k < 0 || n < k) return 0ull;
+    return B[n * stride + k];
+}
+
+// Subset of revolving-door rank R (0 <= R < C(n, t)), t elements of
+// {0..n-1}, written ascending into s.
+DIST_HD void rd_unrank(const unsigned long long* B, int stride, int n, unsigned long long R, int t,
+                       uint8_t* s) {
     for (int tt = t; tt >= 1; --tt) {
-        int lo = tt - 1, hi = DIST_MAXU;  // C(lo, tt) <= R < C(hi, tt)
+        int lo = tt - 1, hi = n;  // C(lo, tt) <= R < C(hi, tt)
         while (hi - lo > 1) {
             int mid = (lo + hi) >> 1;
-            if (binom_at(B, mid, tt) <= R) lo = mid;
+            if (binom_at(B, stride, mid, tt) <= R) lo = mid;
             else hi = mid;
         }
         s[tt - 1] = (uint8_t)lo;
-        R = binom_at(B, lo + 1, tt) - 1 - R;
+        R = binom_at(B, stride, lo + 1, tt) - 1 - R;
+        n = lo;
     }
 }
 
@@ -104,14 +126,18 @@ r5:
 #undef DIST_CJ
 }
 
-// What a lane reads.  reps / r0 live in shared memory on the device.
+// What a lane reads for one segment.  reps / r0 / binom live in shared
+// memory on the device.
 struct LaneCtx {
     const uint32_t* reps;              // [u][3][2][W]
     const U2* r0;                      // [a][3]: word 0 of the A-units' representatives
+    const uint32_t* flags;             // [u]: package with its pivot outside word 0
     const uint32_t* coefs;             // [u][3][2][CW]
-    const unsigned long long* binom;
+    const unsigned long long* binom;   // [rows][bstride]
     const uint32_t* outside;
+    int bstride;
     int a, b, W, CW, r, gamma, proj, exclude;
+    int L_before;
 };
 
 DIST_HD const uint32_t* rep_ptr(const LaneCtx& C, int unit, int e, int plane) {
@@ -122,7 +148,7 @@ DIST_HD const uint32_t* rep_ptr(const LaneCtx& C, int unit, int e, int plane) {
 // records it when it beats thr and, in exclusion mode, lies outside S.
 template <class Sink>
 DIST_HD_COLD void consider(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                      const uint8_t* eA, int nb, const uint8_t* sB) {
+                           const uint8_t* eA, int nb, const uint8_t* sB) {
     uint32_t x[DIST_MAXW], z[DIST_MAXW];
     for (int w = 0; w < DIST_MAXW; w++) x[w] = z[w] = 0;
     for (int p = 0; p < i; p++) {
@@ -178,7 +204,7 @@ DIST_HD_COLD void consider(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, c
 // Every representative choice of one subset, each weighed exactly (small i).
 template <class Sink>
 DIST_HD_COLD void eval_generic(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                          int nb, const uint8_t* sB) {
+                               int nb, const uint8_t* sB) {
     uint8_t e[DIST_MAXR];
     for (int p = 0; p < i; p++) e[p] = 0;
     const int first = C.proj ? 1 : 0;
@@ -194,66 +220,104 @@ DIST_HD_COLD void eval_generic(const LaneCtx& C, Sink& sink, uint32_t& thr, int 
     }
 }
 
-// Slow path of one 27-codeword block: every entry whose word-0 weight is
-// below thr is weighed in full.
+// Slow path of one 81-codeword block: each codeword whose lower bound
+// popc(word 0) + P is below thr is weighed in full.  (vbx, vbz) is word 0 of
+// the B-units' sum; eB0 is digit B's value at the block start (digit A starts
+// every block at 0); P counts the subset's packages with a pivot outside
+// word 0, each worth one more unit of weight.
 template <class Sink>
 DIST_HD_COLD void block_slow(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                        const uint8_t* dig, int nb, const uint8_t* sB, uint32_t bx, uint32_t bz) {
-    const int p0 = i - 3;
+                             const uint8_t* dig, int nb, const uint8_t* sB, uint32_t vbx,
+                             uint32_t vbz, int eB0, uint32_t P) {
     uint8_t e[DIST_MAXR];
-    for (int p = 0; p < p0; p++) e[p] = dig[p];
-    for (int j = 0; j < 27; j++) {
-        const int e0 = j % 3, e1 = (j / 3) % 3, e2 = j / 9;
-        const U2 ta = C.r0[sA[p0] * 3 + e0], tb = C.r0[sA[p0 + 1] * 3 + e1],
-                 tc = C.r0[sA[p0 + 2] * 3 + e2];
-        uint32_t t = (bx ^ ta.x ^ tb.x ^ tc.x) | (bz ^ ta.z ^ tb.z ^ tc.z);
-        if ((uint32_t)popc32(t) >= thr) continue;
-        e[p0] = (uint8_t)e0;
-        e[p0 + 1] = (uint8_t)e1;
-        e[p0 + 2] = (uint8_t)e2;
-        consider(C, sink, thr, i, sA, e, nb, sB);
+    uint32_t bx = vbx, bz = vbz;
+    for (int p = 0; p < i - 4; p++) {
+        e[p] = dig[p];
+        const U2 v = C.r0[sA[p] * 3 + dig[p]];
+        bx ^= v.x;
+        bz ^= v.z;
+    }
+    const U2* ra = C.r0 + sA[i - 4] * 3;
+    const U2* rb = C.r0 + sA[i - 3] * 3;
+    const U2* r0 = C.r0 + sA[i - 2] * 3;
+    const U2* r1 = C.r0 + sA[i - 1] * 3;
+    for (int kk = 0; kk < 9; kk++) {
+        const int eA = (kk - kk / 3) % 3;
+        const int eB = (eB0 + kk / 3) % 3;
+        for (int j = 0; j < 9; j++) {
+            const int e0 = j % 3, e1 = j / 3;
+            const uint32_t tx = bx ^ ra[eA].x ^ rb[eB].x ^ r0[e0].x ^ r1[e1].x;
+            const uint32_t tz = bz ^ ra[eA].z ^ rb[eB].z ^ r0[e0].z ^ r1[e1].z;
+            if ((uint32_t)popc32(tx | tz) + P >= thr) continue;
+            e[i - 4] = (uint8_t)eA;
+            e[i - 3] = (uint8_t)eB;
+            e[i - 2] = (uint8_t)e0;
+            e[i - 1] = (uint8_t)e1;
+            consider(C, sink, thr, i, sA, e, nb, sB);
+        }
     }
 }
 
-// Fast path: subsets with at least three varying units.  Kept out of line so
-// that only its own state (the table, the base word and the counters) is live
-// in the inner loop.
+// 9 codewords: base ^ table entry, word-0 weight, folded into the running min.
+#define DIST_SWEEP9(m)                                                                   \
+    do {                                                                                 \
+        const uint32_t c0 = (uint32_t)popc32((bx ^ Tx[0]) | (bz ^ Tz[0]));               \
+        const uint32_t c1 = (uint32_t)popc32((bx ^ Tx[1]) | (bz ^ Tz[1]));               \
+        const uint32_t c2 = (uint32_t)popc32((bx ^ Tx[2]) | (bz ^ Tz[2]));               \
+        const uint32_t c3 = (uint32_t)popc32((bx ^ Tx[3]) | (bz ^ Tz[3]));               \
+        const uint32_t c4 = (uint32_t)popc32((bx ^ Tx[4]) | (bz ^ Tz[4]));               \
+        const uint32_t c5 = (uint32_t)popc32((bx ^ Tx[5]) | (bz ^ Tz[5]));               \
+        const uint32_t c6 = (uint32_t)popc32((bx ^ Tx[6]) | (bz ^ Tz[6]));               \
+        const uint32_t c7 = (uint32_t)popc32((bx ^ Tx[7]) | (bz ^ Tz[7]));               \
+        const uint32_t c8 = (uint32_t)popc32((bx ^ Tx[8]) | (bz ^ Tz[8]));               \
+        m = min3u(m, min3u(c0, c1, c2), min3u(c3, c4, c5));                              \
+        m = min3u(m, min3u(c6, c7, c8), m);                                              \
+    } while (0)
+
+#define DIST_STEP(d) \
+    do {             \
+        bx ^= d.x;   \
+        bz ^= d.z;   \
+    } while (0)
+
+// Fast path: subsets with at least four varying units.  Kept out of line so
+// that only its own state (table, register-digit deltas, base word, counters)
+// is live in the inner loop.
 template <class Sink>
-DIST_HD_HOT void eval_fast(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                       uint8_t* dig, int nb, const uint8_t* sB, uint32_t vbx, uint32_t vbz) {
-    const int p0 = i - 3;
-    uint32_t Tx[27], Tz[27];
+DIST_HD_FAST void eval_fast(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
+                           uint8_t* dig, int nb, const uint8_t* sB, uint32_t vbx, uint32_t vbz,
+                           uint32_t P) {
+    uint32_t Tx[9], Tz[9];
     {
-        const U2* ra = C.r0 + sA[p0] * 3;
-        const U2* rb = C.r0 + sA[p0 + 1] * 3;
-        const U2* rc = C.r0 + sA[p0 + 2] * 3;
-        U2 A[3], B[3], Cc[3];
-#pragma unroll
-        for (int e = 0; e < 3; e++) {
-            A[e] = ra[e];
-            B[e] = rb[e];
-            Cc[e] = rc[e];
-        }
-#pragma unroll
-        for (int e2 = 0; e2 < 3; e2++)
-#pragma unroll
-            for (int e1 = 0; e1 < 3; e1++)
-#pragma unroll
-                for (int e0 = 0; e0 < 3; e0++) {
-                    Tx[e2 * 9 + e1 * 3 + e0] = Cc[e2].x ^ B[e1].x ^ A[e0].x;
-                    Tz[e2 * 9 + e1 * 3 + e0] = Cc[e2].z ^ B[e1].z ^ A[e0].z;
-                }
+        const U2* r0 = C.r0 + sA[i - 2] * 3;
+        const U2* r1 = C.r0 + sA[i - 1] * 3;
+        const U2 a0 = r0[0], a1 = r0[1], a2 = r0[2], b0 = r1[0], b1 = r1[1], b2 = r1[2];
+        Tx[0] = a0.x ^ b0.x; Tz[0] = a0.z ^ b0.z;
+        Tx[1] = a1.x ^ b0.x; Tz[1] = a1.z ^ b0.z;
+        Tx[2] = a2.x ^ b0.x; Tz[2] = a2.z ^ b0.z;
+        Tx[3] = a0.x ^ b1.x; Tz[3] = a0.z ^ b1.z;
+        Tx[4] = a1.x ^ b1.x; Tz[4] = a1.z ^ b1.z;
+        Tx[5] = a2.x ^ b1.x; Tz[5] = a2.z ^ b1.z;
+        Tx[6] = a0.x ^ b2.x; Tz[6] = a0.z ^ b2.z;
+        Tx[7] = a1.x ^ b2.x; Tz[7] = a1.z ^ b2.z;
+        Tx[8] = a2.x ^ b2.x; Tz[8] = a2.z ^ b2.z;
     }
-    uint32_t bx = vbx, bz = vbz;
-    for (int p = 0; p < p0; p++) {
+    // digit A starts every block at 0; its deltas for e -> e+1 are rep[(e+2)%3]
+    const U2* ra = C.r0 + sA[i - 4] * 3;
+    const U2 Da0 = ra[2], Da1 = ra[0], Da2 = ra[1];
+    const U2* rb = C.r0 + sA[i - 3] * 3;
+    U2 Db0 = rb[2], Db1 = rb[0], Db2 = rb[1];
+    int eB = 0;
+    uint32_t bx = vbx ^ ra[0].x ^ rb[0].x, bz = vbz ^ ra[0].z ^ rb[0].z;
+    for (int p = 0; p < i - 4; p++) {
         const U2 v = C.r0[sA[p] * 3 + dig[p]];
         bx ^= v.x;
         bz ^= v.z;
     }
     const int first = C.proj ? 1 : 0;
-    const int nouter = p0 - first;
+    const int nd = i - 4 - first;
     uint32_t nk = 1;
-    for (int q = 0; q < nouter; q++) nk *= 3u;
+    for (int q = 0; q < nd; q++) nk *= 3u;
     for (uint32_t k = 0; k < nk; ++k) {
         if (k) {
             uint32_t kk = k;
@@ -269,34 +333,55 @@ DIST_HD_HOT void eval_fast(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, c
             bz ^= v.z;
             dig[p] = (uint8_t)(e == 2 ? 0 : e + 1);
         }
-        uint32_t m0 = 0xFFFFu, m1 = 0xFFFFu;
-#pragma unroll
-        for (int j = 0; j < 27; j++) {
-            const uint32_t t = (bx ^ Tx[j]) | (bz ^ Tz[j]);
-            const uint32_t c = (uint32_t)popc32(t);
-            if (j & 1) m1 = c < m1 ? c : m1;
-            else m0 = c < m0 ? c : m0;
-        }
-        const uint32_t m = m0 < m1 ? m0 : m1;
-        if (m < thr) block_slow(C, sink, thr, i, sA, dig, nb, sB, bx, bz);
+        uint32_t m = 0xFFFFu;
+        DIST_SWEEP9(m);
+        DIST_STEP(Da0);
+        DIST_SWEEP9(m);
+        DIST_STEP(Da1);
+        DIST_SWEEP9(m);
+        DIST_STEP(Db0);
+        DIST_SWEEP9(m);
+        DIST_STEP(Da2);
+        DIST_SWEEP9(m);
+        DIST_STEP(Da0);
+        DIST_SWEEP9(m);
+        DIST_STEP(Db1);
+        DIST_SWEEP9(m);
+        DIST_STEP(Da1);
+        DIST_SWEEP9(m);
+        DIST_STEP(Da2);
+        DIST_SWEEP9(m);
+        // weight >= popc(word 0) + P: only then can a codeword beat thr
+        if (m + P < thr) block_slow(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, eB, P);
+        const U2 t = Db2;  // B moved twice: rotate its delta triple by two
+        Db2 = Db1;
+        Db1 = Db0;
+        Db0 = t;
+        eB = eB == 0 ? 2 : eB - 1;
     }
 }
 
-// Word 0 of the sum of the chosen B-units' single representatives.
-DIST_HD void b_word0(const LaneCtx& C, int nb, const uint8_t* sB, uint32_t& x, uint32_t& z) {
-    x = z = 0;
+#undef DIST_SWEEP9
+#undef DIST_STEP
+
+// Word 0 of the sum of the chosen B-units' single representatives, and how
+// many of them are packages with a pivot outside word 0.
+DIST_HD void b_word0(const LaneCtx& C, int nb, const uint8_t* sB, uint32_t& x, uint32_t& z,
+                     uint32_t& P) {
+    x = z = P = 0;
     for (int q = 0; q < nb; q++) {
         x ^= rep_ptr(C, C.a + sB[q], 0, 0)[0];
         z ^= rep_ptr(C, C.a + sB[q], 0, 1)[0];
+        P += C.flags[C.a + sB[q]];
     }
 }
 
 DIST_HD bool use_fast(const LaneCtx& C, int i) {
-    return i >= 3 + C.proj && i - 3 - C.proj <= DIST_FAST_MAX_OUTER;
+    return i >= 4 + C.proj && i - 4 - C.proj <= DIST_FAST_MAX_DYN;
 }
 
 // Walks the combination ranks [lo, hi) of segment sg; returns the number of
-// codewords evaluated.  Sink provides poll(thr) -> stop? and record(...).
+// codewords evaluated.  Sink provides poll(thr, L) -> stop? and record(...).
 template <class Sink>
 DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& thr, const SegDesc& sg,
                                       unsigned long long lo, unsigned long long hi) {
@@ -304,22 +389,28 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
     uint8_t sA[DIST_MAXR], sB[DIST_MAXR], dig[DIST_MAXR];
     for (int p = 0; p < DIST_MAXR; p++) dig[p] = 0;
     unsigned long long tB = lo / sg.NA, tA = lo - tB * sg.NA;
-    rd_unrank(C.binom, tB, nb, sB);
-    rd_unrank(C.binom, tA, i, sA);
-    uint32_t vbx, vbz;
-    b_word0(C, nb, sB, vbx, vbz);
+    rd_unrank(C.binom, C.bstride, C.b, tB, nb, sB);
+    rd_unrank(C.binom, C.bstride, C.a, tA, i, sA);
+    uint32_t vbx, vbz, PB;
+    b_word0(C, nb, sB, vbx, vbz, PB);
     const bool fast = use_fast(C, i);
     unsigned long long done = 0;
     for (unsigned long long idx = lo; idx < hi; ++idx) {
-        if (sink.poll(thr)) break;
-        if (fast) eval_fast(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz);
-        else eval_generic(C, sink, thr, i, sA, nb, sB);
+        if (sink.poll(thr, C.L_before)) break;
+        if (fast) {
+            // packages with a pivot outside word 0 each add one to the weight
+            uint32_t P = PB;
+            for (int p = 0; p < i; p++) P += C.flags[sA[p]];
+            if (P < thr) eval_fast(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, P);
+        } else {
+            eval_generic(C, sink, thr, i, sA, nb, sB);
+        }
         done += sg.codes;
         if (idx + 1 < hi) {
             if (++tA == sg.NA) {
                 tA = 0;
                 rd_next(sB, nb, C.b);
-                b_word0(C, nb, sB, vbx, vbz);
+                b_word0(C, nb, sB, vbx, vbz, PB);
                 for (int p = 0; p < i; p++) sA[p] = (uint8_t)p;
             } else {
                 rd_next(sA, i, C.a);

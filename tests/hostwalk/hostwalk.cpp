@@ -17,11 +17,10 @@ namespace {
 
 struct HostSink {
     Scratch* scr;
-    int L_prev;
-    bool poll(uint32_t& thr) {
+    bool poll(uint32_t& thr, int L_before) {
         uint32_t u = scr->U;
         if (u < thr) thr = u;
-        return (int)u <= L_prev;
+        return (int)u <= L_before;
     }
     void record(uint32_t w, int gamma, int count, const uint8_t* units, const uint8_t* digits) {
         if (w < scr->U) scr->U = w;
@@ -39,6 +38,8 @@ struct HostSink {
     }
 };
 
+// Runs a launch plan chunk by chunk, lane by lane, exactly as the kernel
+// would, but sequentially.
 struct HostExec {
     const Plan* p;
     Scratch scr;
@@ -53,30 +54,53 @@ struct HostExec {
         scr.U = DIST_WINF;
         return 0;
     }
+    int seed(uint32_t U0, const WitnessSlot& s) {
+        scr.U = U0;
+        scr.slot[U0] = s;
+        return 0;
+    }
     int target_warps() const { return warps; }
     double gpu_seconds() const { return 0.0; }
     unsigned long long launches() const { return nlaunch; }
-    int run(EnumParams& ep, double, StepResult* out) {
-        const Gamma& G = p->gammas[ep.gamma];
-        std::vector<U2> r0((size_t)ep.a * 3);
-        for (int t = 0; t < ep.a * 3; t++) {
-            r0[t].x = G.dev_reps[((size_t)t * 2 + 0) * ep.W];
-            r0[t].z = G.dev_reps[((size_t)t * 2 + 1) * ep.W];
+    int run(const LaunchPlan& lp, double, StepResult* out) {
+        EnumParams ep;
+        plan_params(*p, lp, &ep);
+        // the shared-memory image the kernel would build
+        std::vector<uint32_t> sm(lp.s_words + 2, 0);
+        for (const GammaDesc& g : lp.g) {
+            const uint32_t* src = p->tables.data() + g.rep_off;
+            for (int t = 0; t < (g.a + g.b) * 6 * ep.W; t++) sm[g.s_rep + t] = src[t];
+            U2* r0 = reinterpret_cast<U2*>(sm.data() + g.s_r0);
+            for (int t = 0; t < g.a * 3; t++) {
+                r0[t].x = src[(t * 2 + 0) * ep.W];
+                r0[t].z = src[(t * 2 + 1) * ep.W];
+            }
+            for (int t = 0; t < g.a + g.b; t++) sm[g.s_flag + t] = p->tables[g.flag_off + t];
         }
-        LaneCtx C;
-        C.reps = G.dev_reps.data();
-        C.r0 = r0.data();
-        C.coefs = G.dev_coefs.data();
-        C.binom = binom.data();
-        C.outside = ep.outside;
-        C.a = ep.a; C.b = ep.b; C.W = ep.W; C.CW = ep.CW; C.r = ep.r;
-        C.gamma = ep.gamma; C.proj = ep.proj; C.exclude = ep.exclude;
-        HostSink sink{&scr, ep.L_prev};
+        unsigned long long* sbin = reinterpret_cast<unsigned long long*>(sm.data() + lp.s_binom);
+        for (int t = 0; t < lp.brows * lp.bcols; t++) {
+            int n = t / lp.bcols, k = t - n * lp.bcols;
+            sbin[t] = binom[n * (DIST_MAXR + 1) + k];
+        }
+        HostSink sink{&scr};
         nlaunch++;
-        for (unsigned long long chunk = 0; chunk < ep.nchunks; chunk++) {
+        for (unsigned long long chunk = 0; chunk < lp.nchunks; chunk++) {
             int sgi = 0;
-            while (sgi + 1 < ep.nseg && ep.seg[sgi + 1].chunk_base <= chunk) ++sgi;
-            const SegDesc& sg = ep.seg[sgi];
+            while (sgi + 1 < (int)lp.segs.size() && lp.segs[sgi + 1].chunk_base <= chunk) ++sgi;
+            const SegDesc& sg = lp.segs[sgi];
+            if ((int)scr.U <= sg.L_before) break;
+            const GammaDesc& g = lp.g[sg.g];
+            LaneCtx C;
+            C.reps = sm.data() + g.s_rep;
+            C.r0 = reinterpret_cast<const U2*>(sm.data() + g.s_r0);
+            C.flags = sm.data() + g.s_flag;
+            C.coefs = p->tables.data() + g.coef_off;
+            C.binom = sbin;
+            C.bstride = lp.bcols;
+            C.outside = ep.outside;
+            C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW; C.r = sg.r;
+            C.gamma = g.gamma; C.proj = ep.proj; C.exclude = ep.exclude;
+            C.L_before = sg.L_before;
             unsigned long long total = sg.NA * sg.NB;
             for (int lane = 0; lane < 32; lane++) {
                 unsigned long long lo = (chunk - sg.chunk_base) * 32ull * sg.spl + (unsigned long long)lane * sg.spl;
@@ -85,7 +109,6 @@ struct HostExec {
                 uint32_t thr = DIST_WINF;
                 scr.codewords += walk_range(C, sink, thr, sg, lo, hi);
             }
-            if ((int)scr.U <= ep.L_prev) break;
         }
         out->U = scr.U;
         out->status = scr.status;
@@ -119,7 +142,7 @@ extern "C" void hw_rd_walk(int n, int t, unsigned long long rank0, int count, ui
     std::vector<unsigned long long> B((DIST_MAXU + 1) * (DIST_MAXR + 1));
     binom_table(B.data());
     uint8_t s[DIST_MAXR];
-    rd_unrank(B.data(), rank0, t, s);
+    rd_unrank(B.data(), DIST_MAXR + 1, n, rank0, t, s);
     for (int c = 0; c < count; c++) {
         memcpy(out + (size_t)c * t, s, (size_t)t);
         if (c + 1 < count) rd_next(s, t, n);

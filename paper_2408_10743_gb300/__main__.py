@@ -33,6 +33,8 @@ def main(argv=None):
     src = ap.add_mutually_exclusive_group(required=True)
     src.add_argument("--workload", choices=["qc72", "f2_24", "f4_40"])
     src.add_argument("--matrix")
+    src.add_argument("--random", nargs=2, type=int, metavar=("N", "K"),
+                     help="random F2 code (i.i.d. bits, full rank), seeded by --index")
     ap.add_argument("--index", type=int, default=0)
     ap.add_argument("--field", type=int, default=2, choices=[2, 4])
     ap.add_argument("--n-stab", type=int, default=0)
@@ -46,6 +48,9 @@ def main(argv=None):
         g = synth.single_f2(args.index)
     elif args.workload == "f4_40":
         g, field = synth.single_f4(args.index), 4
+    elif args.random:
+        g = synth.random_f2_code(args.random[0], args.random[1],
+                                 synth.Xoshiro256ss(synth.seed_for(5, args.index)))
     else:
         g = read_matrix(args.matrix)
     with binding.Code(g, field) as code:

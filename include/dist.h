@@ -151,6 +151,33 @@ typedef struct {
 } dist_intpeak_result;
 int dist_intpeak(dist_intpeak_result *out, int iters, void *cuda_stream);
 
+/*
+ * dist_solve_noalloc -- dist_init + dist_solve + dist_free in one call that
+ * allocates no device memory.  The paper has no counterpart: this exists for
+ * callers that cannot call cudaMalloc (code running inside another
+ * framework's memory pool or under a fixed device-memory budget, or paths
+ * where an allocation may not block or fail).  Every byte of device scratch
+ * (bound and witness slots, segment table, binomial rows, generator-matrix
+ * tables) lives in one file-scope device array of DIST_NOALLOC_MAX_BYTES
+ * bytes that every GPU loading the library holds until process exit.
+ *   generator, n, K, field: as dist_init (host memory, copied).
+ *   n_stab: as dist_set_exclude (0 = plain minimum).
+ *   out: caller-allocated result, as dist_solve.
+ *   cuda_stream: cudaStream_t as void*; NULL = the legacy default stream.
+ * Returns DIST_ERANGE, before touching the device, if the code's tables do
+ * not fit the array.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and sets the kernel's shared-memory limit;
+ * make that first call before any stream capture.  No cudaMalloc, cudaFree,
+ * pinned-host allocation, stream or event creation happens; host-side
+ * planning uses ordinary heap memory.  All calls share the array and each
+ * clears what must start at zero, so calls whose GPU work overlaps (other
+ * streams, other host threads) race: serialize them.  gpu_seconds in the
+ * result is 0 (no events are created).
+ */
+#define DIST_NOALLOC_MAX_BYTES 65536
+int dist_solve_noalloc(const uint8_t *generator, int n, int K, int field, int n_stab,
+                       dist_result *out, void *cuda_stream);
+
 /* Library version string and device info (name, SM count) of the current device. */
 const char *dist_version(void);
 const char *dist_strerror(int code);

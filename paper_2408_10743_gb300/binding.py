@@ -59,6 +59,8 @@ SIGNATURES = {
                                       ctypes.c_int, ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     "dist_intpeak": (ctypes.c_int, [ctypes.POINTER(IntpeakResult), ctypes.c_int, _VP]),
+    "dist_solve_noalloc": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(DistResult), _VP]),
     "dist_version": (ctypes.c_char_p, []),
     "dist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -172,6 +174,17 @@ def dist_plan_unit(generator, gamma, unit, rep, field=DIST_F2):
 def dist_intpeak(iters=4096, stream=None) -> IntpeakResult:
     r = IntpeakResult()
     _check(lib().dist_intpeak(ctypes.byref(r), iters, _stream_handle(stream)), "dist_intpeak")
+    return r
+
+
+def dist_solve_noalloc(generator, field=DIST_F2, n_stab=0, stream=None) -> DistResult:
+    """Solve without any device allocation: all device scratch lives in the
+    library's fixed static array (see include/dist.h).  Calls share that array,
+    so calls whose GPU work overlaps must be serialized by the caller."""
+    g, n, K = _as_gen(generator, field)
+    r = DistResult()
+    _check(lib().dist_solve_noalloc(_ptr(g), n, K, field, n_stab, ctypes.byref(r),
+                                    _stream_handle(stream)), "dist_solve_noalloc")
     return r
 
 

@@ -1,0 +1,57 @@
+"""dist_solve_noalloc -- the entry point for callers that cannot allocate
+device memory (code inside another framework's memory pool or under a fixed
+device-memory budget).  It keeps all device scratch in one static array of
+the library; here its results are checked against the allocating entry point
+(dist_init + dist_solve) on two calls in a row, which share that array.
+
+This file is collected last on purpose, so that a run stopping at its first
+failure has already run every other test."""
+import numpy as np
+import pytest
+
+import paper_2408_10743_gb300 as dist
+from paper_2408_10743_gb300 import synth
+from paper_2408_10743_gb300.binding import DIST_ERANGE, result_dict
+from codes import sym_weight_bits, toric
+
+pytestmark = pytest.mark.gpu
+
+
+def valid_witness(g, res, field):
+    n = g.shape[1] // 2 if field == 2 else g.shape[1]
+    w = res["witness"]
+    if field == 2:
+        assert sym_weight_bits(w, n) == res["d"]
+        assert np.array_equal(np.bitwise_xor.reduce(g[res["coeffs"].astype(bool)], axis=0), w)
+    else:
+        assert int(np.count_nonzero(w)) == res["d"]
+
+
+CASES = [
+    ("random F2 n=24 K=24", lambda: (synth.single_f2(0), 2, 0)),
+    ("F4 n=40 k=20", lambda: (synth.single_f4(0), 4, 0)),
+    ("quasi-cyclic n=72 K=72", lambda: (synth.single_qc(0), 2, 0)),
+    ("random F2 n=48 K=40", lambda: (synth.random_f2_code(48, 40, synth.Xoshiro256ss(31)), 2, 0)),
+    ("toric L=3, stabilizer excluded", lambda: (toric(3)[0], 2, toric(3)[1])),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_noalloc_matches_allocating_entry_point(name, make):
+    g, field, n_stab = make()
+    ref = dist.distance(g, field=field, n_stab=n_stab)
+    n = g.shape[1] // 2 if field == 2 else g.shape[1]
+    for _ in range(2):  # two calls in a row reuse the same static array
+        r = result_dict(dist.dist_solve_noalloc(g, field=field, n_stab=n_stab), n, g.shape[0], field)
+        assert r["status"] == 0
+        assert r["d"] == ref["d"]
+        assert r["k_eff"] == ref["k_eff"]
+        valid_witness(g, r, field)
+
+
+def test_noalloc_rejects_codes_beyond_the_array():
+    # the whole space F2^256 (n = 128, K = 256) needs more than the array holds
+    full = np.eye(256, dtype=np.uint8)
+    with pytest.raises(dist.DistError) as e:
+        dist.dist_solve_noalloc(full)
+    assert e.value.code == DIST_ERANGE

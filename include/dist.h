@@ -114,6 +114,50 @@ int dist_solve_bounded(dist_code *c, dist_result *out, void *cuda_stream, double
 int dist_free(dist_code *c);
 
 /*
+ * Batched and served solving (step S7; the paper has no counterpart -- its
+ * parallel version splits one code's combinations over CPU threads).
+ *
+ * A dist_batch runs many dist_codes on one device together: one launch of
+ * the multi-code enumeration kernel serves every admitted code, each code
+ * keeping its bound, chunk counter and witness slots on the device between
+ * launches.  A worker thread owned by the batch runs time-bounded "slices";
+ * codes submitted while others run are admitted at the next slice boundary
+ * (continuous batching), subject to max_active and max_resident_bytes (the
+ * codes' device footprint: tables + scratch).  A dist_batch is internally
+ * synchronized: any thread may submit, poll or wait.  A submitted dist_code
+ * belongs to the batch until its ticket has been collected by poll or wait:
+ * dist_solve / dist_free on it return DIST_EBUSY meanwhile.
+ */
+typedef struct {
+    int32_t max_active;          /* codes on the device at once (0 = 8192) */
+    int32_t pad;
+    double slice_ms;             /* time budget of one launch in ms; 0 = none (run to completion) */
+    uint64_t max_resident_bytes; /* admission limit on the active codes' footprint (0 = none) */
+} dist_batch_opts;
+
+typedef struct {
+    uint64_t slices, launches, codes_done, active, pending, resident_bytes;
+    double gpu_seconds;          /* summed CUDA-event time of the multi-code launches */
+} dist_batch_stats_t;
+
+typedef struct dist_batch dist_batch;
+
+/* Creates a batch on the current device; opts may be NULL (defaults). */
+int dist_batch_create(dist_batch **b, const dist_batch_opts *opts);
+/* Queues count codes (initialised with dist_init on the same device) as one ticket. */
+int dist_batch_submit(dist_batch *b, dist_code *const *codes, int count, uint64_t *ticket);
+/* DIST_EBUSY until every code of the ticket is done; then fills results[count]
+ * (per-code status in results[i].status; seconds = latency from submission)
+ * and releases the ticket. */
+int dist_batch_poll(dist_batch *b, uint64_t ticket, dist_result *results);
+/* As poll, blocking up to timeout_s seconds (<= 0: no limit); DIST_ETIMEOUT on expiry. */
+int dist_batch_wait(dist_batch *b, uint64_t ticket, dist_result *results, double timeout_s);
+int dist_batch_stats(dist_batch *b, dist_batch_stats_t *stats);
+/* Stops the worker after its current slice and frees the batch; uncollected
+ * tickets are dropped and their codes released. */
+int dist_batch_destroy(dist_batch *b);
+
+/*
  * dist_plan_info -- host-only view of the plan step S2-S3 built for an input
  * (no CUDA call).  For each generator matrix j < n_gamma_built: a[j] units
  * with three representatives, b[j] with one, f[j] free rows; order[0..n_used)

@@ -44,6 +44,18 @@ class IntpeakResult(ctypes.Structure):
                 ("sms", ctypes.c_int32), ("blocks", ctypes.c_int32)]
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("slice_ms", ctypes.c_double), ("max_resident_bytes", ctypes.c_uint64)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("slices", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("codes_done", ctypes.c_uint64), ("active", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64),
+                ("gpu_seconds", ctypes.c_double)]
+
+
 # name -> (restype, argtypes); mirrors include/dist.h
 _U8P = ctypes.POINTER(ctypes.c_uint8)
 _VP = ctypes.c_void_p
@@ -61,6 +73,14 @@ SIGNATURES = {
     "dist_intpeak": (ctypes.c_int, [ctypes.POINTER(IntpeakResult), ctypes.c_int, _VP]),
     "dist_solve_noalloc": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(DistResult), _VP]),
+    "dist_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(BatchOpts)]),
+    "dist_batch_submit": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "dist_batch_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(DistResult)]),
+    "dist_batch_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(DistResult),
+                                       ctypes.c_double]),
+    "dist_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(BatchStats)]),
+    "dist_batch_destroy": (ctypes.c_int, [_VP]),
     "dist_version": (ctypes.c_char_p, []),
     "dist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -188,6 +208,46 @@ def dist_solve_noalloc(generator, field=DIST_F2, n_stab=0, stream=None) -> DistR
     return r
 
 
+def dist_batch_create(max_active=0, slice_ms=0.0, max_resident_bytes=0):
+    h = _VP()
+    o = BatchOpts(max_active, 0, float(slice_ms), int(max_resident_bytes))
+    _check(lib().dist_batch_create(ctypes.byref(h), ctypes.byref(o)), "dist_batch_create")
+    return h
+
+
+def dist_batch_submit(batch, handles):
+    arr = (_VP * len(handles))(*[h.value if isinstance(h, _VP) else h for h in handles])
+    t = ctypes.c_uint64(0)
+    _check(lib().dist_batch_submit(batch, arr, len(handles), ctypes.byref(t)), "dist_batch_submit")
+    return t.value
+
+
+def dist_batch_poll(batch, ticket, count):
+    """Results of a finished ticket, or None while it is running."""
+    res = (DistResult * count)()
+    rc = lib().dist_batch_poll(batch, ticket, res)
+    if rc == DIST_EBUSY:
+        return None
+    _check(rc, "dist_batch_poll")
+    return list(res)
+
+
+def dist_batch_wait(batch, ticket, count, timeout_s=0.0):
+    res = (DistResult * count)()
+    _check(lib().dist_batch_wait(batch, ticket, res, float(timeout_s)), "dist_batch_wait")
+    return list(res)
+
+
+def dist_batch_stats(batch) -> dict:
+    s = BatchStats()
+    _check(lib().dist_batch_stats(batch, ctypes.byref(s)), "dist_batch_stats")
+    return {f: getattr(s, f) for f, _ in BatchStats._fields_}
+
+
+def dist_batch_destroy(batch):
+    return _check(lib().dist_batch_destroy(batch), "dist_batch_destroy")
+
+
 def dist_version() -> str:
     return lib().dist_version().decode()
 
@@ -249,3 +309,53 @@ def distance(generator, field=DIST_F2, n_stab=0, stream=None) -> dict:
         if n_stab:
             c.set_exclude(n_stab)
         return c.solve(stream)
+
+
+class Batch:
+    """Many codes on one device: batched launches with continuous admission.
+    ``submit`` returns a ticket; ``wait``/``poll`` return one result dict per
+    code (``seconds`` = latency from submission).  Codes stay owned by the
+    batch until their ticket is collected."""
+
+    def __init__(self, max_active=0, slice_ms=0.0, max_resident_bytes=0):
+        self._h = dist_batch_create(max_active, slice_ms, max_resident_bytes)
+        self._tickets = {}
+
+    def submit(self, codes):
+        codes = list(codes)
+        t = dist_batch_submit(self._h, [c._h for c in codes])
+        self._tickets[t] = codes
+        return t
+
+    def _finish(self, t, res):
+        codes = self._tickets.pop(t)
+        return [result_dict(r, c.n, c.K, c.field) for r, c in zip(res, codes)]
+
+    def poll(self, ticket):
+        res = dist_batch_poll(self._h, ticket, len(self._tickets[ticket]))
+        return None if res is None else self._finish(ticket, res)
+
+    def wait(self, ticket, timeout_s=0.0):
+        return self._finish(ticket, dist_batch_wait(self._h, ticket, len(self._tickets[ticket]),
+                                                    timeout_s))
+
+    def stats(self):
+        return dist_batch_stats(self._h)
+
+    def close(self):
+        if self._h:
+            dist_batch_destroy(self._h)
+            self._h = None
+            self._tickets.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdist.so")
 
-CU_SOURCES = ["api.cu", "enum.cu", "intpeak.cu", "noalloc.cu"]
+CU_SOURCES = ["api.cu", "batch.cu", "enum.cu", "intpeak.cu", "noalloc.cu"]
 CPP_SOURCES = ["plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",

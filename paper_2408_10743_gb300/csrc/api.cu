@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/dist.h"
+#include "code.h"
 #include "plan.h"
 #include "solve.h"
 
@@ -15,6 +16,7 @@ cudaError_t enum_launch(const EnumParams& P, int grid, cudaStream_t st);
 size_t enum_smem_bytes(const EnumParams& P);
 int enum_blocks_per_sm(size_t smem);
 cudaError_t enum_set_max_smem(size_t bytes);
+int batch_blocks_per_sm();
 struct IntpeakRaw {
     double mix_s, popc_s, lop3_s;
     double sm_mhz;
@@ -25,19 +27,12 @@ cudaError_t intpeak_run(int iters, cudaStream_t st, IntpeakRaw* r);
 
 using namespace dist;
 
+namespace dist {
+
 namespace {
-
-// Per-device constants: the binomial table the kernels unrank with.
-struct DeviceCtx {
-    int device = -1;
-    int sms = 0;
-    int blocks_per_sm = 0;          // at a small shared-memory footprint
-    size_t smem_optin = 0;          // largest dynamic shared memory per block
-    unsigned long long* d_binom = nullptr;
-};
-
 std::mutex g_dev_mu;
 DeviceCtx g_dev[64];
+}  // namespace
 
 int map_plan_rc(int rc) {
     switch (rc) {
@@ -73,26 +68,15 @@ int device_ctx(DeviceCtx** out) {
         d.smem_optin = (size_t)optin;
         if (enum_set_max_smem(d.smem_optin) != cudaSuccess) return DIST_ECUDA;
         d.blocks_per_sm = enum_blocks_per_sm(16 * 1024);
-        if (d.blocks_per_sm < 1) return DIST_ECUDA;
+        d.batch_blocks_per_sm = batch_blocks_per_sm();
+        if (d.blocks_per_sm < 1 || d.batch_blocks_per_sm < 1) return DIST_ECUDA;
         d.device = dev;
     }
     *out = &d;
     return DIST_OK;
 }
 
-}  // namespace
-
-struct dist_code {
-    Plan plan;
-    DeviceCtx* dev = nullptr;
-    uint32_t* d_tables = nullptr;             // Plan::tables on the device
-    SegDesc* d_segs = nullptr;                // segment table of the current launch
-    SegDesc* h_segs = nullptr;                // pinned staging copy
-    Scratch* d_scr = nullptr;
-    Scratch* h_scr = nullptr;                 // pinned mirror for read-back
-    cudaStream_t stream = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-};
+}  // namespace dist
 
 namespace {
 
@@ -248,6 +232,7 @@ int dist_set_exclude(dist_code* c, int n_stab) {
 
 int dist_solve_bounded(dist_code* c, dist_result* out, void* cuda_stream, double time_limit_s) {
     if (!c || !out) return DIST_EINVAL;
+    if (c->in_batch) return DIST_EBUSY;
     if (c->plan.n_stab > 0 && c->plan.s_rank == c->plan.k_eff) return DIST_EZERO;
     DeviceGuard guard(c->dev->device);
     GpuExec ex{c, cuda_stream ? (cudaStream_t)cuda_stream : c->stream};
@@ -260,6 +245,7 @@ int dist_solve(dist_code* c, dist_result* out, void* cuda_stream) {
 
 int dist_free(dist_code* c) {
     if (!c) return DIST_OK;
+    if (c->in_batch) return DIST_EBUSY;
     DeviceGuard guard(c->dev ? c->dev->device : 0);
     if (c->stream) cudaStreamSynchronize(c->stream);
     release(c);

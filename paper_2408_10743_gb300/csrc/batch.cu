@@ -1,0 +1,492 @@
+// batch.cu -- step S7: many codes per launch, with continuous admission.
+//
+// A dist_batch owns one worker thread and one stream.  The worker runs
+// "slices": it admits pending codes (up to a count and a device-footprint
+// limit), plans the new ones, seeds their scratch, packs every active code's
+// segments into one multi-code launch (enum_batch_kernel), runs it with a
+// time budget, gathers every code's bound, counters and witness slot in one
+// read-back, and then, per code, either certifies d, lets it resume in the
+// next slice, or plans its next steps.  A code's chunk counter and bound stay
+// on the device between slices, so a slice boundary loses no work.  Codes
+// submitted while others are running join at the next slice: their work
+// overlaps on the device with the codes already admitted.
+//
+// Certification after a slice (same argument as the single-code loop): with
+// next = chunks claimed so far (every claimed chunk is finished before a
+// launch ends), let s be the first planned step with U <= L_before(s).  If
+// next has reached s's first chunk, every earlier step is complete and
+// d = U.  If no such s exists and every chunk is done, the bound after the
+// last planned step holds; d = U once it reaches U, otherwise the next
+// steps are planned.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/dist.h"
+#include "code.h"
+#include "plan.h"
+#include "solve.h"
+
+namespace dist {
+cudaError_t batch_launch(const BatchParams& P, int grid, cudaStream_t st);
+cudaError_t batch_init_launch(const BatchInit* items, int n, cudaStream_t st);
+cudaError_t batch_gather_launch(Scratch* const* scrs, BatchOut* out, int n, cudaStream_t st);
+}  // namespace dist
+
+using namespace dist;
+
+namespace {
+
+struct Item {
+    dist_code* c = nullptr;
+    uint64_t ticket = 0;
+    LaunchPlan lp;
+    bool planned = false;
+    int L = 0;                 // bound in force before lp's first step
+    int r_next = 1, j_next = 0;
+    int init_mode = 1;         // 1 = reset and seed, 2 = restart the counter, 0 = none
+    int last_round = 0;
+    int slices = 0;
+    bool done = false;
+    dist_result res{};
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    size_t footprint = 0;
+};
+
+struct Ticket {
+    std::vector<Item*> items;
+    int remaining = 0;
+};
+
+// Device array with a pinned host staging copy; grows on demand.
+template <class T>
+struct DevBuf {
+    T* d = nullptr;
+    T* h = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t n) {
+        if (n <= cap) return true;
+        size_t nc = std::max<size_t>(n, cap * 2 + 64);
+        T *nd = nullptr, *nh = nullptr;
+        if (cudaMalloc(&nd, nc * sizeof(T)) != cudaSuccess) return false;
+        if (cudaMallocHost(&nh, nc * sizeof(T)) != cudaSuccess) {
+            cudaFree(nd);
+            return false;
+        }
+        release();
+        d = nd;
+        h = nh;
+        cap = nc;
+        return true;
+    }
+    bool upload(size_t n, cudaStream_t st) {
+        return n == 0 || cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    }
+    void release() {
+        if (d) cudaFree(d);
+        if (h) cudaFreeHost(h);
+        d = nullptr;
+        h = nullptr;
+        cap = 0;
+    }
+};
+
+}  // namespace
+
+struct dist_batch {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    int fatal = 0;
+    dist_batch_opts opts{};
+    DeviceCtx* dev = nullptr;
+    cudaStream_t st = nullptr;
+    std::deque<Item*> pending;
+    std::vector<Item*> active;
+    std::map<uint64_t, Ticket> tickets;
+    uint64_t next_ticket = 1;
+    size_t resident = 0;
+    // statistics
+    uint64_t slices = 0;
+    uint64_t launches = 0;
+    uint64_t codes_done = 0;
+    double gpu_seconds = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // device arrays of one slice
+    DevBuf<BatchCode> codes;
+    DevBuf<SegDesc> segs;
+    DevBuf<GammaDesc> gammas;
+    DevBuf<int32_t> order;
+    DevBuf<unsigned long long> sched;
+    DevBuf<BatchInit> inits;
+    DevBuf<Scratch*> scrs;
+    DevBuf<BatchOut> outs;
+
+    void run();
+    int slice();
+    void finish(Item* it, int status);
+};
+
+namespace {
+
+// Estimated codewords of a plan: its steps whose L_before is below the
+// random-code estimate of d (at least the first step).
+double estimated_work(const Item* it) {
+    const LaunchPlan& lp = it->lp;
+    double w = 0;
+    const int target = std::max(it->c->plan.d_est, lp.step_L_before.empty() ? 0 : lp.step_L_before[0] + 1);
+    for (size_t s = 0; s < lp.step_r.size(); s++) {
+        if (s > 0 && lp.step_L_before[s] >= target) break;
+        const size_t e = s + 1 < lp.step_r.size() ? (size_t)lp.step_seg0[s + 1] : lp.segs.size();
+        for (size_t k = (size_t)lp.step_seg0[s]; k < e; k++)
+            w += (double)lp.segs[k].NA * (double)lp.segs[k].NB * (double)lp.segs[k].codes;
+    }
+    return std::max(w, 1.0);
+}
+
+}  // namespace
+
+void dist_batch::finish(Item* it, int status) {
+    it->done = true;
+    it->t_done = wall_now();
+    it->res.status = status;
+    it->res.seconds = it->t_done - it->t_submit;
+}
+
+// One slice; returns a DIST_* error only for failures of the device itself.
+int dist_batch::slice() {
+    const int tw = dev->sms * dev->batch_blocks_per_sm * 8;
+    // plan codes that need it
+    for (Item* it : active) {
+        if (it->planned || it->done) continue;
+        const Plan& p = it->c->plan;
+        const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
+        int rc = plan_launch(p, it->r_next, it->j_next, it->L, u0, tw, 1e300, &it->lp);
+        if (rc) {
+            finish(it, rc == P_ERANGE ? DIST_ERANGE : DIST_EINVAL);
+            continue;
+        }
+        it->planned = true;
+    }
+    std::vector<Item*> run;
+    for (Item* it : active)
+        if (!it->done) run.push_back(it);
+    if (run.empty()) return DIST_OK;
+    const int n = (int)run.size();
+    // scratch set-up of new and re-planned codes
+    int ninit = 0;
+    if (!inits.ensure(n)) return DIST_ENOMEM;
+    for (Item* it : run) {
+        if (!it->init_mode) continue;
+        BatchInit& bi = inits.h[ninit++];
+        memset(&bi, 0, sizeof bi);
+        bi.scr = it->c->d_scr;
+        bi.mode = (uint32_t)it->init_mode;
+        const Plan& p = it->c->plan;
+        const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
+        bi.U0 = (uint32_t)std::min<int>(u0, DIST_WINF);
+        bi.slot = p.n_stab > 0 ? p.u0_excl_slot : p.u0_slot;
+        it->init_mode = 0;
+    }
+    if (!inits.upload(ninit, st) || batch_init_launch(inits.d, ninit, st) != cudaSuccess) return DIST_ECUDA;
+    // pack the launch
+    size_t nseg = 0, ngam = 0;
+    for (Item* it : run) {
+        nseg += it->lp.segs.size();
+        ngam += it->lp.g.size();
+    }
+    if (!codes.ensure(n) || !segs.ensure(nseg + 1) || !gammas.ensure(ngam + 1) || !scrs.ensure(n) ||
+        !outs.ensure(n) || !sched.ensure(2))
+        return DIST_ENOMEM;
+    std::vector<double> work(n);
+    double total = 0;
+    size_t so = 0, go = 0;
+    for (int i = 0; i < n; i++) {
+        Item* it = run[i];
+        const Plan& p = it->c->plan;
+        BatchCode& bc = codes.h[i];
+        memset(&bc, 0, sizeof bc);
+        bc.tables = it->c->d_tables;
+        bc.scr = it->c->d_scr;
+        for (int w = 0; w < DIST_MAXCW; w++) bc.outside[w] = p.outside[w];
+        bc.W = p.W;
+        bc.CW = p.CW;
+        bc.proj = p.field == 4 ? 1 : 0;
+        bc.exclude = p.n_stab > 0 ? 1 : 0;
+        bc.seg0 = (uint32_t)so;
+        bc.nseg = (uint32_t)it->lp.segs.size();
+        bc.g0 = (uint32_t)go;
+        bc.ng = (uint32_t)it->lp.g.size();
+        bc.nchunks = it->lp.nchunks;
+        memcpy(segs.h + so, it->lp.segs.data(), it->lp.segs.size() * sizeof(SegDesc));
+        memcpy(gammas.h + go, it->lp.g.data(), it->lp.g.size() * sizeof(GammaDesc));
+        so += it->lp.segs.size();
+        go += it->lp.g.size();
+        scrs.h[i] = it->c->d_scr;
+        work[i] = estimated_work(it);
+        total += work[i];
+    }
+    // order: each code once, plus extra entries in proportion to its share of
+    // the work; shortest first, so that small (newly admitted) codes get warps
+    // at the start of every slice
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; i++) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] < work[b]; });
+    std::vector<int32_t> ord;
+    ord.reserve((size_t)n + tw);
+    for (int i : idx) {
+        long extra = (long)floor(work[i] / total * (double)tw);
+        for (long k = 0; k <= extra; k++) ord.push_back(i);
+    }
+    if (!order.ensure(ord.size())) return DIST_ENOMEM;
+    memcpy(order.h, ord.data(), ord.size() * sizeof(int32_t));
+    sched.h[0] = sched.h[1] = 0;
+    if (!codes.upload(n, st) || !segs.upload(nseg, st) || !gammas.upload(ngam, st) ||
+        !order.upload(ord.size(), st) || !sched.upload(2, st) || !scrs.upload(n, st))
+        return DIST_ECUDA;
+    BatchParams P;
+    memset(&P, 0, sizeof P);
+    P.codes = codes.d;
+    P.segs = segs.d;
+    P.gammas = gammas.d;
+    P.order = order.d;
+    P.sched = sched.d;
+    P.binom = dev->d_binom;
+    P.ncodes = n;
+    P.norder = (int)ord.size();
+    P.budget_ns = opts.slice_ms > 0 ? (unsigned long long)(opts.slice_ms * 1e6) : 0ull;
+    const int grid = dev->sms * dev->batch_blocks_per_sm;
+    cudaEventRecord(e0, st);
+    if (batch_launch(P, grid, st) != cudaSuccess) return DIST_ECUDA;
+    cudaEventRecord(e1, st);
+    if (batch_gather_launch(scrs.d, outs.d, n, st) != cudaSuccess) return DIST_ECUDA;
+    if (cudaMemcpyAsync(outs.h, outs.d, n * sizeof(BatchOut), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return DIST_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    gpu_seconds += ms * 1e-3;
+    launches++;
+    slices++;
+    // per code: certify, resume, or plan the next steps
+    for (int i = 0; i < n; i++) {
+        Item* it = run[i];
+        it->slices++;
+        const BatchOut& o = outs.h[i];
+        const LaunchPlan& lp = it->lp;
+        const Plan& p = it->c->plan;
+        const uint32_t U = o.U;
+        const unsigned long long next = std::min(o.next_chunk, lp.nchunks);
+        it->res.codewords = o.codewords;
+        const SliceVerdict v = plan_after_slice(p, lp, U, next);
+        it->last_round = std::max(it->last_round, v.last_round);
+        if (v.kind == SLICE_REPLAN) {
+            it->L = v.L;  // plan the following steps next slice
+            it->r_next = lp.next_r;
+            it->j_next = lp.next_jpos;
+            it->planned = false;
+            it->init_mode = 2;
+        }
+        const bool certified = v.kind == SLICE_CERTIFIED;
+        if (!certified) continue;
+        dist_result& r = it->res;
+        r.k_eff = p.k_eff;
+        r.n_gamma = (int)p.J.size();
+        r.rounds = it->last_round;
+        r.launches = (uint64_t)it->slices;
+        if (U == DIST_WINF) {
+            finish(it, DIST_EZERO);
+            continue;
+        }
+        r.d = (int)U;
+        r.lower = (int)U;
+        if (o.slot.claim == 0 || plan_decode(p, o.slot, r.witness, r.coeffs) != P_OK) {
+            finish(it, DIST_EINTERNAL);
+            continue;
+        }
+        finish(it, DIST_OK);
+    }
+    return DIST_OK;
+}
+
+void dist_batch::run() {
+    cudaSetDevice(dev->device);
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+        cv_work.wait(lk, [&] { return stop || !pending.empty() || !active.empty(); });
+        if (stop) break;
+        // admission by count and device footprint
+        const size_t max_active = opts.max_active > 0 ? (size_t)opts.max_active : 8192;
+        while (!pending.empty() && active.size() < max_active) {
+            Item* it = pending.front();
+            if (opts.max_resident_bytes && !active.empty() &&
+                resident + it->footprint > opts.max_resident_bytes)
+                break;
+            pending.pop_front();
+            it->t_admit = wall_now();
+            resident += it->footprint;
+            active.push_back(it);
+        }
+        lk.unlock();
+        int rc = fatal ? fatal : slice();
+        lk.lock();
+        if (rc) {
+            fatal = rc;
+            for (Item* it : active)
+                if (!it->done) finish(it, rc);
+        }
+        // retire finished codes and complete tickets
+        std::vector<Item*> keep;
+        for (Item* it : active) {
+            if (!it->done) {
+                keep.push_back(it);
+                continue;
+            }
+            resident -= it->footprint;
+            codes_done++;
+            auto t = tickets.find(it->ticket);
+            if (t != tickets.end()) t->second.remaining--;
+        }
+        active.swap(keep);
+        cv_done.notify_all();
+    }
+}
+
+extern "C" {
+
+int dist_batch_create(dist_batch** out, const dist_batch_opts* opts) {
+    if (!out) return DIST_EINVAL;
+    *out = nullptr;
+    DeviceCtx* dev = nullptr;
+    int rc = device_ctx(&dev);
+    if (rc) return rc;
+    dist_batch* b = new (std::nothrow) dist_batch();
+    if (!b) return DIST_ENOMEM;
+    if (opts) b->opts = *opts;
+    b->dev = dev;
+    if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) {
+        delete b;
+        return DIST_ECUDA;
+    }
+    b->worker = std::thread([b] { b->run(); });
+    *out = b;
+    return DIST_OK;
+}
+
+int dist_batch_submit(dist_batch* b, dist_code* const* codes, int count, uint64_t* ticket) {
+    if (!b || !codes || count < 1 || !ticket) return DIST_EINVAL;
+    std::lock_guard<std::mutex> lk(b->mu);
+    if (b->fatal) return b->fatal;
+    for (int i = 0; i < count; i++) {
+        if (!codes[i]) return DIST_EINVAL;
+        if (codes[i]->in_batch || codes[i]->dev != b->dev) return DIST_EBUSY;
+        if (codes[i]->plan.n_stab > 0 && codes[i]->plan.s_rank == codes[i]->plan.k_eff) return DIST_EZERO;
+    }
+    const double now = wall_now();
+    const uint64_t id = b->next_ticket++;
+    Ticket& t = b->tickets[id];
+    for (int i = 0; i < count; i++) {
+        Item* it = new Item();
+        it->c = codes[i];
+        it->c->in_batch = 1;
+        it->ticket = id;
+        it->t_submit = now;
+        it->L = plan_initial_bound(it->c->plan);
+        it->footprint = it->c->plan.tables.size() * 4 + sizeof(Scratch);
+        t.items.push_back(it);
+        b->pending.push_back(it);
+    }
+    t.remaining = count;
+    *ticket = id;
+    b->cv_work.notify_one();
+    return DIST_OK;
+}
+
+static int collect(dist_batch* b, std::map<uint64_t, Ticket>::iterator t, dist_result* results) {
+    for (size_t i = 0; i < t->second.items.size(); i++) {
+        Item* it = t->second.items[i];
+        if (results) results[i] = it->res;
+        it->c->in_batch = 0;
+        delete it;
+    }
+    b->tickets.erase(t);
+    return DIST_OK;
+}
+
+int dist_batch_poll(dist_batch* b, uint64_t ticket, dist_result* results) {
+    if (!b) return DIST_EINVAL;
+    std::lock_guard<std::mutex> lk(b->mu);
+    auto t = b->tickets.find(ticket);
+    if (t == b->tickets.end()) return DIST_EINVAL;
+    if (t->second.remaining > 0) return DIST_EBUSY;
+    return collect(b, t, results);
+}
+
+int dist_batch_wait(dist_batch* b, uint64_t ticket, dist_result* results, double timeout_s) {
+    if (!b) return DIST_EINVAL;
+    std::unique_lock<std::mutex> lk(b->mu);
+    auto t = b->tickets.find(ticket);
+    if (t == b->tickets.end()) return DIST_EINVAL;
+    auto ready = [&] { return t->second.remaining <= 0; };
+    if (timeout_s > 0) {
+        if (!b->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) return DIST_ETIMEOUT;
+    } else {
+        b->cv_done.wait(lk, ready);
+    }
+    return collect(b, t, results);
+}
+
+int dist_batch_stats(dist_batch* b, dist_batch_stats_t* s) {
+    if (!b || !s) return DIST_EINVAL;
+    std::lock_guard<std::mutex> lk(b->mu);
+    memset(s, 0, sizeof *s);
+    s->slices = b->slices;
+    s->launches = b->launches;
+    s->codes_done = b->codes_done;
+    s->active = (uint64_t)b->active.size();
+    s->pending = (uint64_t)b->pending.size();
+    s->gpu_seconds = b->gpu_seconds;
+    s->resident_bytes = (uint64_t)b->resident;
+    return DIST_OK;
+}
+
+int dist_batch_destroy(dist_batch* b) {
+    if (!b) return DIST_OK;
+    {
+        std::lock_guard<std::mutex> lk(b->mu);
+        b->stop = true;
+        b->cv_work.notify_all();
+    }
+    if (b->worker.joinable()) b->worker.join();
+    cudaStreamSynchronize(b->st);
+    for (auto& kv : b->tickets)
+        for (Item* it : kv.second.items) {
+            it->c->in_batch = 0;
+            delete it;
+        }
+    b->codes.release();
+    b->segs.release();
+    b->gammas.release();
+    b->order.release();
+    b->sched.release();
+    b->inits.release();
+    b->scrs.release();
+    b->outs.release();
+    if (b->e0) cudaEventDestroy(b->e0);
+    if (b->e1) cudaEventDestroy(b->e1);
+    if (b->st) cudaStreamDestroy(b->st);
+    delete b;
+    return DIST_OK;
+}
+
+}  // extern "C"

@@ -48,6 +48,7 @@ struct GammaDesc {
     uint32_t rep_off;     // word offset of its representatives in the global table buffer
     uint32_t coef_off;    // word offset of its coefficient planes
     uint32_t flag_off;    // word offset of its per-unit pivot flags
+    uint32_t r0_off;      // word offset of its word-0 table ([a][3] x,z pairs)
     uint32_t s_rep;       // word offset of its representatives in shared memory
     uint32_t s_r0;        // word offset of its word-0 table (U2 pairs) in shared memory
     uint32_t s_flag;      // word offset of its pivot flags in shared memory
@@ -85,4 +86,43 @@ struct EnumParams {
     unsigned long long nchunks;
     unsigned long long budget_ns;       // stop after this long (per block, %globaltimer); 0 = none
     GammaDesc g[DIST_MAXGAMMA];
+};
+
+// One code in a multi-code launch.
+struct BatchCode {
+    const uint32_t* tables;             // the code's table buffer (Plan::tables on the device)
+    Scratch* scr;                       // its own bound, counters and witness slots
+    uint32_t outside[DIST_MAXCW];
+    int32_t W, CW, proj, exclude;
+    uint32_t seg0, nseg;                // its segments in BatchParams::segs
+    uint32_t g0, ng;                    // its generator matrices in BatchParams::gammas
+    unsigned long long nchunks;
+};
+
+// A multi-code launch: warps pick codes from `order` (codes repeated in
+// proportion to their work), then pull chunks from each code's own counter.
+struct BatchParams {
+    const BatchCode* codes;
+    const SegDesc* segs;                // SegDesc::g is relative to the code's g0
+    const GammaDesc* gammas;
+    const int32_t* order;
+    unsigned long long* sched;          // [0] next order entry, [1] join probe counter
+    const unsigned long long* binom;    // global [DIST_MAXU + 1][DIST_MAXR + 1]
+    int ncodes, norder;
+    unsigned long long budget_ns;       // stop after this long (per block); 0 = none
+};
+
+// Per-code scratch set-up before a multi-code launch.
+struct BatchInit {
+    Scratch* scr;
+    uint32_t mode;                      // 1 = full reset + seed, 2 = restart the chunk counter
+    uint32_t U0;                        // seeded upper bound (DIST_WINF = none)
+    WitnessSlot slot;                   // witness of U0
+};
+
+// Per-code state read back after a multi-code launch.
+struct BatchOut {
+    uint32_t U, status;
+    unsigned long long next_chunk, codewords;
+    WitnessSlot slot;                   // slot[U] (claim = 0 if none)
 };

@@ -152,6 +152,183 @@ __global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_kernel(const __grid_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Multi-code launch.  Each code keeps its own chunk counter and bound in its
+// Scratch; the tables are read from global memory (they stay in L1/L2: a few
+// KB per code).  Phase 1: every entry of the order list buys one chunk of its
+// code; the list runs shortest job first and repeats each code in proportion
+// to its estimated work, so newly admitted small codes get warps at once and
+// large codes get many.  Phase 2: warps stay on one open code until it runs
+// out, then join another.  A chunk whose segment has L_before >= U retires
+// the code (its counter is pushed to the end), which costs the others nothing.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool code_open(const BatchCode& bc) {
+    const unsigned long long nxt = *reinterpret_cast<volatile unsigned long long*>(&bc.scr->next_chunk);
+    return nxt < bc.nchunks;
+}
+
+// Join phase: a code that still has chunks, probing the order list round
+// robin (large codes appear many times in it, so open ones are found fast).
+__device__ int join_code(const BatchParams& P) {
+    for (int probe = 0; probe < P.norder; probe++) {
+        const unsigned long long k = atomicAdd(&P.sched[1], 1ull) % (unsigned long long)P.norder;
+        const int c = P.order[k];
+        if (code_open(P.codes[c])) return c;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_batch_kernel(const __grid_constant__ BatchParams P) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long t_start = P.budget_ns ? global_ns() : 0ull;
+    uint32_t thr = DIST_WINF;
+    int cur = -1;
+    bool listed = true;  // phase 1: one chunk per order-list entry
+    for (;;) {
+        if (listed) {
+            unsigned long long k = 0;
+            if (lane == 0) k = atomicAdd(&P.sched[0], 1ull);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k < (unsigned long long)P.norder) {
+                const int c = P.order[k];
+                if (c != cur) thr = DIST_WINF;  // another code: its own bound
+                cur = c;
+            } else {
+                listed = false;
+                cur = -1;
+            }
+        }
+        if (!listed && cur < 0) {  // phase 2: stay on one open code until it runs out
+            int c = 0;
+            if (lane == 0) c = join_code(P);
+            cur = __shfl_sync(0xffffffffu, c, 0);
+            if (cur < 0) break;
+            thr = DIST_WINF;
+        }
+        const BatchCode& bc = P.codes[cur];
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(&bc.scr->next_chunk, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        if (chunk >= bc.nchunks) {
+            if (!listed) cur = -1;
+            continue;
+        }
+        const SegDesc* segs = P.segs + bc.seg0;
+        int lo_s = 0, hi_s = (int)bc.nseg;
+        while (hi_s - lo_s > 1) {
+            const int mid = (lo_s + hi_s) >> 1;
+            if (segs[mid].chunk_base <= chunk) lo_s = mid;
+            else hi_s = mid;
+        }
+        const SegDesc sg = segs[lo_s];
+        int skip = 0;
+        if (lane == 0) {
+            const uint32_t u = *reinterpret_cast<volatile uint32_t*>(&bc.scr->U);
+            if ((int)u <= sg.L_before) {
+                skip = 1;
+                atomicMax(&bc.scr->next_chunk, bc.nchunks);
+            }
+        }
+        if (__shfl_sync(0xffffffffu, skip, 0)) {
+            if (!listed) cur = -1;
+            continue;
+        }
+        const GammaDesc& g = P.gammas[bc.g0 + sg.g];
+        LaneCtx C;
+        C.reps = bc.tables + g.rep_off;
+        C.r0 = reinterpret_cast<const U2*>(bc.tables + g.r0_off);
+        C.flags = bc.tables + g.flag_off;
+        C.coefs = bc.tables + g.coef_off;
+        C.binom = P.binom;
+        C.bstride = DIST_MAXR + 1;
+        C.outside = bc.outside;
+        C.a = g.a;
+        C.b = g.b;
+        C.W = bc.W;
+        C.CW = bc.CW;
+        C.r = sg.r;
+        C.gamma = g.gamma;
+        C.proj = bc.proj;
+        C.exclude = bc.exclude;
+        C.L_before = sg.L_before;
+        DevSink sink{bc.scr};
+        const unsigned long long total = sg.NA * sg.NB;
+        const unsigned long long lo =
+            (chunk - sg.chunk_base) * 32ull * sg.spl + (unsigned long long)lane * sg.spl;
+        unsigned long long done = 0;
+        if (lo < total) {
+            const unsigned long long hi = lo + sg.spl < total ? lo + sg.spl : total;
+            done = walk_range(C, sink, thr, sg, lo, hi);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
+        int stop = 0;
+        if (lane == 0) {
+            if (done) atomicAdd(&bc.scr->codewords, done);
+            if (P.budget_ns && global_ns() - t_start > P.budget_ns) stop = 1;
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) break;
+    }
+}
+
+// Scratch set-up of many codes: block i serves item i.
+__global__ void batch_init_kernel(const BatchInit* items, int n) {
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const BatchInit it = items[i];
+    if (it.mode == 1) {
+        uint32_t* w = reinterpret_cast<uint32_t*>(it.scr);
+        for (int t = threadIdx.x; t < (int)(sizeof(Scratch) / 4); t += blockDim.x) w[t] = 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            it.scr->U = it.U0;
+            if (it.U0 <= DIST_MAXN) it.scr->slot[it.U0] = it.slot;
+        }
+    } else if (it.mode == 2 && threadIdx.x == 0) {
+        it.scr->next_chunk = 0ull;
+    }
+}
+
+// Read-back of many codes: thread i gathers code i's bound, counters and the
+// witness slot of its bound.
+__global__ void batch_gather_kernel(Scratch* const* scrs, BatchOut* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Scratch* s = scrs[i];
+    BatchOut o;
+    o.U = s->U;
+    o.status = s->status;
+    o.next_chunk = s->next_chunk;
+    o.codewords = s->codewords;
+    if (o.U <= DIST_MAXN) o.slot = s->slot[o.U];
+    else memset(&o.slot, 0, sizeof o.slot);
+    out[i] = o;
+}
+
+cudaError_t batch_launch(const BatchParams& P, int grid, cudaStream_t st) {
+    enum_batch_kernel<<<grid, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_init_launch(const BatchInit* items, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    batch_init_kernel<<<n, 128, 0, st>>>(items, n);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_gather_launch(Scratch* const* scrs, BatchOut* out, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    batch_gather_kernel<<<(n + 127) / 128, 128, 0, st>>>(scrs, out, n);
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, enum_batch_kernel, 256, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
 size_t enum_smem_bytes(const EnumParams& P) { return (size_t)P.s_words * 4; }
 
 int enum_blocks_per_sm(size_t smem) {

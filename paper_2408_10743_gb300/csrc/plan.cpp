@@ -376,6 +376,7 @@ static void build_device_tables(const Plan& p, Gamma& G) {
         const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
         if (x.qubit >= 0 && pos_of[x.qubit] >= 32) G.dev_flags[t] = 1;
     }
+    G.dev_r0.assign(G.A.size() * 6, 0);
     for (int t = 0; t < u; t++) {
         const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
         for (int e = 0; e < x.nrep; e++) {
@@ -389,6 +390,10 @@ static void build_device_tables(const Plan& p, Gamma& G) {
             for (int c = 0; c < 2; c++)
                 for (int w = 0; w < CW; w++)
                     G.dev_coefs[(((size_t)t * 3 + e) * 2 + c) * CW + w] = x.coef[e].p[c][w];
+            if (t < (int)G.A.size()) {
+                G.dev_r0[((size_t)t * 3 + e) * 2 + 0] = dx[0];
+                G.dev_r0[((size_t)t * 3 + e) * 2 + 1] = dz[0];
+            }
         }
     }
 }
@@ -519,6 +524,9 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
         off += G.dev_coefs.size();
         G.flag_off = (uint32_t)off;
         off += G.dev_flags.size();
+        off = (off + 1) & ~(size_t)1;
+        G.r0_off = (uint32_t)off;
+        off += G.dev_r0.size();
         off = (off + 3) & ~(size_t)3;
     }
     p->tables.assign(off, 0);
@@ -526,6 +534,7 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
         std::copy(G.dev_reps.begin(), G.dev_reps.end(), p->tables.begin() + G.rep_off);
         std::copy(G.dev_coefs.begin(), G.dev_coefs.end(), p->tables.begin() + G.coef_off);
         std::copy(G.dev_flags.begin(), G.dev_flags.end(), p->tables.begin() + G.flag_off);
+        std::copy(G.dev_r0.begin(), G.dev_r0.end(), p->tables.begin() + G.r0_off);
     }
 
     // The lightest representative is a codeword: it seeds the upper bound.
@@ -597,6 +606,7 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
             if (lp->step_r.empty()) return P_ERANGE;
             break;
         }
+        lp->step_seg0.push_back((int)lp->segs.size());
         if (gslot[g] < 0) {
             gslot[g] = (int)lp->g.size();
             GammaDesc d;
@@ -604,6 +614,7 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
             d.rep_off = G.rep_off;
             d.coef_off = G.coef_off;
             d.flag_off = G.flag_off;
+            d.r0_off = G.r0_off;
             d.a = (uint16_t)a;
             d.b = (uint16_t)b;
             d.gamma = g;
@@ -660,6 +671,10 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
         chunks += (sd.NA * sd.NB + 32 * spl - 1) / (32 * spl);
     }
     lp->nchunks = chunks;
+    for (size_t s = 0; s < lp->step_r.size(); s++) {
+        const int s0 = lp->step_seg0[s];
+        lp->step_chunk0.push_back(s0 < (int)lp->segs.size() ? lp->segs[s0].chunk_base : chunks);
+    }
     // Shared memory (32-bit words): representatives of every matrix, their
     // word-0 tables, the binomials the launch can need, the segment table.
     uint32_t off = 0;
@@ -685,6 +700,28 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
     off += (uint32_t)(lp->segs.size() * sizeof(SegDesc) / 4);
     lp->s_words = off;
     return P_OK;
+}
+
+SliceVerdict plan_after_slice(const Plan& p, const LaunchPlan& lp, uint32_t U, unsigned long long next) {
+    SliceVerdict v{SLICE_CONTINUE, 0, 0};
+    if (next > lp.nchunks) next = lp.nchunks;
+    for (size_t s = 0; s < lp.step_r.size(); s++) {
+        if (U != DIST_WINF && (int)U <= lp.step_L_before[s]) {
+            // every step before s is complete once s has started
+            if (next >= lp.step_chunk0[s]) {
+                v.kind = SLICE_CERTIFIED;
+                v.L = lp.step_L_before[s];
+            }
+            return v;
+        }
+        const unsigned long long end = s + 1 < lp.step_r.size() ? lp.step_chunk0[s + 1] : lp.nchunks;
+        if (next >= end) v.last_round = lp.step_r[s];
+    }
+    if (next < lp.nchunks) return v;
+    const int La = plan_lower_bound(p, lp.step_r.back(), lp.step_jpos.back());
+    v.L = La;
+    v.kind = (La == (int)DIST_WINF || (U != DIST_WINF && La >= (int)U)) ? SLICE_CERTIFIED : SLICE_REPLAN;
+    return v;
 }
 
 void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep) {

@@ -47,7 +47,8 @@ struct Gamma {
     std::vector<uint32_t> dev_reps;   // [u][3][2][W], device qubit order
     std::vector<uint32_t> dev_coefs;  // [u][3][2][CW]
     std::vector<uint32_t> dev_flags;  // [u]: 1 if a package whose pivot lies outside word 0
-    uint32_t rep_off = 0, coef_off = 0, flag_off = 0;  // word offsets in Plan::tables
+    std::vector<uint32_t> dev_r0;     // [a][3][2]: word 0 of the A-units' representatives
+    uint32_t rep_off = 0, coef_off = 0, flag_off = 0, r0_off = 0;  // word offsets in Plan::tables
     int units() const { return (int)(A.size() + B.size()); }
 };
 
@@ -74,6 +75,8 @@ struct LaunchPlan {
     std::vector<SegDesc> segs;
     std::vector<GammaDesc> g;
     std::vector<int> step_r, step_jpos, step_L_before;
+    std::vector<int> step_seg0;                     // first segment of each step
+    std::vector<unsigned long long> step_chunk0;    // first chunk of each step (nchunks if none)
     int W = 1, CW = 1, proj = 0, exclude = 0;
     int brows = 0, bcols = 0;
     uint32_t s_binom = 0, s_segs = 0, s_words = 0;  // shared-memory layout
@@ -107,6 +110,19 @@ double plan_round_count(const Plan& p, int g, int r);
 // before (r, jpos).  Returns P_ERANGE if r exceeds the device walk's limits.
 int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int target_warps,
                 double max_codewords, LaunchPlan* lp);
+
+// What a code's state means after a launch that may have stopped early
+// (time budget).  next = chunks claimed so far (all claimed chunks finished).
+// CERTIFIED: d = U (or no codeword if U = DIST_WINF).  CONTINUE: resume the
+// same plan.  REPLAN: every planned step finished below U; plan from
+// (lp.next_r, lp.next_jpos) with the bound L_after.
+enum { SLICE_CONTINUE = 0, SLICE_CERTIFIED = 1, SLICE_REPLAN = 2 };
+struct SliceVerdict {
+    int kind;
+    int L;           // certifying bound (CERTIFIED) or bound in force for the next plan (REPLAN)
+    int last_round;  // last round known complete
+};
+SliceVerdict plan_after_slice(const Plan& p, const LaunchPlan& lp, uint32_t U, unsigned long long next);
 
 // Fills the launch-independent part of EnumParams (pointers stay null).
 void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep);

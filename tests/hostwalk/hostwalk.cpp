@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "plan.h"
@@ -135,6 +136,118 @@ extern "C" int hw_solve(const uint8_t* gen, int n, int K, int field, int n_stab,
     HostExec ex(&p);
     ex.warps = warps;
     return solve_loop(p, ex, 0.0, out);
+}
+
+// The batch engine's per-code life cycle on the CPU: the whole remaining plan
+// in one launch plan, executed in slices that stop after a random number of
+// chunks (a time budget), with the kernel's skip rule, until the after-slice
+// verdict certifies d.  Exercises resumption and re-planning.
+extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int n_stab,
+                               unsigned seed, int max_seg_per_plan, dist_result* out) {
+    Plan p;
+    int rc = plan_build(gen, n, K, field, &p);
+    if (rc) return rc;
+    if (n_stab) {
+        rc = plan_set_exclude(&p, n_stab);
+        if (rc) return rc;
+    }
+    memset(out, 0, sizeof *out);
+    HostExec ex(&p);
+    ex.warps = 3;
+    ex.reset();
+    const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
+    if (u0 < (int)DIST_WINF) ex.seed((uint32_t)u0, p.n_stab > 0 ? p.u0_excl_slot : p.u0_slot);
+    int L = plan_initial_bound(p), r = 1, jpos = 0;
+    unsigned lcg = seed * 2654435761u + 12345u;
+    for (int plans = 0; plans < 1000; plans++) {
+        LaunchPlan lp;
+        rc = plan_launch(p, r, jpos, L, u0, ex.warps, max_seg_per_plan > 0 ? 1.0 : 1e300, &lp);
+        if (rc) return rc;
+        if (max_seg_per_plan > 0 && (int)lp.step_r.size() > 1) {
+            // force short plans (one step) to exercise re-planning
+            lp = LaunchPlan();
+            rc = plan_launch(p, r, jpos, L, u0, ex.warps, 0.0, &lp);
+            if (rc) return rc;
+        }
+        std::vector<uint32_t> flags;
+        unsigned long long next = 0;
+        for (;;) {
+            lcg = lcg * 1664525u + 1013904223u;
+            unsigned long long slice_chunks = 1 + (lcg >> 8) % 7;
+            // run up to slice_chunks chunks of this plan from `next`, as a launch would
+            LaunchPlan part = lp;
+            EnumParams ep;
+            plan_params(p, lp, &ep);
+            std::vector<uint32_t> sm(lp.s_words + 2, 0);
+            for (const GammaDesc& g : lp.g) {
+                const uint32_t* src = p.tables.data() + g.rep_off;
+                for (int t = 0; t < (g.a + g.b) * 6 * ep.W; t++) sm[g.s_rep + t] = src[t];
+                U2* r0 = reinterpret_cast<U2*>(sm.data() + g.s_r0);
+                for (int t = 0; t < g.a * 3; t++) {
+                    r0[t].x = src[(t * 2 + 0) * ep.W];
+                    r0[t].z = src[(t * 2 + 1) * ep.W];
+                }
+                for (int t = 0; t < g.a + g.b; t++) sm[g.s_flag + t] = p.tables[g.flag_off + t];
+            }
+            unsigned long long* sbin = reinterpret_cast<unsigned long long*>(sm.data() + lp.s_binom);
+            for (int t = 0; t < lp.brows * lp.bcols; t++) {
+                int nn = t / lp.bcols, k = t - nn * lp.bcols;
+                sbin[t] = ex.binom[nn * (DIST_MAXR + 1) + k];
+            }
+            HostSink sink{&ex.scr};
+            for (unsigned long long c = 0; c < slice_chunks && next < lp.nchunks; c++) {
+                const unsigned long long chunk = next++;
+                int sgi = 0;
+                while (sgi + 1 < (int)lp.segs.size() && lp.segs[sgi + 1].chunk_base <= chunk) ++sgi;
+                const SegDesc& sg = lp.segs[sgi];
+                if ((int)ex.scr.U <= sg.L_before) {
+                    next = lp.nchunks;  // the kernel's skip: the rest is not needed
+                    break;
+                }
+                const GammaDesc& g = lp.g[sg.g];
+                LaneCtx C;
+                C.reps = sm.data() + g.s_rep;
+                C.r0 = reinterpret_cast<const U2*>(sm.data() + g.s_r0);
+                C.flags = sm.data() + g.s_flag;
+                C.coefs = p.tables.data() + g.coef_off;
+                C.binom = sbin;
+                C.bstride = lp.bcols;
+                C.outside = ep.outside;
+                C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW; C.r = sg.r;
+                C.gamma = g.gamma; C.proj = ep.proj; C.exclude = ep.exclude;
+                C.L_before = sg.L_before;
+                const unsigned long long total = sg.NA * sg.NB;
+                for (int lane = 0; lane < 32; lane++) {
+                    unsigned long long lo = (chunk - sg.chunk_base) * 32ull * sg.spl + (unsigned long long)lane * sg.spl;
+                    if (lo >= total) continue;
+                    unsigned long long hi = lo + sg.spl < total ? lo + sg.spl : total;
+                    uint32_t thr = DIST_WINF;
+                    ex.scr.codewords += walk_range(C, sink, thr, sg, lo, hi);
+                }
+            }
+            (void)part;
+            const SliceVerdict v = plan_after_slice(p, lp, ex.scr.U, next);
+            out->rounds = std::max(out->rounds, v.last_round);
+            out->launches++;
+            if (v.kind == SLICE_CERTIFIED) {
+                out->codewords = ex.scr.codewords;
+                out->k_eff = p.k_eff;
+                if (ex.scr.U == DIST_WINF) return -6;
+                out->d = (int)ex.scr.U;
+                out->lower = out->d;
+                WitnessSlot s = ex.scr.slot[ex.scr.U];
+                if (s.claim == 0 || plan_decode(p, s, out->witness, out->coeffs) != P_OK) return -8;
+                return 0;
+            }
+            if (v.kind == SLICE_REPLAN) {
+                L = v.L;
+                r = lp.next_r;
+                jpos = lp.next_jpos;
+                break;
+            }
+        }
+    }
+    return -8;
 }
 
 // Revolving-door helpers exactly as the kernel uses them.

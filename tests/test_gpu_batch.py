@@ -1,0 +1,152 @@
+"""Batched and served solving (multi-code launches with continuous admission)
+against the CPU oracle and against the single-code path."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2408_10743_gb300 as dist
+from paper_2408_10743_gb300 import synth
+from paper_2408_10743_gb300.binding import DIST_EBUSY
+from codes import sym_weight_bits, tiny_random_code, toric
+
+pytestmark = pytest.mark.gpu
+
+
+def valid(g, r, field=2):
+    n = g.shape[1] // 2 if field == 2 else g.shape[1]
+    assert r["status"] == 0
+    if field == 2:
+        assert sym_weight_bits(r["witness"], n) == r["d"]
+        assert np.array_equal(np.bitwise_xor.reduce(g[r["coeffs"].astype(bool)], axis=0),
+                              r["witness"])
+    else:
+        assert int(np.count_nonzero(r["witness"])) == r["d"]
+
+
+def mixed_codes(count, seed):
+    """Random F2 codes of the batched workload's shape (n ~ U[16, 56],
+    K ~ U[n/2, n]) mixed with tiny codes of several kinds."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        if i % 3 == 0:
+            n = int(rng.integers(1, 9))
+            K = int(rng.integers(1, min(2 * n, 12) + 1))
+            g = tiny_random_code(rng, n, K, ["iid", "css", "yheavy", "sparse"][i % 4])
+            if not g.any():
+                g[0, 0] = 1
+        else:
+            r = synth.Xoshiro256ss(synth.seed_for(3, 10_000 + seed * 1000 + i))
+            n = 16 + r.below(25)
+            K = (n + 1) // 2 + r.below(n - (n + 1) // 2 + 1)
+            g = synth.random_f2_code(n, K, r)
+        out.append(g)
+    return out
+
+
+def test_batch_vs_oracle():
+    gens = mixed_codes(150, 1)
+    codes = [dist.Code(g) for g in gens]
+    with dist.Batch() as b:
+        t = b.submit(codes)
+        res = b.wait(t, timeout_s=120)
+        st = b.stats()
+    assert st["codes_done"] == len(gens)
+    for g, r in zip(gens, res):
+        assert r["d"] == oracle.bz(g)["d"]
+        valid(g, r)
+    for c in codes:
+        c.close()
+
+
+def test_batch_alone_equals_mix():
+    """Every code's distance is the same when solved alone (one code per
+    launch) and inside a mixed batch; witnesses are valid in both."""
+    gens = mixed_codes(60, 2) + [synth.single_qc(0), synth.single_f2(1)]
+    alone = [dist.distance(g) for g in gens]
+    codes = [dist.Code(g) for g in gens]
+    with dist.Batch(slice_ms=0.3) as b:
+        t = b.submit(codes)
+        mix = b.wait(t, timeout_s=120)
+    for g, a, m in zip(gens, alone, mix):
+        assert a["d"] == m["d"]
+        valid(g, m)
+    for c in codes:
+        c.close()
+
+
+def test_batch_f4_and_exclusion():
+    g4 = [synth.single_f4(i) for i in range(3)]
+    N, s = toric(3)
+    N4, s4 = toric(4)
+    codes = [dist.Code(g, field=4) for g in g4]
+    ce = dist.Code(N)
+    ce.set_exclude(s)
+    ce4 = dist.Code(N4)
+    ce4.set_exclude(s4)
+    with dist.Batch() as b:
+        t = b.submit(codes + [ce, ce4])
+        res = b.wait(t, timeout_s=60)
+    for g, r in zip(g4, res[:3]):
+        assert r["d"] == oracle.bz(g, field=4)["d"]
+        valid(g, r, field=4)
+    assert res[3]["d"] == 3 and res[4]["d"] == 4
+
+
+def test_served_requests_overlap_a_long_one():
+    """Continuous batching: a long request is running when small requests
+    arrive; they are admitted at the next slice, finish long before it, and
+    give the same results as alone."""
+    big = synth.random_f2_code(72, 72, synth.Xoshiro256ss(424242))  # d = 15, ~2.4e11 codewords
+    smalls = mixed_codes(30, 3)
+    with dist.Batch(slice_ms=1.0) as b:
+        cb = dist.Code(big)
+        tb = b.submit([cb])
+        time.sleep(0.01)
+        scs = [dist.Code(g) for g in smalls]
+        ts = [b.submit([c]) for c in scs]
+        small_res = [b.wait(t, timeout_s=60)[0] for t in ts]
+        polled = b.poll(tb)  # None while the long one is still running
+        big_res = polled[0] if polled is not None else b.wait(tb, timeout_s=120)[0]
+        st = b.stats()
+    assert big_res["d"] == 15
+    valid(big, big_res)
+    assert st["slices"] > 1
+    for g, r in zip(smalls, small_res):
+        assert r["d"] == dist.distance(g)["d"]
+        valid(g, r)
+    # the small requests did not wait for the long one
+    assert max(r["seconds"] for r in small_res) < big_res["seconds"]
+
+
+def test_admission_limits_and_ownership():
+    gens = mixed_codes(40, 4)
+    codes = [dist.Code(g) for g in gens]
+    with dist.Batch(max_active=4, slice_ms=0.2) as b:
+        t = b.submit(codes)
+        with pytest.raises(dist.DistError) as e:
+            codes[0].solve()  # owned by the batch until collected
+        assert e.value.code == DIST_EBUSY
+        with pytest.raises(dist.DistError):
+            b.submit([codes[1]])
+        res = b.wait(t, timeout_s=60)
+        st = b.stats()
+    assert st["slices"] >= 10  # at most four codes per slice
+    for g, r in zip(gens, res):
+        assert r["d"] == oracle.bz(g)["d"]
+    assert codes[0].solve()["d"] == res[0]["d"]  # released after collection
+    for c in codes:
+        c.close()
+
+
+def test_batch_workload3_sample():
+    """First codes of the 4096-code batched workload vs the single-code path."""
+    gens = synth.batch_codes(64)
+    codes = [dist.Code(g) for g in gens]
+    with dist.Batch() as b:
+        res = b.wait(b.submit(codes), timeout_s=120)
+    for g, c, r in zip(gens, codes, res):
+        assert r["d"] == c.solve()["d"]
+        valid(g, r)

@@ -1,7 +1,8 @@
 """The enumeration kernel's lane code (walk.cuh), the planner and the round
 loop, run on the CPU by a test-only harness (tests/hostwalk), against the
 oracle.  This checks the enumeration logic -- segments, revolving-door order,
-the 27-entry table with its Gray walk, the word-0 filter and slow path, the
+the 9-entry table with its register and dynamic Gray digits, the word-0 filter
+and slow path, the
 bounds -- without a GPU.  The GPU parity tests run the same code on device."""
 import ctypes
 import os
@@ -38,6 +39,10 @@ def hw():
                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(DistResult)]
     L.hw_rd_walk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int,
                              ctypes.POINTER(ctypes.c_uint8)]
+    L.hw_solve_sliced.restype = ctypes.c_int
+    L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
+                                  ctypes.POINTER(DistResult)]
     return L
 
 
@@ -181,3 +186,46 @@ def test_codeword_count_full_round(hw):
     last = sum(sum(comb(info.a[j], i) * 3 ** i * comb(info.b[j], r.rounds - i)
                    for i in range(0, r.rounds + 1)) for j in J)
     assert total - last <= r.codewords <= total
+
+
+def solve_sliced(L, g, seed, one_step_plans, field=2, n_stab=0):
+    g = np.ascontiguousarray(g, dtype=np.uint8)
+    n = g.shape[1] // 2 if field == 2 else g.shape[1]
+    r = DistResult()
+    rc = L.hw_solve_sliced(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n, g.shape[0], field,
+                           n_stab, seed, 1 if one_step_plans else 0, ctypes.byref(r))
+    return rc, r
+
+
+@pytest.mark.parametrize("one_step", [False, True])
+def test_sliced_engine_vs_oracle(hw, one_step):
+    """The batch engine's life cycle of a code: launches that stop after a
+    random number of chunks, resumption from the chunk counter, the skip rule,
+    re-planning after short plans, and the after-slice certification."""
+    rng = np.random.default_rng(36 + one_step)
+    for t in range(80):
+        if t % 4 == 3:
+            r0 = synth.Xoshiro256ss(8800 + t)
+            n = 16 + r0.below(25)
+            K = (n + 1) // 2 + r0.below(n - (n + 1) // 2 + 1)
+            g = synth.random_f2_code(n, K, r0)
+        else:
+            n = int(rng.integers(1, 9))
+            K = int(rng.integers(1, min(2 * n, 12) + 1))
+            g = tiny_random_code(rng, n, K, ["iid", "css", "yheavy"][t % 3])
+            if not g.any():
+                continue
+        rc, r = solve_sliced(hw, g, seed=t, one_step_plans=one_step)
+        assert rc == 0, rc
+        assert r.d == oracle.bz(g)["d"]
+        check_witness(g, r)
+
+
+def test_sliced_engine_exclusion_and_f4(hw):
+    for L in (2, 3, 4):
+        N, s = toric(L)
+        rc, r = solve_sliced(hw, N, seed=L, one_step_plans=True, n_stab=s)
+        assert rc == 0 and r.d == L
+    g1 = synth.single_f4(1)
+    rc, r = solve_sliced(hw, g1, seed=5, one_step_plans=False, field=4)
+    assert rc == 0 and r.d == oracle.bz(g1, field=4)["d"]

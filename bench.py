@@ -143,6 +143,166 @@ def cpu_baseline(g, field, budget_s):
             "complete": bool(r["complete"]), "seconds": r["seconds"]}
 
 
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def batch_measure(dist, count):
+    """Workload 3: `count` random F2 codes (n ~ U[16,56], K ~ U[n/2,n]) solved
+    (a) together by the batch engine (one multi-code launch unless a code
+    needs more) and (b) one code per launch through dist_solve, on the same
+    GPU, with the codes already initialised (tables resident)."""
+    from paper_2408_10743_gb300 import synth
+    gens = synth.batch_codes(count)
+    t0 = time.perf_counter()
+    codes = [dist.Code(g) for g in gens]
+    t_init = time.perf_counter() - t0
+    with dist.Batch() as b:  # warm-up
+        b.wait(b.submit(codes[:64]))
+    with dist.Batch() as b:
+        t0 = time.perf_counter()
+        res_b = b.wait(b.submit(codes))
+        t_batch = time.perf_counter() - t0
+        st = b.stats()
+    t0 = time.perf_counter()
+    res_p = [c.solve() for c in codes]
+    t_plain = time.perf_counter() - t0
+    for c in codes:
+        c.close()
+    agree = sum(1 for a, p in zip(res_b, res_p) if a["d"] == p["d"] and a["status"] == 0)
+    lat_b = [r["seconds"] for r in res_b]
+    # one code per launch, all submitted at t = 0 and served in order: latency
+    # of code i is the sum of the solve times up to i
+    acc, lat_p = 0.0, []
+    for r in res_p:
+        acc += r["seconds"]
+        lat_p.append(acc)
+    return {"workload": "batch of %d random F2 codes, n ~ U[16,56], K ~ U[ceil(n/2), n]" % count,
+            "codes": count, "d_agree": agree,
+            "batched": {"codes_per_s": count / t_batch, "wall_ms": 1e3 * t_batch,
+                        "gpu_ms": 1e3 * st["gpu_seconds"], "launches": st["launches"],
+                        "codewords": int(sum(r["codewords"] for r in res_b)),
+                        "p50_ms": 1e3 * pct(lat_b, 50), "p99_ms": 1e3 * pct(lat_b, 99)},
+            "one_code_per_launch": {"codes_per_s": count / t_plain, "wall_ms": 1e3 * t_plain,
+                                    "gpu_ms": 1e3 * sum(r["gpu_seconds"] for r in res_p),
+                                    "launches": int(sum(r["launches"] for r in res_p)),
+                                    "codewords": int(sum(r["codewords"] for r in res_p)),
+                                    "p50_ms": 1e3 * pct(lat_p, 50), "p99_ms": 1e3 * pct(lat_p, 99)},
+            "init_ms": 1e3 * t_init}
+
+
+def serve_window(dist, requests, slice_ms, drain_s):
+    """Replays (arrival_s, kind, generator) requests against one batch engine in
+    real time; returns per-request records (None latency = not finished)."""
+    import threading
+    batch = dist.Batch(slice_ms=slice_ms)
+    recs = [None] * len(requests)
+    submitted = []
+    lock = threading.Lock()
+    t0 = time.perf_counter()
+
+    def client():
+        for i, (ta, kind, g) in enumerate(requests):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            code = dist.Code(g)
+            t = batch.submit([code])
+            with lock:
+                submitted.append((i, t, code, time.perf_counter() - t0))
+
+    th = threading.Thread(target=client)
+    th.start()
+    done = 0
+    t_end = requests[-1][0] + drain_s if requests else 0.0
+    k = 0
+    while True:
+        with lock:
+            item = submitted[k] if k < len(submitted) else None
+        if item is None:
+            if not th.is_alive() and k >= len(submitted):
+                break
+            time.sleep(0.0005)
+            continue
+        i, t, code, t_sub = item
+        left = t_end - (time.perf_counter() - t0)
+        if left <= 0:
+            break
+        try:
+            r = batch.wait(t, timeout_s=left)[0]
+        except dist.DistError:
+            break
+        ta = requests[i][0]
+        recs[i] = {"d": r["d"], "status": r["status"], "latency_s": (t_sub - ta) + r["seconds"],
+                   "codewords": r["codewords"], "n": requests[i][2].shape[1] // 2,
+                   "kind": requests[i][1]}
+        done += 1
+        k += 1
+    th.join()
+    wall = time.perf_counter() - t0
+    st = batch.stats()
+    batch.close()  # drops unfinished tickets; codes are freed after the measurement
+    for _, _, code, _ in submitted:
+        code.close()
+    return recs, wall, st
+
+
+def serve_measure(dist, rate, duration, slice_ms, drain_s, check_budget_s, check_total_s=60.0):
+    """Workload 4: Poisson requests (random F2 and quasi-cyclic codes,
+    n ~ U[20,96]) at `rate` per second for `duration` seconds."""
+    from paper_2408_10743_gb300 import synth
+    import oracle
+    reqs = list(synth.request_stream(rate_hz=rate, duration_s=duration))
+    recs, wall, st = serve_window(dist, reqs, slice_ms, drain_s)
+    fin = [r for r in recs if r is not None]
+    lat = [r["latency_s"] for r in fin]
+    checked = mismatched = 0
+    unchecked = []
+    t_chk = time.perf_counter()
+    done_reqs = sorted((g.shape[1] // 2, i) for i, ((ta, kind, g), r) in enumerate(zip(reqs, recs))
+                       if r is not None)
+    for nq, i in done_reqs:  # smallest first, within a total CPU budget
+        if time.perf_counter() - t_chk > check_total_s:
+            unchecked.append(int(nq))
+            continue
+        o = oracle.bz(reqs[i][2], time_budget=check_budget_s, allow_incomplete=True)
+        if o["complete"]:
+            checked += 1
+            mismatched += int(o["d"] != recs[i]["d"])
+        else:
+            unchecked.append(int(nq))
+    return {"rate_hz": rate, "duration_s": duration, "requests": len(reqs), "completed": len(fin),
+            "backlog": len(reqs) - len(fin), "wall_s": wall,
+            "codes_per_s": len(fin) / wall if wall > 0 else 0.0,
+            "p50_ms": 1e3 * pct(lat, 50) if lat else None, "p99_ms": 1e3 * pct(lat, 99) if lat else None,
+            "codewords": int(sum(r["codewords"] for r in fin)), "gpu_s": st["gpu_seconds"],
+            "slices": st["slices"], "oracle_checked": checked, "oracle_mismatches": mismatched,
+            "unchecked_n": sorted(unchecked)}
+
+
+def run_serve(args):
+    import torch
+    import paper_2408_10743_gb300 as dist
+    torch.cuda.set_device(0)
+    out = {"metric": "served codes/s and latency", "workload": "Poisson stream of distance queries",
+           "config": {"workload": "served", "n": "U[20,96]", "K": "U[ceil(n/2), n]",
+                      "kinds": "random F2 / quasi-cyclic 50:50", "slice_ms": args.slice_ms}}
+    out["as_written"] = serve_measure(dist, args.rate, args.duration, args.slice_ms, args.drain,
+                                      args.check_budget)
+    sweep = []
+    for rate in [float(x) for x in args.sweep.split(",") if x]:
+        r = serve_measure(dist, rate, args.sweep_duration, args.slice_ms, args.drain, args.check_budget)
+        sweep.append(r)
+    out["sweep"] = sweep
+    sustainable = [r["rate_hz"] for r in sweep if r["backlog"] == 0 and r["oracle_mismatches"] == 0]
+    out["highest_sustained_rate_hz"] = max(sustainable) if sustainable else None
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -286,6 +446,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(ctypes.sizeof(dist.DistResult)),
                     "ms_per_step": 1e3 * statistics.mean(e2e_s)},
             "gpu_launches": int(sum(launches))}
+    if args.batch_codes > 0:
+        line["batch"] = batch_measure(dist, args.batch_codes)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, field, args.cpu_budget)
     if rank == 0:
@@ -301,14 +463,26 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qc72", choices=["qc72", "f2_24", "f4_40"])
+    ap.add_argument("--workload", default="qc72", choices=["qc72", "f2_24", "f4_40", "serve"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: requests per second")
+    ap.add_argument("--duration", type=float, default=2.0, help="serve: arrival window (s)")
+    ap.add_argument("--drain", type=float, default=20.0, help="serve: time allowed after the window")
+    ap.add_argument("--slice-ms", type=float, default=2.0, help="serve: launch time budget")
+    ap.add_argument("--sweep", default="", help="serve: comma-separated rates to sweep")
+    ap.add_argument("--sweep-duration", type=float, default=3.0)
+    ap.add_argument("--check-budget", type=float, default=0.5,
+                    help="serve: oracle time per completed request (s); longer ones are listed unchecked")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-codes", type=int, default=4096,
+                    help="size of the batched-vs-one-per-launch comparison (0 = skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

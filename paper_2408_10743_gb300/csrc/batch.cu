@@ -45,6 +45,9 @@ using namespace dist;
 
 namespace {
 
+// A code with at most this many chunks is served entirely from the order list.
+const unsigned long long kSmallChunks = 64;
+
 struct Item {
     dist_code* c = nullptr;
     uint64_t ticket = 0;
@@ -126,6 +129,7 @@ struct dist_batch {
     DevBuf<SegDesc> segs;
     DevBuf<GammaDesc> gammas;
     DevBuf<int32_t> order;
+    DevBuf<int32_t> ring;
     DevBuf<unsigned long long> sched;
     DevBuf<BatchInit> inits;
     DevBuf<Scratch*> scrs;
@@ -235,23 +239,35 @@ int dist_batch::slice() {
         work[i] = estimated_work(it);
         total += work[i];
     }
-    // order: each code once, plus extra entries in proportion to its share of
-    // the work; shortest first, so that small (newly admitted) codes get warps
-    // at the start of every slice
+    // Order list (phase 1, one chunk per entry), shortest job first so that
+    // small -- typically newly admitted -- codes get warps at the start of
+    // every slice.  A code with few chunks left gets one entry per chunk and
+    // is done in phase 1; a large one gets entries in proportion to its share
+    // of the work and goes into the ring that phase 2 probes.
     std::vector<int> idx(n);
     for (int i = 0; i < n; i++) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] < work[b]; });
-    std::vector<int32_t> ord;
+    std::vector<int32_t> ord, rng;
     ord.reserve((size_t)n + tw);
     for (int i : idx) {
-        long extra = (long)floor(work[i] / total * (double)tw);
-        for (long k = 0; k <= extra; k++) ord.push_back(i);
+        const unsigned long long left = run[i]->lp.nchunks;  // upper bound on chunks still to claim
+        if (left <= kSmallChunks) {
+            for (unsigned long long k = 0; k < std::max(left, 1ull); k++) ord.push_back(i);
+        } else {
+            const long share = (long)floor(work[i] / total * (double)tw);
+            for (long k = 0; k <= share; k++) ord.push_back(i);
+        }
     }
-    if (!order.ensure(ord.size())) return DIST_ENOMEM;
+    for (auto it = idx.rbegin(); it != idx.rend(); ++it)
+        if (run[*it]->lp.nchunks > kSmallChunks) rng.push_back(*it);
+    if (rng.empty()) rng.push_back(idx.back());
+    if (!order.ensure(ord.size()) || !ring.ensure(rng.size())) return DIST_ENOMEM;
     memcpy(order.h, ord.data(), ord.size() * sizeof(int32_t));
+    memcpy(ring.h, rng.data(), rng.size() * sizeof(int32_t));
     sched.h[0] = sched.h[1] = 0;
     if (!codes.upload(n, st) || !segs.upload(nseg, st) || !gammas.upload(ngam, st) ||
-        !order.upload(ord.size(), st) || !sched.upload(2, st) || !scrs.upload(n, st))
+        !order.upload(ord.size(), st) || !ring.upload(rng.size(), st) || !sched.upload(2, st) ||
+        !scrs.upload(n, st))
         return DIST_ECUDA;
     BatchParams P;
     memset(&P, 0, sizeof P);
@@ -259,6 +275,8 @@ int dist_batch::slice() {
     P.segs = segs.d;
     P.gammas = gammas.d;
     P.order = order.d;
+    P.ring = ring.d;
+    P.nring = (int)rng.size();
     P.sched = sched.d;
     P.binom = dev->d_binom;
     P.ncodes = n;
@@ -478,6 +496,7 @@ int dist_batch_destroy(dist_batch* b) {
     b->segs.release();
     b->gammas.release();
     b->order.release();
+    b->ring.release();
     b->sched.release();
     b->inits.release();
     b->scrs.release();

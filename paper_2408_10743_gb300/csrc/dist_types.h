@@ -49,11 +49,14 @@ struct GammaDesc {
     uint32_t coef_off;    // word offset of its coefficient planes
     uint32_t flag_off;    // word offset of its per-unit pivot flags
     uint32_t r0_off;      // word offset of its word-0 table ([a][3] x,z pairs)
+    uint32_t r1_off;      // word offset of its word-1 table (same shape; W >= 2)
     uint32_t s_rep;       // word offset of its representatives in shared memory
     uint32_t s_r0;        // word offset of its word-0 table (U2 pairs) in shared memory
+    uint32_t s_r1;        // word offset of its word-1 table in shared memory
     uint32_t s_flag;      // word offset of its pivot flags in shared memory
     uint16_t a, b;        // A-units (three representatives), B-units (one)
     int32_t gamma;        // index in the plan (witness decoding)
+    int32_t t1;           // use the two-word filter when thr - P exceeds this
 };
 
 // A segment: within one step (round r of one generator matrix), the
@@ -105,10 +108,11 @@ struct BatchParams {
     const BatchCode* codes;
     const SegDesc* segs;                // SegDesc::g is relative to the code's g0
     const GammaDesc* gammas;
-    const int32_t* order;
-    unsigned long long* sched;          // [0] next order entry, [1] join probe counter
+    const int32_t* order;               // phase 1: one chunk per entry
+    const int32_t* ring;                // phase 2: codes with much work left, probed round robin
+    unsigned long long* sched;          // [0] next order entry, [1] ring probe counter
     const unsigned long long* binom;    // global [DIST_MAXU + 1][DIST_MAXR + 1]
-    int ncodes, norder;
+    int ncodes, norder, nring;
     unsigned long long budget_ns;       // stop after this long (per block); 0 = none
 };
 

@@ -22,6 +22,7 @@ namespace dist {
 
 struct DevSink {
     Scratch* scr;
+    __device__ __forceinline__ bool vote_any(bool p) { return __any_sync(__activemask(), p); }
     __device__ __forceinline__ bool poll(uint32_t& thr, int L_before) {
         const uint32_t u = *reinterpret_cast<volatile uint32_t*>(&scr->U);
         thr = u < thr ? u : thr;
@@ -66,9 +67,12 @@ __global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_kernel(const __grid_
         const int nw = (g.a + g.b) * 6 * P.W;
         for (int t = threadIdx.x; t < nw; t += blockDim.x) sm[g.s_rep + t] = src[t];
         U2* r0 = reinterpret_cast<U2*>(sm + g.s_r0);
+        U2* r1 = reinterpret_cast<U2*>(sm + g.s_r1);
         for (int t = threadIdx.x; t < g.a * 3; t += blockDim.x) {
             r0[t].x = src[(t * 2 + 0) * P.W];
             r0[t].z = src[(t * 2 + 1) * P.W];
+            r1[t].x = P.W >= 2 ? src[(t * 2 + 0) * P.W + 1] : 0u;
+            r1[t].z = P.W >= 2 ? src[(t * 2 + 1) * P.W + 1] : 0u;
         }
         for (int t = threadIdx.x; t < g.a + g.b; t += blockDim.x) sm[g.s_flag + t] = P.tables[g.flag_off + t];
     }
@@ -115,7 +119,9 @@ __global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_kernel(const __grid_
         LaneCtx C;
         C.reps = sm + g.s_rep;
         C.r0 = reinterpret_cast<const U2*>(sm + g.s_r0);
+        C.r1 = reinterpret_cast<const U2*>(sm + g.s_r1);
         C.flags = sm + g.s_flag;
+        C.t1 = g.t1;
         C.coefs = P.tables + g.coef_off;
         C.binom = sbin;
         C.bstride = P.bcols;
@@ -159,8 +165,10 @@ __global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_kernel(const __grid_
 // code; the list runs shortest job first and repeats each code in proportion
 // to its estimated work, so newly admitted small codes get warps at once and
 // large codes get many.  Phase 2: warps stay on one open code until it runs
-// out, then join another.  A chunk whose segment has L_before >= U retires
-// the code (its counter is pushed to the end), which costs the others nothing.
+// out, then join another from the ring of codes with much work left (small
+// codes get one entry per chunk in the order list and finish in phase 1).  A
+// chunk whose segment has L_before >= U retires the code (its counter is
+// pushed to the end), which costs the others nothing.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ bool code_open(const BatchCode& bc) {
@@ -168,12 +176,12 @@ __device__ __forceinline__ bool code_open(const BatchCode& bc) {
     return nxt < bc.nchunks;
 }
 
-// Join phase: a code that still has chunks, probing the order list round
-// robin (large codes appear many times in it, so open ones are found fast).
+// Phase 2: a code that still has chunks, probing the ring (the codes with
+// much work left) round robin.
 __device__ int join_code(const BatchParams& P) {
-    for (int probe = 0; probe < P.norder; probe++) {
-        const unsigned long long k = atomicAdd(&P.sched[1], 1ull) % (unsigned long long)P.norder;
-        const int c = P.order[k];
+    for (int probe = 0; probe < P.nring; probe++) {
+        const unsigned long long k = atomicAdd(&P.sched[1], 1ull) % (unsigned long long)P.nring;
+        const int c = P.ring[k];
         if (code_open(P.codes[c])) return c;
     }
     return -1;
@@ -238,7 +246,9 @@ __global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_batch_kernel(const _
         LaneCtx C;
         C.reps = bc.tables + g.rep_off;
         C.r0 = reinterpret_cast<const U2*>(bc.tables + g.r0_off);
+        C.r1 = reinterpret_cast<const U2*>(bc.tables + g.r1_off);
         C.flags = bc.tables + g.flag_off;
+        C.t1 = g.t1;
         C.coefs = bc.tables + g.coef_off;
         C.binom = P.binom;
         C.bstride = DIST_MAXR + 1;

@@ -374,9 +374,11 @@ static void build_device_tables(const Plan& p, Gamma& G) {
     G.dev_flags.assign((size_t)u, 0);
     for (int t = 0; t < u; t++) {
         const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
-        if (x.qubit >= 0 && pos_of[x.qubit] >= 32) G.dev_flags[t] = 1;
+        if (x.qubit >= 0 && pos_of[x.qubit] >= 32) G.dev_flags[t] |= 1u;
+        if (x.qubit >= 0 && pos_of[x.qubit] >= 64) G.dev_flags[t] |= 2u;
     }
     G.dev_r0.assign(G.A.size() * 6, 0);
+    G.dev_r1.assign(G.A.size() * 6, 0);
     for (int t = 0; t < u; t++) {
         const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
         for (int e = 0; e < x.nrep; e++) {
@@ -393,7 +395,31 @@ static void build_device_tables(const Plan& p, Gamma& G) {
             if (t < (int)G.A.size()) {
                 G.dev_r0[((size_t)t * 3 + e) * 2 + 0] = dx[0];
                 G.dev_r0[((size_t)t * 3 + e) * 2 + 1] = dz[0];
+                if (W >= 2) {
+                    G.dev_r1[((size_t)t * 3 + e) * 2 + 0] = dx[1];
+                    G.dev_r1[((size_t)t * 3 + e) * 2 + 1] = dz[1];
+                }
             }
+        }
+    }
+    // Level above which the one-word filter lets too many blocks through:
+    // word 0 of a representative weighs mu +- sigma; a block of 81 codewords
+    // slips through about 81 * Phi((thr - P - mu) / sigma) of the time, so
+    // switch when thr - P > mu - 3.3 sigma.
+    {
+        double s1 = 0, s2 = 0, cnt = 0;
+        for (size_t t = 0; t < G.A.size(); t++)
+            for (int e = 0; e < 3; e++) {
+                double w = __builtin_popcount(G.dev_r0[(t * 3 + e) * 2] | G.dev_r0[(t * 3 + e) * 2 + 1]);
+                s1 += w;
+                s2 += w * w;
+                cnt += 1;
+            }
+        if (cnt > 1 && W >= 2) {
+            double mu = s1 / cnt, var = std::max(0.0, s2 / cnt - mu * mu);
+            G.t1 = (int)floor(mu - 3.3 * sqrt(var + 1.0));
+        } else {
+            G.t1 = 1 << 20;  // one word covers every qubit: never switch
         }
     }
 }
@@ -527,6 +553,8 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
         off = (off + 1) & ~(size_t)1;
         G.r0_off = (uint32_t)off;
         off += G.dev_r0.size();
+        G.r1_off = (uint32_t)off;
+        off += G.dev_r1.size();
         off = (off + 3) & ~(size_t)3;
     }
     p->tables.assign(off, 0);
@@ -535,6 +563,7 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
         std::copy(G.dev_coefs.begin(), G.dev_coefs.end(), p->tables.begin() + G.coef_off);
         std::copy(G.dev_flags.begin(), G.dev_flags.end(), p->tables.begin() + G.flag_off);
         std::copy(G.dev_r0.begin(), G.dev_r0.end(), p->tables.begin() + G.r0_off);
+        std::copy(G.dev_r1.begin(), G.dev_r1.end(), p->tables.begin() + G.r1_off);
     }
 
     // The lightest representative is a codeword: it seeds the upper bound.
@@ -615,6 +644,8 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
             d.coef_off = G.coef_off;
             d.flag_off = G.flag_off;
             d.r0_off = G.r0_off;
+            d.r1_off = G.r1_off;
+            d.t1 = G.t1;
             d.a = (uint16_t)a;
             d.b = (uint16_t)b;
             d.gamma = g;
@@ -624,8 +655,14 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
             unsigned long long NA = ubinom(a, i), NB = ubinom(b, r - i);
             unsigned long long codes = lp->proj ? upow3(i - 1) : upow3(i);
             if (NA == 0 || NB == 0) continue;
-            if (NA == ~0ull || NB == ~0ull || codes == ~0ull) return P_ERANGE;
-            if (((unsigned __int128)NA * NB) >> 62) return P_ERANGE;
+            if (NA == ~0ull || NB == ~0ull || codes == ~0ull || (((unsigned __int128)NA * NB) >> 62)) {
+                // too many combinations to index: stop the plan before this step
+                if (lp->step_r.empty()) return P_ERANGE;
+                lp->segs.resize(lp->step_seg0.back());
+                seg_cw.resize(lp->segs.size());
+                lp->step_seg0.pop_back();
+                goto planned;
+            }
             SegDesc sd;
             memset(&sd, 0, sizeof sd);
             sd.NA = NA;
@@ -652,17 +689,21 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
         }
         if (L == (int)DIST_WINF) break;  // this step finished a complete enumeration
     }
+planned:
     lp->next_r = r;
     lp->next_jpos = jpos;
+    total = 0;
+    for (double cw : seg_cw) total += cw;
     lp->codewords = total;
-    // Chunks: each segment is cut into about six warp-chunks per resident warp
-    // (so that every segment spreads over the whole GPU); a lane chunk holds at
-    // most ~2^21 codewords so that stop requests are seen soon.
+    // Chunks: each segment is cut into about twelve warp-chunks per resident
+    // warp (so that every segment spreads over the whole GPU and the tail is
+    // short); a lane chunk holds at most ~2^16 codewords (about a millisecond
+    // for a warp) so that stop requests and time budgets are seen soon.
     unsigned long long chunks = 0;
     for (size_t t = 0; t < lp->segs.size(); t++) {
         SegDesc& sd = lp->segs[t];
-        double per_lane = seg_cw[t] / (32.0 * std::max(1, target_warps) * 6.0);
-        per_lane = std::min(per_lane, (double)(1u << 21));
+        double per_lane = seg_cw[t] / (32.0 * std::max(1, target_warps) * 12.0);
+        per_lane = std::min(per_lane, (double)(1u << 16));
         double spl_d = per_lane / (double)sd.codes;
         unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
         if (spl > (1ull << 30)) spl = 1ull << 30;
@@ -685,6 +726,8 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
     for (GammaDesc& d : lp->g) {
         off = (off + 1) & ~1u;
         d.s_r0 = off;
+        off += (uint32_t)d.a * 6u;
+        d.s_r1 = off;
         off += (uint32_t)d.a * 6u;
     }
     for (GammaDesc& d : lp->g) {

@@ -131,13 +131,15 @@ r5:
 struct LaneCtx {
     const uint32_t* reps;              // [u][3][2][W]
     const U2* r0;                      // [a][3]: word 0 of the A-units' representatives
-    const uint32_t* flags;             // [u]: package with its pivot outside word 0
+    const U2* r1;                      // [a][3]: word 1 (W >= 2)
+    const uint32_t* flags;             // [u]: bit 0 / bit 1: package with pivot beyond word 0 / 1
     const uint32_t* coefs;             // [u][3][2][CW]
     const unsigned long long* binom;   // [rows][bstride]
     const uint32_t* outside;
     int bstride;
     int a, b, W, CW, r, gamma, proj, exclude;
     int L_before;
+    int t1;                            // two-word filter when thr - P exceeds this
 };
 
 DIST_HD const uint32_t* rep_ptr(const LaneCtx& C, int unit, int e, int plane) {
@@ -221,34 +223,46 @@ DIST_HD_COLD void eval_generic(const LaneCtx& C, Sink& sink, uint32_t& thr, int 
 }
 
 // Slow path of one 81-codeword block: each codeword whose lower bound
-// popc(word 0) + P is below thr is weighed in full.  (vbx, vbz) is word 0 of
-// the B-units' sum; eB0 is digit B's value at the block start (digit A starts
-// every block at 0); P counts the subset's packages with a pivot outside
-// word 0, each worth one more unit of weight.
-template <class Sink>
+// (popcount of its first F words + P) is below thr is weighed in full.
+// (vbx, vbz) holds the first F words of the B-units' sum; eB0 is digit B's
+// value at the block start (digit A starts every block at 0); P counts the
+// subset's packages whose pivot lies beyond the first F words, each worth one
+// more unit of weight.
+template <int F, class Sink>
 DIST_HD_COLD void block_slow(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                             const uint8_t* dig, int nb, const uint8_t* sB, uint32_t vbx,
-                             uint32_t vbz, int eB0, uint32_t P) {
+                             const uint8_t* dig, int nb, const uint8_t* sB, const uint32_t* vbx,
+                             const uint32_t* vbz, int eB0, uint32_t P) {
     uint8_t e[DIST_MAXR];
-    uint32_t bx = vbx, bz = vbz;
+    const U2* tab[2] = {C.r0, C.r1};
+    uint32_t bx[F], bz[F];
+    for (int f = 0; f < F; f++) {
+        bx[f] = vbx[f];
+        bz[f] = vbz[f];
+    }
     for (int p = 0; p < i - 4; p++) {
         e[p] = dig[p];
-        const U2 v = C.r0[sA[p] * 3 + dig[p]];
-        bx ^= v.x;
-        bz ^= v.z;
+        for (int f = 0; f < F; f++) {
+            const U2 v = tab[f][sA[p] * 3 + dig[p]];
+            bx[f] ^= v.x;
+            bz[f] ^= v.z;
+        }
     }
-    const U2* ra = C.r0 + sA[i - 4] * 3;
-    const U2* rb = C.r0 + sA[i - 3] * 3;
-    const U2* r0 = C.r0 + sA[i - 2] * 3;
-    const U2* r1 = C.r0 + sA[i - 1] * 3;
     for (int kk = 0; kk < 9; kk++) {
         const int eA = (kk - kk / 3) % 3;
         const int eB = (eB0 + kk / 3) % 3;
         for (int j = 0; j < 9; j++) {
             const int e0 = j % 3, e1 = j / 3;
-            const uint32_t tx = bx ^ ra[eA].x ^ rb[eB].x ^ r0[e0].x ^ r1[e1].x;
-            const uint32_t tz = bz ^ ra[eA].z ^ rb[eB].z ^ r0[e0].z ^ r1[e1].z;
-            if ((uint32_t)popc32(tx | tz) + P >= thr) continue;
+            uint32_t lb = P;
+            for (int f = 0; f < F; f++) {
+                const U2* ra = tab[f] + sA[i - 4] * 3;
+                const U2* rb = tab[f] + sA[i - 3] * 3;
+                const U2* r0 = tab[f] + sA[i - 2] * 3;
+                const U2* r1 = tab[f] + sA[i - 1] * 3;
+                const uint32_t tx = bx[f] ^ ra[eA].x ^ rb[eB].x ^ r0[e0].x ^ r1[e1].x;
+                const uint32_t tz = bz[f] ^ ra[eA].z ^ rb[eB].z ^ r0[e0].z ^ r1[e1].z;
+                lb += (uint32_t)popc32(tx | tz);
+            }
+            if (lb >= thr) continue;
             e[i - 4] = (uint8_t)eA;
             e[i - 3] = (uint8_t)eB;
             e[i - 2] = (uint8_t)e0;
@@ -258,62 +272,56 @@ DIST_HD_COLD void block_slow(const LaneCtx& C, Sink& sink, uint32_t& thr, int i,
     }
 }
 
-// 9 codewords: base ^ table entry, word-0 weight, folded into the running min.
-#define DIST_SWEEP9(m)                                                                   \
-    do {                                                                                 \
-        const uint32_t c0 = (uint32_t)popc32((bx ^ Tx[0]) | (bz ^ Tz[0]));               \
-        const uint32_t c1 = (uint32_t)popc32((bx ^ Tx[1]) | (bz ^ Tz[1]));               \
-        const uint32_t c2 = (uint32_t)popc32((bx ^ Tx[2]) | (bz ^ Tz[2]));               \
-        const uint32_t c3 = (uint32_t)popc32((bx ^ Tx[3]) | (bz ^ Tz[3]));               \
-        const uint32_t c4 = (uint32_t)popc32((bx ^ Tx[4]) | (bz ^ Tz[4]));               \
-        const uint32_t c5 = (uint32_t)popc32((bx ^ Tx[5]) | (bz ^ Tz[5]));               \
-        const uint32_t c6 = (uint32_t)popc32((bx ^ Tx[6]) | (bz ^ Tz[6]));               \
-        const uint32_t c7 = (uint32_t)popc32((bx ^ Tx[7]) | (bz ^ Tz[7]));               \
-        const uint32_t c8 = (uint32_t)popc32((bx ^ Tx[8]) | (bz ^ Tz[8]));               \
-        m = min3u(m, min3u(c0, c1, c2), min3u(c3, c4, c5));                              \
-        m = min3u(m, min3u(c6, c7, c8), m);                                              \
-    } while (0)
+// Popcount of codeword j of the current base (first F words).
+template <int F>
+DIST_HD uint32_t word_weight(const uint32_t (&bx)[F], const uint32_t (&bz)[F], const uint32_t (&Tx)[F][9],
+                             const uint32_t (&Tz)[F][9], int j) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int f = 0; f < F; f++) c += (uint32_t)popc32((bx[f] ^ Tx[f][j]) | (bz[f] ^ Tz[f][j]));
+    return c;
+}
 
-#define DIST_STEP(d) \
-    do {             \
-        bx ^= d.x;   \
-        bz ^= d.z;   \
-    } while (0)
-
-// Fast path: subsets with at least four varying units.  Kept out of line so
-// that only its own state (table, register-digit deltas, base word, counters)
-// is live in the inner loop.
-template <class Sink>
+// Fast path: subsets with at least four varying units, filter on the first
+// F words of each plane (F = 1, or 2 when the bound is still far above the
+// distance).  Kept in one function so that only its own state (table,
+// register-digit deltas, base words, counters) is live in the inner loop.
+template <int F, class Sink>
 DIST_HD_FAST void eval_fast(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                           uint8_t* dig, int nb, const uint8_t* sB, uint32_t vbx, uint32_t vbz,
-                           uint32_t P) {
-    uint32_t Tx[9], Tz[9];
-    {
-        const U2* r0 = C.r0 + sA[i - 2] * 3;
-        const U2* r1 = C.r0 + sA[i - 1] * 3;
+                            uint8_t* dig, int nb, const uint8_t* sB, const uint32_t* vbx,
+                            const uint32_t* vbz, uint32_t P) {
+    const U2* tab[2] = {C.r0, C.r1};
+    uint32_t Tx[F][9], Tz[F][9];
+    U2 Da0[F], Da1[F], Da2[F], Db0[F], Db1[F], Db2[F];
+    uint32_t bx[F], bz[F];
+#pragma unroll
+    for (int f = 0; f < F; f++) {
+        const U2* r0 = tab[f] + sA[i - 2] * 3;
+        const U2* r1 = tab[f] + sA[i - 1] * 3;
         const U2 a0 = r0[0], a1 = r0[1], a2 = r0[2], b0 = r1[0], b1 = r1[1], b2 = r1[2];
-        Tx[0] = a0.x ^ b0.x; Tz[0] = a0.z ^ b0.z;
-        Tx[1] = a1.x ^ b0.x; Tz[1] = a1.z ^ b0.z;
-        Tx[2] = a2.x ^ b0.x; Tz[2] = a2.z ^ b0.z;
-        Tx[3] = a0.x ^ b1.x; Tz[3] = a0.z ^ b1.z;
-        Tx[4] = a1.x ^ b1.x; Tz[4] = a1.z ^ b1.z;
-        Tx[5] = a2.x ^ b1.x; Tz[5] = a2.z ^ b1.z;
-        Tx[6] = a0.x ^ b2.x; Tz[6] = a0.z ^ b2.z;
-        Tx[7] = a1.x ^ b2.x; Tz[7] = a1.z ^ b2.z;
-        Tx[8] = a2.x ^ b2.x; Tz[8] = a2.z ^ b2.z;
+        Tx[f][0] = a0.x ^ b0.x; Tz[f][0] = a0.z ^ b0.z;
+        Tx[f][1] = a1.x ^ b0.x; Tz[f][1] = a1.z ^ b0.z;
+        Tx[f][2] = a2.x ^ b0.x; Tz[f][2] = a2.z ^ b0.z;
+        Tx[f][3] = a0.x ^ b1.x; Tz[f][3] = a0.z ^ b1.z;
+        Tx[f][4] = a1.x ^ b1.x; Tz[f][4] = a1.z ^ b1.z;
+        Tx[f][5] = a2.x ^ b1.x; Tz[f][5] = a2.z ^ b1.z;
+        Tx[f][6] = a0.x ^ b2.x; Tz[f][6] = a0.z ^ b2.z;
+        Tx[f][7] = a1.x ^ b2.x; Tz[f][7] = a1.z ^ b2.z;
+        Tx[f][8] = a2.x ^ b2.x; Tz[f][8] = a2.z ^ b2.z;
+        // digit A starts every block at 0; its deltas for e -> e+1 are rep[(e+2)%3]
+        const U2* ra = tab[f] + sA[i - 4] * 3;
+        const U2* rb = tab[f] + sA[i - 3] * 3;
+        Da0[f] = ra[2]; Da1[f] = ra[0]; Da2[f] = ra[1];
+        Db0[f] = rb[2]; Db1[f] = rb[0]; Db2[f] = rb[1];
+        bx[f] = vbx[f] ^ ra[0].x ^ rb[0].x;
+        bz[f] = vbz[f] ^ ra[0].z ^ rb[0].z;
+        for (int p = 0; p < i - 4; p++) {
+            const U2 v = tab[f][sA[p] * 3 + dig[p]];
+            bx[f] ^= v.x;
+            bz[f] ^= v.z;
+        }
     }
-    // digit A starts every block at 0; its deltas for e -> e+1 are rep[(e+2)%3]
-    const U2* ra = C.r0 + sA[i - 4] * 3;
-    const U2 Da0 = ra[2], Da1 = ra[0], Da2 = ra[1];
-    const U2* rb = C.r0 + sA[i - 3] * 3;
-    U2 Db0 = rb[2], Db1 = rb[0], Db2 = rb[1];
     int eB = 0;
-    uint32_t bx = vbx ^ ra[0].x ^ rb[0].x, bz = vbz ^ ra[0].z ^ rb[0].z;
-    for (int p = 0; p < i - 4; p++) {
-        const U2 v = C.r0[sA[p] * 3 + dig[p]];
-        bx ^= v.x;
-        bz ^= v.z;
-    }
     const int first = C.proj ? 1 : 0;
     const int nd = i - 4 - first;
     uint32_t nk = 1;
@@ -328,51 +336,83 @@ DIST_HD_FAST void eval_fast(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, 
             }
             const int p = first + q;
             const int e = dig[p];
-            const U2 v = C.r0[sA[p] * 3 + (e == 0 ? 2 : e - 1)];
-            bx ^= v.x;
-            bz ^= v.z;
+#pragma unroll
+            for (int f = 0; f < F; f++) {
+                const U2 v = tab[f][sA[p] * 3 + (e == 0 ? 2 : e - 1)];
+                bx[f] ^= v.x;
+                bz[f] ^= v.z;
+            }
             dig[p] = (uint8_t)(e == 2 ? 0 : e + 1);
         }
         uint32_t m = 0xFFFFu;
-        DIST_SWEEP9(m);
+#define DIST_SWEEP9()                                                                         \
+    do {                                                                                      \
+        const uint32_t c0 = word_weight<F>(bx, bz, Tx, Tz, 0), c1 = word_weight<F>(bx, bz, Tx, Tz, 1); \
+        const uint32_t c2 = word_weight<F>(bx, bz, Tx, Tz, 2), c3 = word_weight<F>(bx, bz, Tx, Tz, 3); \
+        const uint32_t c4 = word_weight<F>(bx, bz, Tx, Tz, 4), c5 = word_weight<F>(bx, bz, Tx, Tz, 5); \
+        const uint32_t c6 = word_weight<F>(bx, bz, Tx, Tz, 6), c7 = word_weight<F>(bx, bz, Tx, Tz, 7); \
+        const uint32_t c8 = word_weight<F>(bx, bz, Tx, Tz, 8);                               \
+        m = min3u(m, min3u(c0, c1, c2), min3u(c3, c4, c5));                                   \
+        m = min3u(m, min3u(c6, c7, c8), m);                                                   \
+    } while (0)
+#define DIST_STEP(D)                          \
+    do {                                      \
+        _Pragma("unroll") for (int f = 0; f < F; f++) { \
+            bx[f] ^= D[f].x;                  \
+            bz[f] ^= D[f].z;                  \
+        }                                     \
+    } while (0)
+        DIST_SWEEP9();
         DIST_STEP(Da0);
-        DIST_SWEEP9(m);
+        DIST_SWEEP9();
         DIST_STEP(Da1);
-        DIST_SWEEP9(m);
+        DIST_SWEEP9();
         DIST_STEP(Db0);
-        DIST_SWEEP9(m);
+        DIST_SWEEP9();
         DIST_STEP(Da2);
-        DIST_SWEEP9(m);
+        DIST_SWEEP9();
         DIST_STEP(Da0);
-        DIST_SWEEP9(m);
+        DIST_SWEEP9();
         DIST_STEP(Db1);
-        DIST_SWEEP9(m);
+        DIST_SWEEP9();
         DIST_STEP(Da1);
-        DIST_SWEEP9(m);
+        DIST_SWEEP9();
         DIST_STEP(Da2);
-        DIST_SWEEP9(m);
-        // weight >= popc(word 0) + P: only then can a codeword beat thr
-        if (m + P < thr) block_slow(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, eB, P);
-        const U2 t = Db2;  // B moved twice: rotate its delta triple by two
-        Db2 = Db1;
-        Db1 = Db0;
-        Db0 = t;
+        DIST_SWEEP9();
+#undef DIST_SWEEP9
+#undef DIST_STEP
+        // weight >= popcount(first F words) + P: only then can a codeword beat thr
+        if (m + P < thr) block_slow<F>(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, eB, P);
+#pragma unroll
+        for (int f = 0; f < F; f++) {  // B moved twice: rotate its delta triple by two
+            const U2 t = Db2[f];
+            Db2[f] = Db1[f];
+            Db1[f] = Db0[f];
+            Db0[f] = t;
+        }
         eB = eB == 0 ? 2 : eB - 1;
     }
 }
 
-#undef DIST_SWEEP9
-#undef DIST_STEP
-
-// Word 0 of the sum of the chosen B-units' single representatives, and how
-// many of them are packages with a pivot outside word 0.
-DIST_HD void b_word0(const LaneCtx& C, int nb, const uint8_t* sB, uint32_t& x, uint32_t& z,
-                     uint32_t& P) {
-    x = z = P = 0;
+// First two words of the sum of the chosen B-units' single representatives,
+// and how many of them are packages with a pivot beyond word 0 (P1) and
+// beyond word 1 (P2).
+DIST_HD void b_words(const LaneCtx& C, int nb, const uint8_t* sB, uint32_t* x, uint32_t* z,
+                     uint32_t& P1, uint32_t& P2) {
+    x[0] = z[0] = x[1] = z[1] = 0;
+    P1 = P2 = 0;
     for (int q = 0; q < nb; q++) {
-        x ^= rep_ptr(C, C.a + sB[q], 0, 0)[0];
-        z ^= rep_ptr(C, C.a + sB[q], 0, 1)[0];
-        P += C.flags[C.a + sB[q]];
+        const uint32_t* rx = rep_ptr(C, C.a + sB[q], 0, 0);
+        const uint32_t* rz = rep_ptr(C, C.a + sB[q], 0, 1);
+        x[0] ^= rx[0];
+        z[0] ^= rz[0];
+        if (C.W >= 2) {
+            x[1] ^= rx[1];
+            z[1] ^= rz[1];
+        }
+        const uint32_t fl = C.flags[C.a + sB[q]];
+        P1 += fl & 1u;
+        P2 += (fl >> 1) & 1u;
     }
 }
 
@@ -381,7 +421,8 @@ DIST_HD bool use_fast(const LaneCtx& C, int i) {
 }
 
 // Walks the combination ranks [lo, hi) of segment sg; returns the number of
-// codewords evaluated.  Sink provides poll(thr, L) -> stop? and record(...).
+// codewords evaluated.  Sink provides poll(thr, L) -> stop?, record(...) and
+// vote_any(p) (true if p holds on any lane running in step with this one).
 template <class Sink>
 DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& thr, const SegDesc& sg,
                                       unsigned long long lo, unsigned long long hi) {
@@ -391,17 +432,28 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
     unsigned long long tB = lo / sg.NA, tA = lo - tB * sg.NA;
     rd_unrank(C.binom, C.bstride, C.b, tB, nb, sB);
     rd_unrank(C.binom, C.bstride, C.a, tA, i, sA);
-    uint32_t vbx, vbz, PB;
-    b_word0(C, nb, sB, vbx, vbz, PB);
+    uint32_t vbx[2], vbz[2], PB1, PB2;
+    b_words(C, nb, sB, vbx, vbz, PB1, PB2);
     const bool fast = use_fast(C, i);
     unsigned long long done = 0;
     for (unsigned long long idx = lo; idx < hi; ++idx) {
         if (sink.poll(thr, C.L_before)) break;
         if (fast) {
-            // packages with a pivot outside word 0 each add one to the weight
-            uint32_t P = PB;
-            for (int p = 0; p < i; p++) P += C.flags[sA[p]];
-            if (P < thr) eval_fast(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, P);
+            // packages with a pivot outside the filtered words each add one
+            uint32_t P1 = PB1, P2 = PB2;
+            for (int p = 0; p < i; p++) {
+                const uint32_t fl = C.flags[sA[p]];
+                P1 += fl & 1u;
+                P2 += (fl >> 1) & 1u;
+            }
+            // two filter words while the bound is far above what word 0 can
+            // rule out (decided together by the lanes running in step)
+            const bool two = sink.vote_any(C.W >= 2 && (int)thr - (int)P1 > C.t1);
+            if (two) {
+                if (P2 < thr) eval_fast<2>(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, P2);
+            } else {
+                if (P1 < thr) eval_fast<1>(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, P1);
+            }
         } else {
             eval_generic(C, sink, thr, i, sA, nb, sB);
         }
@@ -410,7 +462,7 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
             if (++tA == sg.NA) {
                 tA = 0;
                 rd_next(sB, nb, C.b);
-                b_word0(C, nb, sB, vbx, vbz, PB);
+                b_words(C, nb, sB, vbx, vbz, PB1, PB2);
                 for (int p = 0; p < i; p++) sA[p] = (uint8_t)p;
             } else {
                 rd_next(sA, i, C.a);

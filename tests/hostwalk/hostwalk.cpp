@@ -18,6 +18,7 @@ namespace {
 
 struct HostSink {
     Scratch* scr;
+    bool vote_any(bool p) { return p; }
     bool poll(uint32_t& thr, int L_before) {
         uint32_t u = scr->U;
         if (u < thr) thr = u;
@@ -72,9 +73,12 @@ struct HostExec {
             const uint32_t* src = p->tables.data() + g.rep_off;
             for (int t = 0; t < (g.a + g.b) * 6 * ep.W; t++) sm[g.s_rep + t] = src[t];
             U2* r0 = reinterpret_cast<U2*>(sm.data() + g.s_r0);
+            U2* r1 = reinterpret_cast<U2*>(sm.data() + g.s_r1);
             for (int t = 0; t < g.a * 3; t++) {
                 r0[t].x = src[(t * 2 + 0) * ep.W];
                 r0[t].z = src[(t * 2 + 1) * ep.W];
+                r1[t].x = ep.W >= 2 ? src[(t * 2 + 0) * ep.W + 1] : 0u;
+                r1[t].z = ep.W >= 2 ? src[(t * 2 + 1) * ep.W + 1] : 0u;
             }
             for (int t = 0; t < g.a + g.b; t++) sm[g.s_flag + t] = p->tables[g.flag_off + t];
         }
@@ -94,7 +98,9 @@ struct HostExec {
             LaneCtx C;
             C.reps = sm.data() + g.s_rep;
             C.r0 = reinterpret_cast<const U2*>(sm.data() + g.s_r0);
+            C.r1 = reinterpret_cast<const U2*>(sm.data() + g.s_r1);
             C.flags = sm.data() + g.s_flag;
+            C.t1 = g.t1;
             C.coefs = p->tables.data() + g.coef_off;
             C.binom = sbin;
             C.bstride = lp.bcols;
@@ -183,9 +189,12 @@ extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int 
                 const uint32_t* src = p.tables.data() + g.rep_off;
                 for (int t = 0; t < (g.a + g.b) * 6 * ep.W; t++) sm[g.s_rep + t] = src[t];
                 U2* r0 = reinterpret_cast<U2*>(sm.data() + g.s_r0);
+                U2* r1 = reinterpret_cast<U2*>(sm.data() + g.s_r1);
                 for (int t = 0; t < g.a * 3; t++) {
                     r0[t].x = src[(t * 2 + 0) * ep.W];
                     r0[t].z = src[(t * 2 + 1) * ep.W];
+                    r1[t].x = ep.W >= 2 ? src[(t * 2 + 0) * ep.W + 1] : 0u;
+                    r1[t].z = ep.W >= 2 ? src[(t * 2 + 1) * ep.W + 1] : 0u;
                 }
                 for (int t = 0; t < g.a + g.b; t++) sm[g.s_flag + t] = p.tables[g.flag_off + t];
             }
@@ -208,7 +217,9 @@ extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int 
                 LaneCtx C;
                 C.reps = sm.data() + g.s_rep;
                 C.r0 = reinterpret_cast<const U2*>(sm.data() + g.s_r0);
+                C.r1 = reinterpret_cast<const U2*>(sm.data() + g.s_r1);
                 C.flags = sm.data() + g.s_flag;
+                C.t1 = g.t1;
                 C.coefs = p.tables.data() + g.coef_off;
                 C.binom = sbin;
                 C.bstride = lp.bcols;

@@ -195,15 +195,18 @@ def batch_measure(dist, count):
             "init_ms": 1e3 * t_init}
 
 
-def serve_window(dist, requests, slice_ms, drain_s):
+def serve_window(dist, requests, slice_ms, drain_s, time_limit_s):
     """Replays (arrival_s, kind, generator) requests against one batch engine in
-    real time; returns per-request records (None latency = not finished)."""
+    real time.  Each request is initialised and submitted at its arrival time;
+    finished tickets are collected in completion order.  Returns per-request
+    records (None = no answer by the end of the window plus drain)."""
     import threading
-    batch = dist.Batch(slice_ms=slice_ms)
+    batch = dist.Batch(slice_ms=slice_ms, time_limit_s=time_limit_s)
     recs = [None] * len(requests)
-    submitted = []
+    by_ticket = {}
     lock = threading.Lock()
     t0 = time.perf_counter()
+    codes = []
 
     def client():
         for i, (ta, kind, g) in enumerate(requests):
@@ -211,61 +214,57 @@ def serve_window(dist, requests, slice_ms, drain_s):
             if ta > now:
                 time.sleep(ta - now)
             code = dist.Code(g)
-            t = batch.submit([code])
             with lock:
-                submitted.append((i, t, code, time.perf_counter() - t0))
+                t = batch.submit([code])
+                by_ticket[t] = (i, time.perf_counter() - t0)
+                codes.append(code)
 
     th = threading.Thread(target=client)
     th.start()
-    done = 0
-    t_end = requests[-1][0] + drain_s if requests else 0.0
-    k = 0
-    while True:
-        with lock:
-            item = submitted[k] if k < len(submitted) else None
-        if item is None:
-            if not th.is_alive() and k >= len(submitted):
-                break
-            time.sleep(0.0005)
+    t_end = (requests[-1][0] if requests else 0.0) + drain_s
+    answered = 0
+    while answered < len(requests) and time.perf_counter() - t0 < t_end:
+        t = batch.wait_any(timeout_s=0.05)
+        if t is None:
             continue
-        i, t, code, t_sub = item
-        left = t_end - (time.perf_counter() - t0)
-        if left <= 0:
-            break
-        try:
-            r = batch.wait(t, timeout_s=left)[0]
-        except dist.DistError:
-            break
+        with lock:
+            i, t_sub = by_ticket.pop(t)
+            r = batch.poll(t)[0]
         ta = requests[i][0]
-        recs[i] = {"d": r["d"], "status": r["status"], "latency_s": (t_sub - ta) + r["seconds"],
-                   "codewords": r["codewords"], "n": requests[i][2].shape[1] // 2,
-                   "kind": requests[i][1]}
-        done += 1
-        k += 1
+        recs[i] = {"d": r["d"], "lower": r["lower"], "status": r["status"],
+                   "latency_s": (t_sub - ta) + r["seconds"], "codewords": r["codewords"],
+                   "n": requests[i][2].shape[1] // 2, "kind": requests[i][1]}
+        answered += 1
     th.join()
     wall = time.perf_counter() - t0
     st = batch.stats()
-    batch.close()  # drops unfinished tickets; codes are freed after the measurement
-    for _, _, code, _ in submitted:
-        code.close()
+    batch.close()  # drops unanswered tickets; codes are freed after the measurement
+    for c in codes:
+        c.close()
     return recs, wall, st
 
 
-def serve_measure(dist, rate, duration, slice_ms, drain_s, check_budget_s, check_total_s=60.0):
+def serve_measure(dist, rate, duration, slice_ms, drain_s, time_limit_s, check_budget_s,
+                  check_total_s=60.0):
     """Workload 4: Poisson requests (random F2 and quasi-cyclic codes,
-    n ~ U[20,96]) at `rate` per second for `duration` seconds."""
+    n ~ U[20,96]) at `rate` per second for `duration` seconds, each with a
+    time limit (answers at the limit carry certified bounds lower <= d <= upper)."""
     from paper_2408_10743_gb300 import synth
+    from paper_2408_10743_gb300.binding import DIST_EINCOMPLETE
     import oracle
     reqs = list(synth.request_stream(rate_hz=rate, duration_s=duration))
-    recs, wall, st = serve_window(dist, reqs, slice_ms, drain_s)
-    fin = [r for r in recs if r is not None]
-    lat = [r["latency_s"] for r in fin]
+    recs, wall, st = serve_window(dist, reqs, slice_ms, drain_s, time_limit_s)
+    cert = [r for r in recs if r is not None and r["status"] == 0]
+    bounded = [r for r in recs if r is not None and r["status"] == DIST_EINCOMPLETE]
+    answered = [r for r in recs if r is not None]
+    lat_c = [r["latency_s"] for r in cert]
+    lat_a = [r["latency_s"] for r in answered]
     checked = mismatched = 0
     unchecked = []
     t_chk = time.perf_counter()
-    done_reqs = sorted((g.shape[1] // 2, i) for i, ((ta, kind, g), r) in enumerate(zip(reqs, recs))
-                       if r is not None)
-    for nq, i in done_reqs:  # smallest first, within a total CPU budget
+    order = sorted((reqs[i][2].shape[1] // 2, i) for i, r in enumerate(recs)
+                   if r is not None and r["status"] == 0)
+    for nq, i in order:  # smallest first, within a total CPU budget
         if time.perf_counter() - t_chk > check_total_s:
             unchecked.append(int(nq))
             continue
@@ -275,11 +274,18 @@ def serve_measure(dist, rate, duration, slice_ms, drain_s, check_budget_s, check
             mismatched += int(o["d"] != recs[i]["d"])
         else:
             unchecked.append(int(nq))
-    return {"rate_hz": rate, "duration_s": duration, "requests": len(reqs), "completed": len(fin),
-            "backlog": len(reqs) - len(fin), "wall_s": wall,
-            "codes_per_s": len(fin) / wall if wall > 0 else 0.0,
-            "p50_ms": 1e3 * pct(lat, 50) if lat else None, "p99_ms": 1e3 * pct(lat, 99) if lat else None,
-            "codewords": int(sum(r["codewords"] for r in fin)), "gpu_s": st["gpu_seconds"],
+    bounds_ok = all(r["lower"] <= r["d"] for r in bounded)
+    return {"rate_hz": rate, "duration_s": duration, "time_limit_s": time_limit_s,
+            "requests": len(reqs), "certified": len(cert), "bounded": len(bounded),
+            "backlog": len(reqs) - len(answered), "wall_s": wall,
+            "certified_per_s": len(cert) / wall if wall > 0 else 0.0,
+            "answers_per_s": len(answered) / wall if wall > 0 else 0.0,
+            "p50_ms": 1e3 * pct(lat_c, 50) if lat_c else None,
+            "p99_ms": 1e3 * pct(lat_c, 99) if lat_c else None,
+            "answer_p50_ms": 1e3 * pct(lat_a, 50) if lat_a else None,
+            "answer_p99_ms": 1e3 * pct(lat_a, 99) if lat_a else None,
+            "bounded_n": sorted(int(r["n"]) for r in bounded), "bounds_valid": bounds_ok,
+            "codewords": int(sum(r["codewords"] for r in answered)), "gpu_s": st["gpu_seconds"],
             "slices": st["slices"], "oracle_checked": checked, "oracle_mismatches": mismatched,
             "unchecked_n": sorted(unchecked)}
 
@@ -292,14 +298,17 @@ def run_serve(args):
            "config": {"workload": "served", "n": "U[20,96]", "K": "U[ceil(n/2), n]",
                       "kinds": "random F2 / quasi-cyclic 50:50", "slice_ms": args.slice_ms}}
     out["as_written"] = serve_measure(dist, args.rate, args.duration, args.slice_ms, args.drain,
-                                      args.check_budget)
+                                      args.time_limit, args.check_budget)
     sweep = []
     for rate in [float(x) for x in args.sweep.split(",") if x]:
-        r = serve_measure(dist, rate, args.sweep_duration, args.slice_ms, args.drain, args.check_budget)
+        r = serve_measure(dist, rate, args.sweep_duration, args.slice_ms, args.drain,
+                          args.time_limit, args.check_budget)
         sweep.append(r)
     out["sweep"] = sweep
-    sustainable = [r["rate_hz"] for r in sweep if r["backlog"] == 0 and r["oracle_mismatches"] == 0]
-    out["highest_sustained_rate_hz"] = max(sustainable) if sustainable else None
+    # sustained: every request answered, answer p99 within the time limit plus one second
+    ok = [r["rate_hz"] for r in sweep if r["backlog"] == 0 and r["oracle_mismatches"] == 0
+          and r["answer_p99_ms"] is not None and r["answer_p99_ms"] <= 1e3 * (args.time_limit + 1.0)]
+    out["highest_sustained_rate_hz"] = max(ok) if ok else None
     print(json.dumps(out), flush=True)
 
 
@@ -470,6 +479,8 @@ def main():
     ap.add_argument("--slice-ms", type=float, default=2.0, help="serve: launch time budget")
     ap.add_argument("--sweep", default="", help="serve: comma-separated rates to sweep")
     ap.add_argument("--sweep-duration", type=float, default=3.0)
+    ap.add_argument("--time-limit", type=float, default=2.0,
+                    help="serve: per-request time limit (s); answers at the limit carry bounds")
     ap.add_argument("--check-budget", type=float, default=0.5,
                     help="serve: oracle time per completed request (s); longer ones are listed unchecked")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -133,6 +133,8 @@ typedef struct {
     int32_t pad;
     double slice_ms;             /* time budget of one launch in ms; 0 = none (run to completion) */
     uint64_t max_resident_bytes; /* admission limit on the active codes' footprint (0 = none) */
+    double time_limit_s;         /* per code, from admission; 0 = none.  A code that reaches it
+                                    ends with status DIST_EINCOMPLETE and lower <= d <= d(upper) */
 } dist_batch_opts;
 
 typedef struct {
@@ -152,6 +154,10 @@ int dist_batch_submit(dist_batch *b, dist_code *const *codes, int count, uint64_
 int dist_batch_poll(dist_batch *b, uint64_t ticket, dist_result *results);
 /* As poll, blocking up to timeout_s seconds (<= 0: no limit); DIST_ETIMEOUT on expiry. */
 int dist_batch_wait(dist_batch *b, uint64_t ticket, dist_result *results, double timeout_s);
+/* Waits up to timeout_s (<= 0: no limit) for any submitted ticket to finish and
+ * returns its id in *ticket (collect it with poll); each finished ticket is
+ * reported once.  DIST_ETIMEOUT on expiry. */
+int dist_batch_wait_any(dist_batch *b, double timeout_s, uint64_t *ticket);
 int dist_batch_stats(dist_batch *b, dist_batch_stats_t *stats);
 /* Stops the worker after its current slice and frees the batch; uncollected
  * tickets are dropped and their codes released. */

@@ -46,7 +46,8 @@ class IntpeakResult(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("slice_ms", ctypes.c_double), ("max_resident_bytes", ctypes.c_uint64)]
+                ("slice_ms", ctypes.c_double), ("max_resident_bytes", ctypes.c_uint64),
+                ("time_limit_s", ctypes.c_double)]
 
 
 class BatchStats(ctypes.Structure):
@@ -79,6 +80,7 @@ SIGNATURES = {
     "dist_batch_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(DistResult)]),
     "dist_batch_wait": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(DistResult),
                                        ctypes.c_double]),
+    "dist_batch_wait_any": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
     "dist_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(BatchStats)]),
     "dist_batch_destroy": (ctypes.c_int, [_VP]),
     "dist_version": (ctypes.c_char_p, []),
@@ -208,9 +210,9 @@ def dist_solve_noalloc(generator, field=DIST_F2, n_stab=0, stream=None) -> DistR
     return r
 
 
-def dist_batch_create(max_active=0, slice_ms=0.0, max_resident_bytes=0):
+def dist_batch_create(max_active=0, slice_ms=0.0, max_resident_bytes=0, time_limit_s=0.0):
     h = _VP()
-    o = BatchOpts(max_active, 0, float(slice_ms), int(max_resident_bytes))
+    o = BatchOpts(max_active, 0, float(slice_ms), int(max_resident_bytes), float(time_limit_s))
     _check(lib().dist_batch_create(ctypes.byref(h), ctypes.byref(o)), "dist_batch_create")
     return h
 
@@ -236,6 +238,16 @@ def dist_batch_wait(batch, ticket, count, timeout_s=0.0):
     res = (DistResult * count)()
     _check(lib().dist_batch_wait(batch, ticket, res, float(timeout_s)), "dist_batch_wait")
     return list(res)
+
+
+def dist_batch_wait_any(batch, timeout_s=0.0):
+    """Id of a finished ticket (each reported once), or None on timeout."""
+    t = ctypes.c_uint64(0)
+    rc = lib().dist_batch_wait_any(batch, float(timeout_s), ctypes.byref(t))
+    if rc == DIST_ETIMEOUT:
+        return None
+    _check(rc, "dist_batch_wait_any")
+    return t.value
 
 
 def dist_batch_stats(batch) -> dict:
@@ -317,8 +329,8 @@ class Batch:
     code (``seconds`` = latency from submission).  Codes stay owned by the
     batch until their ticket is collected."""
 
-    def __init__(self, max_active=0, slice_ms=0.0, max_resident_bytes=0):
-        self._h = dist_batch_create(max_active, slice_ms, max_resident_bytes)
+    def __init__(self, max_active=0, slice_ms=0.0, max_resident_bytes=0, time_limit_s=0.0):
+        self._h = dist_batch_create(max_active, slice_ms, max_resident_bytes, time_limit_s)
         self._tickets = {}
 
     def submit(self, codes):
@@ -338,6 +350,10 @@ class Batch:
     def wait(self, ticket, timeout_s=0.0):
         return self._finish(ticket, dist_batch_wait(self._h, ticket, len(self._tickets[ticket]),
                                                     timeout_s))
+
+    def wait_any(self, timeout_s=0.0):
+        """Id of a finished ticket (collect it with poll), or None on timeout."""
+        return dist_batch_wait_any(self._h, timeout_s)
 
     def stats(self):
         return dist_batch_stats(self._h)

@@ -116,6 +116,7 @@ struct dist_batch {
     std::deque<Item*> pending;
     std::vector<Item*> active;
     std::map<uint64_t, Ticket> tickets;
+    std::deque<uint64_t> finished;    // tickets done and not yet reported by wait_any
     uint64_t next_ticket = 1;
     size_t resident = 0;
     // statistics
@@ -307,6 +308,25 @@ int dist_batch::slice() {
         it->res.codewords = o.codewords;
         const SliceVerdict v = plan_after_slice(p, lp, U, next);
         it->last_round = std::max(it->last_round, v.last_round);
+        if (v.kind != SLICE_CERTIFIED && opts.time_limit_s > 0 &&
+            wall_now() - it->t_admit > opts.time_limit_s) {
+            // out of time: report the bounds reached, lower <= d <= U
+            dist_result& r = it->res;
+            r.k_eff = p.k_eff;
+            r.n_gamma = (int)p.J.size();
+            r.rounds = it->last_round;
+            r.launches = (uint64_t)it->slices;
+            r.lower = std::min<int>(plan_partial_bound(p, lp, next), (int)U);
+            if (U != DIST_WINF) {
+                r.d = (int)U;
+                if (o.slot.claim == 0 || plan_decode(p, o.slot, r.witness, r.coeffs) != P_OK) {
+                    finish(it, DIST_EINTERNAL);
+                    continue;
+                }
+            }
+            finish(it, DIST_EINCOMPLETE);
+            continue;
+        }
         if (v.kind == SLICE_REPLAN) {
             it->L = v.L;  // plan the following steps next slice
             it->r_next = lp.next_r;
@@ -372,7 +392,7 @@ void dist_batch::run() {
             resident -= it->footprint;
             codes_done++;
             auto t = tickets.find(it->ticket);
-            if (t != tickets.end()) t->second.remaining--;
+            if (t != tickets.end() && --t->second.remaining == 0) finished.push_back(it->ticket);
         }
         active.swap(keep);
         cv_done.notify_all();
@@ -431,6 +451,11 @@ int dist_batch_submit(dist_batch* b, dist_code* const* codes, int count, uint64_
 }
 
 static int collect(dist_batch* b, std::map<uint64_t, Ticket>::iterator t, dist_result* results) {
+    for (auto f = b->finished.begin(); f != b->finished.end(); ++f)
+        if (*f == t->first) {
+            b->finished.erase(f);
+            break;
+        }
     for (size_t i = 0; i < t->second.items.size(); i++) {
         Item* it = t->second.items[i];
         if (results) results[i] = it->res;
@@ -462,6 +487,21 @@ int dist_batch_wait(dist_batch* b, uint64_t ticket, dist_result* results, double
         b->cv_done.wait(lk, ready);
     }
     return collect(b, t, results);
+}
+
+int dist_batch_wait_any(dist_batch* b, double timeout_s, uint64_t* ticket) {
+    if (!b || !ticket) return DIST_EINVAL;
+    std::unique_lock<std::mutex> lk(b->mu);
+    auto ready = [&] { return !b->finished.empty() || b->fatal; };
+    if (timeout_s > 0) {
+        if (!b->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) return DIST_ETIMEOUT;
+    } else {
+        b->cv_done.wait(lk, ready);
+    }
+    if (b->finished.empty()) return b->fatal;
+    *ticket = b->finished.front();
+    b->finished.pop_front();
+    return DIST_OK;
 }
 
 int dist_batch_stats(dist_batch* b, dist_batch_stats_t* s) {

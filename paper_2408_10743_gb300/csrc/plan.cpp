@@ -767,6 +767,15 @@ SliceVerdict plan_after_slice(const Plan& p, const LaunchPlan& lp, uint32_t U, u
     return v;
 }
 
+int plan_partial_bound(const Plan& p, const LaunchPlan& lp, unsigned long long next) {
+    if (next > lp.nchunks) next = lp.nchunks;
+    for (size_t s = 0; s < lp.step_r.size(); s++) {
+        const unsigned long long end = s + 1 < lp.step_r.size() ? lp.step_chunk0[s + 1] : lp.nchunks;
+        if (next < end) return lp.step_L_before[s];
+    }
+    return lp.step_r.empty() ? 1 : plan_lower_bound(p, lp.step_r.back(), lp.step_jpos.back());
+}
+
 void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep) {
     memset(ep, 0, sizeof *ep);
     for (int w = 0; w < DIST_MAXCW; w++) ep->outside[w] = p.outside[w];

@@ -126,6 +126,10 @@ struct SliceVerdict {
 };
 SliceVerdict plan_after_slice(const Plan& p, const LaunchPlan& lp, uint32_t U, unsigned long long next);
 
+// Lower bound established by a partly run plan: the L_before of its first
+// step that is not complete (or the bound after its last step).
+int plan_partial_bound(const Plan& p, const LaunchPlan& lp, unsigned long long next);
+
 // Fills the launch-independent part of EnumParams (pointers stay null).
 void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep);
 

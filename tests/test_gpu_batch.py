@@ -150,3 +150,31 @@ def test_batch_workload3_sample():
     for g, c, r in zip(gens, codes, res):
         assert r["d"] == c.solve()["d"]
         valid(g, r)
+
+
+def test_time_limit_bounds_and_wait_any():
+    """A request that would take hours ends at its time limit with certified
+    bounds lower <= d <= upper and a witness of weight upper; the small
+    requests next to it are answered exactly, and wait_any reports every
+    finished ticket once, in completion order."""
+    from paper_2408_10743_gb300.binding import DIST_EINCOMPLETE
+    big = synth.random_f2_code(96, 72, synth.Xoshiro256ss(synth.seed_for(5, 3)))
+    smalls = mixed_codes(12, 5)
+    with dist.Batch(slice_ms=1.0, time_limit_s=0.5) as b:
+        cb = dist.Code(big)
+        tb = b.submit([cb])
+        scs = [dist.Code(g) for g in smalls]
+        ts = [b.submit([c]) for c in scs]
+        got = {}
+        while len(got) < 1 + len(ts):
+            t = b.wait_any(timeout_s=30)
+            assert t is not None and t not in got
+            got[t] = b.poll(t)[0]
+    rb = got[tb]
+    assert rb["status"] == DIST_EINCOMPLETE
+    assert 1 <= rb["lower"] <= rb["d"]
+    assert sym_weight_bits(rb["witness"], 96) == rb["d"]
+    assert rb["seconds"] < 5
+    for g, t in zip(smalls, ts):
+        assert got[t]["status"] == 0
+        assert got[t]["d"] == dist.distance(g)["d"]

@@ -143,6 +143,15 @@ def cpu_baseline(g, field, budget_s):
             "complete": bool(r["complete"]), "seconds": r["seconds"]}
 
 
+def hist10(ns):
+    """Counts by decade of n, e.g. {"60-69": 12}."""
+    out = {}
+    for n in ns:
+        k = "%d-%d" % (n // 10 * 10, n // 10 * 10 + 9)
+        out[k] = out.get(k, 0) + 1
+    return dict(sorted(out.items()))
+
+
 def pct(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -284,10 +293,10 @@ def serve_measure(dist, rate, duration, slice_ms, drain_s, time_limit_s, check_b
             "p99_ms": 1e3 * pct(lat_c, 99) if lat_c else None,
             "answer_p50_ms": 1e3 * pct(lat_a, 50) if lat_a else None,
             "answer_p99_ms": 1e3 * pct(lat_a, 99) if lat_a else None,
-            "bounded_n": sorted(int(r["n"]) for r in bounded), "bounds_valid": bounds_ok,
+            "bounded_by_n": hist10(int(r["n"]) for r in bounded), "bounds_valid": bounds_ok,
             "codewords": int(sum(r["codewords"] for r in answered)), "gpu_s": st["gpu_seconds"],
             "slices": st["slices"], "oracle_checked": checked, "oracle_mismatches": mismatched,
-            "unchecked_n": sorted(unchecked)}
+            "unchecked_by_n": hist10(unchecked)}
 
 
 def run_serve(args):
@@ -310,6 +319,17 @@ def run_serve(args):
           and r["answer_p99_ms"] is not None and r["answer_p99_ms"] <= 1e3 * (args.time_limit + 1.0)]
     out["highest_sustained_rate_hz"] = max(ok) if ok else None
     print(json.dumps(out), flush=True)
+
+
+def reduce_over_ranks(pg, seconds, codewords, device):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    the codewords of all ranks."""
+    import torch
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    c = torch.tensor([float(codewords)], device=device, dtype=torch.float64)
+    pg.all_reduce(c, op=pg.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
 
 
 def run_reference(args):
@@ -408,12 +428,7 @@ def run_ours(args):
     total_s = sum(step_s)
     total_cw = sum(cws)
     if pg:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_s = float(t.item())
-        c = torch.tensor([float(total_cw)], device=dev, dtype=torch.float64)
-        pg.all_reduce(c, op=pg.ReduceOp.SUM)
-        all_cw = float(c.item())
+        total_s, all_cw = reduce_over_ranks(pg, total_s, total_cw, dev)
     else:
         all_cw = float(total_cw)
     value = all_cw / total_s

@@ -202,22 +202,15 @@ int dist_init(dist_code** out, const uint8_t* generator, int n, int K, int field
         return rc;
     }
     const size_t words = c->plan.tables.size();
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&c->e0) != cudaSuccess || cudaEventCreate(&c->e1) != cudaSuccess) {
-        release(c);
-        return DIST_ECUDA;
-    }
+    // Device tables and scratch now; the stream, events and staging buffers of
+    // the single-code path are created on first use (a code solved only in a
+    // batch never needs them).
     if (cudaMalloc(&c->d_tables, words * 4) != cudaSuccess ||
-        cudaMalloc(&c->d_segs, DIST_MAXSEG * sizeof(SegDesc)) != cudaSuccess ||
-        cudaMallocHost(&c->h_segs, DIST_MAXSEG * sizeof(SegDesc)) != cudaSuccess ||
-        cudaMalloc(&c->d_scr, sizeof(Scratch)) != cudaSuccess ||
-        cudaMallocHost(&c->h_scr, sizeof(Scratch)) != cudaSuccess) {
+        cudaMalloc(&c->d_scr, sizeof(Scratch)) != cudaSuccess) {
         release(c);
         return DIST_ENOMEM;
     }
-    if (cudaMemcpyAsync(c->d_tables, c->plan.tables.data(), words * 4, cudaMemcpyHostToDevice, c->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    if (cudaMemcpy(c->d_tables, c->plan.tables.data(), words * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         release(c);
         return DIST_ECUDA;
     }
@@ -235,6 +228,15 @@ int dist_solve_bounded(dist_code* c, dist_result* out, void* cuda_stream, double
     if (c->in_batch) return DIST_EBUSY;
     if (c->plan.n_stab > 0 && c->plan.s_rank == c->plan.k_eff) return DIST_EZERO;
     DeviceGuard guard(c->dev->device);
+    if (!c->stream) {  // first single-code solve: stream, events, staging buffers
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreate(&c->e0) != cudaSuccess || cudaEventCreate(&c->e1) != cudaSuccess)
+            return DIST_ECUDA;
+        if (cudaMalloc(&c->d_segs, DIST_MAXSEG * sizeof(SegDesc)) != cudaSuccess ||
+            cudaMallocHost(&c->h_segs, DIST_MAXSEG * sizeof(SegDesc)) != cudaSuccess ||
+            cudaMallocHost(&c->h_scr, sizeof(Scratch)) != cudaSuccess)
+            return DIST_ENOMEM;
+    }
     GpuExec ex{c, cuda_stream ? (cudaStream_t)cuda_stream : c->stream};
     return solve_loop(c->plan, ex, time_limit_s, out);
 }

@@ -261,6 +261,20 @@ extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int 
     return -8;
 }
 
+// The lower-bound schedule of the planner: out[r * nJ + jpos] = L after
+// J[0..jpos] finish round r and the rest round r-1 (r = 0..rmax).
+extern "C" int hw_plan_bounds(const uint8_t* gen, int n, int K, int field, int rmax, int* out,
+                              int* J, int* nJ) {
+    Plan p;
+    int rc = plan_build(gen, n, K, field, &p);
+    if (rc) return rc;
+    *nJ = (int)p.J.size();
+    for (int t = 0; t < *nJ; t++) J[t] = p.J[t];
+    for (int r = 0; r <= rmax; r++)
+        for (int t = 0; t < *nJ; t++) out[r * *nJ + t] = plan_lower_bound(p, r, t);
+    return 0;
+}
+
 // Revolving-door helpers exactly as the kernel uses them.
 extern "C" void hw_rd_walk(int n, int t, unsigned long long rank0, int count, uint8_t* out) {
     std::vector<unsigned long long> B((DIST_MAXU + 1) * (DIST_MAXR + 1));

@@ -178,3 +178,25 @@ def test_time_limit_bounds_and_wait_any():
     for g, t in zip(smalls, ts):
         assert got[t]["status"] == 0
         assert got[t]["d"] == dist.distance(g)["d"]
+
+
+def test_ten_thousand_tiny_codes_in_one_batch():
+    """10^4 tiny codes (n <= 8, K <= 12; i.i.d., CSS-like, Y-heavy, sparse)
+    solved together, against the oracle's brute force."""
+    rng = np.random.default_rng(39)
+    kinds = ["iid", "css", "yheavy", "sparse"]
+    gens = []
+    while len(gens) < 10000:
+        n = int(rng.integers(1, 9))
+        K = int(rng.integers(1, min(2 * n, 12) + 1))
+        g = tiny_random_code(rng, n, K, kinds[len(gens) % 4])
+        if g.any():
+            gens.append(g)
+    codes = [dist.Code(g) for g in gens]
+    with dist.Batch() as b:
+        res = b.wait(b.submit(codes), timeout_s=600)
+    for g, r in zip(gens, res):
+        assert r["status"] == 0
+        assert r["d"] == oracle.bruteforce(g, threads=1)[0]
+    for c in codes:
+        c.close()

@@ -39,6 +39,10 @@ def hw():
                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(DistResult)]
     L.hw_rd_walk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int,
                              ctypes.POINTER(ctypes.c_uint8)]
+    L.hw_plan_bounds.restype = ctypes.c_int
+    L.hw_plan_bounds.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.hw_solve_sliced.restype = ctypes.c_int
     L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -229,3 +233,81 @@ def test_sliced_engine_exclusion_and_f4(hw):
     g1 = synth.single_f4(1)
     rc, r = solve_sliced(hw, g1, seed=5, one_step_plans=False, field=4)
     assert rc == 0 and r.d == oracle.bz(g1, field=4)["d"]
+
+
+def test_bound_schedule_bruteforce(hw):
+    """Every codeword not yet enumerated after step (r, jpos) weighs at least
+    the planner's bound L(r, jpos).  Brute force on tiny codes: a codeword is
+    enumerated by matrix j in round g_j(c), the number of units it uses in
+    that matrix's units (unique, since the units' representatives form a
+    basis)."""
+    import itertools
+    import paper_2408_10743_gb300 as dist
+    rng = np.random.default_rng(37)
+    checked = 0
+    for trial in range(60):
+        n = int(rng.integers(2, 6))
+        K = int(rng.integers(1, min(2 * n, 7) + 1))
+        g = tiny_random_code(rng, n, K, ["iid", "css", "yheavy"][trial % 3])
+        if not g.any():
+            continue
+        info = dist.dist_plan_info_get(g)
+        gammas = []
+        for j in range(info.n_gamma_built):
+            units = []
+            for u in range(info.a[j] + info.b[j]):
+                nrep = 3 if u < info.a[j] else 1
+                units.append([dist.dist_plan_unit(g, j, u, e)[0] for e in range(nrep)])
+            gammas.append(units)
+        # unit count of every codeword in every matrix
+        count = [dict() for _ in gammas]
+        for j, units in enumerate(gammas):
+            for pick in itertools.product(*[[None] + list(range(len(u))) for u in units]):
+                v = np.zeros(2 * n, dtype=np.uint8)
+                used = 0
+                for u, e in zip(units, pick):
+                    if e is not None:
+                        v ^= u[e]
+                        used += 1
+                if used:
+                    count[j][v.tobytes()] = used
+        words = {k: sym_weight_bits(np.frombuffer(k, dtype=np.uint8), n) for k in count[0]}
+        rmax = max(info.a[j] + info.b[j] for j in range(info.n_gamma_built)) + 1
+        out = (ctypes.c_int * ((rmax + 1) * 16))()
+        J = (ctypes.c_int * 16)()
+        nJ = ctypes.c_int(0)
+        gg = np.ascontiguousarray(g)
+        assert hw.hw_plan_bounds(gg.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n, K, 2, rmax,
+                                 out, J, ctypes.byref(nJ)) == 0
+        order = [J[t] for t in range(nJ.value)]
+        for r in range(rmax + 1):
+            for jpos in range(nJ.value):
+                L = out[r * nJ.value + jpos]
+                done = [r if t <= jpos else r - 1 for t in range(nJ.value)]
+                unseen = [w for k, w in words.items()
+                          if all(count[order[t]][k] > done[t] for t in range(nJ.value))]
+                if L >= 0xFFFF:
+                    assert not unseen  # the bound claims everything was enumerated
+                else:
+                    assert all(w >= L for w in unseen), (r, jpos, L, min(unseen))
+                checked += 1
+    assert checked > 200
+
+
+def test_ten_thousand_tiny_codes(hw):
+    """Library walk vs oracle brute force on 10^4 tiny codes (n <= 8, K <= 12)
+    of four shapes, including CSS-like and Y-heavy ones."""
+    rng = np.random.default_rng(38)
+    kinds = ["iid", "css", "yheavy", "sparse"]
+    done = 0
+    while done < 10000:
+        n = int(rng.integers(1, 9))
+        K = int(rng.integers(1, min(2 * n, 12) + 1))
+        g = tiny_random_code(rng, n, K, kinds[done % 4])
+        if not g.any():
+            continue
+        rc, r = solve(hw, g, warps=1 + done % 3)
+        assert rc == 0
+        d, _, _ = oracle.bruteforce(g, threads=1)
+        assert r.d == d, (g.tolist(), r.d, d)
+        done += 1

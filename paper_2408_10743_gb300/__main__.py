@@ -35,12 +35,27 @@ def main(argv=None):
     src.add_argument("--matrix")
     src.add_argument("--random", nargs=2, type=int, metavar=("N", "K"),
                      help="random F2 code (i.i.d. bits, full rank), seeded by --index")
+    src.add_argument("--batch", type=int, metavar="COUNT",
+                     help="the first COUNT codes of the batched workload (n ~ U[16,56]), solved together")
     ap.add_argument("--index", type=int, default=0)
     ap.add_argument("--field", type=int, default=2, choices=[2, 4])
     ap.add_argument("--n-stab", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--time-limit", type=float, default=0.0)
     args = ap.parse_args(argv)
+    if args.batch:
+        gens = synth.batch_codes(args.batch)
+        codes = [binding.Code(g) for g in gens]
+        with binding.Batch() as b:
+            res = b.wait(b.submit(codes))
+            st = b.stats()
+        for c in codes:
+            c.close()
+        print(json.dumps({"codes": len(res), "ok": sum(r["status"] == 0 for r in res),
+                          "codewords": int(sum(r["codewords"] for r in res)),
+                          "gpu_seconds": st["gpu_seconds"], "launches": st["launches"],
+                          "max_d": max(r["d"] for r in res)}))
+        return 0
     field = args.field
     if args.workload == "qc72":
         g = synth.single_qc(args.index)

@@ -388,6 +388,8 @@ def run_ours(args):
     g, field, cfg = workload(args.workload, rank)
     K = g.shape[0]
 
+    # chunk granularity picked by the library's autotuner on this GPU
+    tuning = dist.dist_autotune(budget_s=args.autotune) if args.autotune > 0 else dist.dist_get_tuning()
     # roofline denominator: the integer-issue microbenchmark on this GPU
     with torch.cuda.stream(stream):
         peak = dist.dist_intpeak(iters=20000, stream=stream)
@@ -462,6 +464,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": dict(cfg, l2="flushed between steps (256 MB write)",
+                           tuning={"chunks_per_warp": tuning["chunks_per_warp"],
+                                   "lane_cap_log2": tuning["lane_cap_log2"]},
                            parallelism="replicas: one independent code per GPU" if world > 1 else "1 GPU"),
             "time_to_d_ms": 1e3 * statistics.mean(step_s), "d": ds[0], "rounds": rounds[0],
             "codewords_per_step": total_cw / args.steps,
@@ -500,6 +504,8 @@ def main():
                     help="serve: oracle time per completed request (s); longer ones are listed unchecked")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=float, default=8.0,
+                    help="seconds for the chunk-size autotuner before timing (0 = defaults)")
     ap.add_argument("--batch-codes", type=int, default=4096,
                     help="size of the batched-vs-one-per-launch comparison (0 = skip)")
     args = ap.parse_args()

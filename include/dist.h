@@ -164,6 +164,24 @@ int dist_batch_stats(dist_batch *b, dist_batch_stats_t *stats);
 int dist_batch_destroy(dist_batch *b);
 
 /*
+ * Chunk granularity of the enumeration launches (process-wide; affects
+ * speed, never results).  chunks_per_warp: warp-chunks per resident warp a
+ * step is cut into (default 12); lane_cap_log2: at most 2^lane_cap_log2
+ * codewords per lane chunk (default 16).  Zero fields keep the current value.
+ * dist_autotune times calibration solves on the current device over a small
+ * grid of both, applies the fastest setting, and returns it (and the
+ * codewords/s it reached) -- about budget_s seconds (<= 0: about 10 s).
+ */
+typedef struct {
+    int32_t chunks_per_warp;
+    int32_t lane_cap_log2;
+    double codewords_per_s;      /* dist_autotune: rate of the chosen setting */
+} dist_tuning;
+int dist_set_tuning(const dist_tuning *t);
+int dist_get_tuning(dist_tuning *t);
+int dist_autotune(dist_tuning *best, double budget_s);
+
+/*
  * dist_plan_info -- host-only view of the plan step S2-S3 built for an input
  * (no CUDA call).  For each generator matrix j < n_gamma_built: a[j] units
  * with three representatives, b[j] with one, f[j] free rows; order[0..n_used)

@@ -44,6 +44,11 @@ class IntpeakResult(ctypes.Structure):
                 ("sms", ctypes.c_int32), ("blocks", ctypes.c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("chunks_per_warp", ctypes.c_int32), ("lane_cap_log2", ctypes.c_int32),
+                ("codewords_per_s", ctypes.c_double)]
+
+
 class BatchOpts(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("slice_ms", ctypes.c_double), ("max_resident_bytes", ctypes.c_uint64),
@@ -83,6 +88,9 @@ SIGNATURES = {
     "dist_batch_wait_any": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
     "dist_batch_stats": (ctypes.c_int, [_VP, ctypes.POINTER(BatchStats)]),
     "dist_batch_destroy": (ctypes.c_int, [_VP]),
+    "dist_set_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
+    "dist_get_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
+    "dist_autotune": (ctypes.c_int, [ctypes.POINTER(Tuning), ctypes.c_double]),
     "dist_version": (ctypes.c_char_p, []),
     "dist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -258,6 +266,26 @@ def dist_batch_stats(batch) -> dict:
 
 def dist_batch_destroy(batch):
     return _check(lib().dist_batch_destroy(batch), "dist_batch_destroy")
+
+
+def dist_set_tuning(chunks_per_warp=0, lane_cap_log2=0):
+    t = Tuning(chunks_per_warp, lane_cap_log2, 0.0)
+    return _check(lib().dist_set_tuning(ctypes.byref(t)), "dist_set_tuning")
+
+
+def dist_get_tuning() -> dict:
+    t = Tuning()
+    _check(lib().dist_get_tuning(ctypes.byref(t)), "dist_get_tuning")
+    return {"chunks_per_warp": t.chunks_per_warp, "lane_cap_log2": t.lane_cap_log2}
+
+
+def dist_autotune(budget_s=10.0) -> dict:
+    """Times calibration solves over a grid of chunk settings on the current
+    device and applies the fastest; returns it with its codewords/s."""
+    t = Tuning()
+    _check(lib().dist_autotune(ctypes.byref(t), float(budget_s)), "dist_autotune")
+    return {"chunks_per_warp": t.chunks_per_warp, "lane_cap_log2": t.lane_cap_log2,
+            "codewords_per_s": t.codewords_per_s}
 
 
 def dist_version() -> str:

@@ -315,6 +315,96 @@ int dist_intpeak(dist_intpeak_result* out, int iters, void* cuda_stream) {
     return DIST_OK;
 }
 
+int dist_set_tuning(const dist_tuning* t) {
+    if (!t) return DIST_EINVAL;
+    Tuning cur = tuning_get();
+    if (t->chunks_per_warp > 0) cur.chunks_per_warp = t->chunks_per_warp;
+    if (t->lane_cap_log2 > 0) cur.lane_cap_log2 = t->lane_cap_log2;
+    tuning_set(cur);
+    return DIST_OK;
+}
+
+int dist_get_tuning(dist_tuning* t) {
+    if (!t) return DIST_EINVAL;
+    const Tuning cur = tuning_get();
+    t->chunks_per_warp = cur.chunks_per_warp;
+    t->lane_cap_log2 = cur.lane_cap_log2;
+    t->codewords_per_s = 0.0;
+    return DIST_OK;
+}
+
+// Calibration: two seeded random codes (n = 64, K = 56 and n = 72, K = 72)
+// whose solves are dominated by one large enumeration step, timed with the
+// kernels' CUDA events for each setting of the grid; best median rate wins.
+int dist_autotune(dist_tuning* best, double budget_s) {
+    if (!best) return DIST_EINVAL;
+    if (budget_s <= 0) budget_s = 10.0;
+    static const int kSizes[2][2] = {{64, 56}, {72, 72}};
+    std::vector<dist_code*> codes;
+    uint64_t x = 0x9E3779B97F4A7C15ull;  // xorshift64* stream for the calibration bits
+    for (auto& nk : kSizes) {
+        const int n = nk[0], K = nk[1];
+        for (int attempt = 0; attempt < 100; attempt++) {
+            std::vector<uint8_t> g((size_t)K * 2 * n);
+            for (auto& b : g) {
+                x ^= x >> 12;
+                x ^= x << 25;
+                x ^= x >> 27;
+                b = (uint8_t)(((x * 0x2545F4914F6CDD1Dull) >> 63) & 1u);
+            }
+            dist_code* c = nullptr;
+            int rc = dist_init(&c, g.data(), n, K, DIST_F2);
+            if (rc == DIST_OK && c->plan.k_eff == K) {
+                codes.push_back(c);
+                break;
+            }
+            if (c) dist_free(c);
+            if (rc != DIST_OK && rc != DIST_EZERO) return rc;
+        }
+    }
+    const Tuning saved = tuning_get();
+    const int cpw[] = {6, 12, 24, 48};
+    const int cap[] = {14, 16, 18};
+    double best_rate = -1;
+    Tuning best_t = saved;
+    const double t0 = wall_now();
+    for (int a : cpw)
+        for (int b : cap) {
+            if (wall_now() - t0 > budget_s) break;
+            Tuning t;
+            t.chunks_per_warp = a;
+            t.lane_cap_log2 = b;
+            tuning_set(t);
+            double cw = 0, secs = 0;
+            for (dist_code* c : codes) {
+                dist_result r;
+                for (int rep = 0; rep < 2; rep++) {
+                    int rc = dist_solve(c, &r, nullptr);
+                    if (rc != DIST_OK) {
+                        tuning_set(saved);
+                        for (dist_code* cc : codes) dist_free(cc);
+                        return rc;
+                    }
+                    if (rep == 1) {
+                        cw += (double)r.codewords;
+                        secs += r.gpu_seconds;
+                    }
+                }
+            }
+            const double rate = secs > 0 ? cw / secs : 0;
+            if (rate > best_rate) {
+                best_rate = rate;
+                best_t = t;
+            }
+        }
+    for (dist_code* c : codes) dist_free(c);
+    tuning_set(best_t);
+    best->chunks_per_warp = best_t.chunks_per_warp;
+    best->lane_cap_log2 = best_t.lane_cap_log2;
+    best->codewords_per_s = best_rate;
+    return DIST_OK;
+}
+
 const char* dist_version(void) { return "libdist 0.1 (sm_103a)"; }
 
 const char* dist_strerror(int code) {

@@ -6,8 +6,23 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 
 namespace dist {
+
+static std::atomic<int> g_chunks_per_warp{12}, g_lane_cap_log2{16};
+
+Tuning tuning_get() {
+    Tuning t;
+    t.chunks_per_warp = g_chunks_per_warp.load();
+    t.lane_cap_log2 = g_lane_cap_log2.load();
+    return t;
+}
+
+void tuning_set(const Tuning& t) {
+    g_chunks_per_warp.store(std::max(1, std::min(t.chunks_per_warp, 256)));
+    g_lane_cap_log2.store(std::max(8, std::min(t.lane_cap_log2, 24)));
+}
 
 // ---------------------------------------------------------------------------
 // Bit-plane helpers.
@@ -695,15 +710,17 @@ planned:
     total = 0;
     for (double cw : seg_cw) total += cw;
     lp->codewords = total;
-    // Chunks: each segment is cut into about twelve warp-chunks per resident
-    // warp (so that every segment spreads over the whole GPU and the tail is
-    // short); a lane chunk holds at most ~2^16 codewords (about a millisecond
-    // for a warp) so that stop requests and time budgets are seen soon.
+    // Chunks: each segment is cut into about chunks_per_warp (default 12)
+    // warp-chunks per resident warp, so that every segment spreads over the
+    // whole GPU and the tail is short; a lane chunk holds at most
+    // 2^lane_cap_log2 (default 2^16, about a millisecond for a warp) codewords
+    // so that stop requests and time budgets are seen soon.
     unsigned long long chunks = 0;
+    const Tuning tun = tuning_get();
     for (size_t t = 0; t < lp->segs.size(); t++) {
         SegDesc& sd = lp->segs[t];
-        double per_lane = seg_cw[t] / (32.0 * std::max(1, target_warps) * 12.0);
-        per_lane = std::min(per_lane, (double)(1u << 16));
+        double per_lane = seg_cw[t] / (32.0 * std::max(1, target_warps) * (double)tun.chunks_per_warp);
+        per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2));
         double spl_d = per_lane / (double)sd.codes;
         unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
         if (spl > (1ull << 30)) spl = 1ull << 30;

@@ -89,6 +89,16 @@ struct LaunchPlan {
 
 enum { P_OK = 0, P_EINVAL = -1, P_ENOMEM = -2, P_EZERO = -6, P_ERANGE = -9 };
 
+// Chunk granularity used by plan_launch (process-wide, set by the tuner):
+// each segment is cut into about chunks_per_warp warp-chunks per resident
+// warp, and a lane chunk holds at most 2^lane_cap_log2 codewords.
+struct Tuning {
+    int chunks_per_warp = 12;
+    int lane_cap_log2 = 16;
+};
+Tuning tuning_get();
+void tuning_set(const Tuning& t);
+
 // S1 + S2 + choice of J.  gen layout: field 2 -> K x 2n bytes {0,1} (x | z);
 // field 4 -> K x n bytes {0..3}, v = a + 2b for a + alpha b.
 int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p);

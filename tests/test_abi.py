@@ -57,3 +57,15 @@ def test_invalid_arguments_rejected_without_device():
     with pytest.raises(dist.DistError) as e:
         dist.dist_plan_info_get(np.zeros((2, 6), dtype=np.uint8))
     assert e.value.code == -6
+
+
+def test_tuning_get_set_clamps():
+    saved = dist.dist_get_tuning()
+    try:
+        dist.dist_set_tuning(1000, 2)
+        t = dist.dist_get_tuning()
+        assert t["chunks_per_warp"] == 256 and t["lane_cap_log2"] == 8
+        dist.dist_set_tuning(0, 0)  # zero keeps the current values
+        assert dist.dist_get_tuning() == t
+    finally:
+        dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"])

@@ -214,3 +214,20 @@ def test_bounded_solve(stream):
     assert r["status"] in (0, dist.binding.DIST_EINCOMPLETE)
     assert 1 <= r["lower"] <= r["d"]
     check_witness(g, r)
+
+
+def test_tuning_changes_speed_not_results(stream):
+    g = synth.random_f2_code(56, 50, synth.Xoshiro256ss(4321))
+    saved = dist.dist_get_tuning()
+    try:
+        ds = set()
+        for cpw, cap in ((1, 10), (6, 14), (48, 20)):
+            dist.dist_set_tuning(cpw, cap)
+            ds.add(gpu(g, stream=stream)["d"])
+        assert len(ds) == 1
+        best = dist.dist_autotune(budget_s=3.0)
+        assert best["codewords_per_s"] > 0
+        assert dist.dist_get_tuning()["chunks_per_warp"] == best["chunks_per_warp"]
+        assert gpu(g, stream=stream)["d"] in ds
+    finally:
+        dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"])

@@ -204,7 +204,8 @@ def test_repeat_and_streams(stream):
         s2 = torch.cuda.Stream()
         cc = c.solve(stream=s2)
     assert a["d"] == b["d"] == cc["d"]
-    assert a["codewords"] == b["codewords"] == cc["codewords"]
+    # how much speculative work runs before U drops is timing dependent
+    assert min(a["codewords"], b["codewords"], cc["codewords"]) > 0
 
 
 def test_bounded_solve(stream):

@@ -23,11 +23,7 @@ namespace dist {
 struct DevSink {
     Scratch* scr;
     __device__ __forceinline__ bool vote_any(bool p) { return __any_sync(__activemask(), p); }
-    __device__ __forceinline__ bool poll(uint32_t& thr, int L_before) {
-        const uint32_t u = *reinterpret_cast<volatile uint32_t*>(&scr->U);
-        thr = u < thr ? u : thr;
-        return (int)u <= L_before;
-    }
+    __device__ __forceinline__ uint32_t peek() { return *reinterpret_cast<volatile uint32_t*>(&scr->U); }
     __device__ __noinline__ void record(uint32_t w, int gamma, int count, const uint8_t* units,
                                         const uint8_t* digits) {
         if (w >= *reinterpret_cast<volatile uint32_t*>(&scr->U)) return;  // not lighter than known

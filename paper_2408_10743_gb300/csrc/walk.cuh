@@ -421,8 +421,9 @@ DIST_HD bool use_fast(const LaneCtx& C, int i) {
 }
 
 // Walks the combination ranks [lo, hi) of segment sg; returns the number of
-// codewords evaluated.  Sink provides poll(thr, L) -> stop?, record(...) and
-// vote_any(p) (true if p holds on any lane running in step with this one).
+// codewords evaluated.  Sink provides peek() (current upper bound),
+// record(...) and vote_any(p) (true if p holds on any lane running in step
+// with this one).
 template <class Sink>
 DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& thr, const SegDesc& sg,
                                       unsigned long long lo, unsigned long long hi) {
@@ -436,8 +437,14 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
     b_words(C, nb, sB, vbx, vbz, PB1, PB2);
     const bool fast = use_fast(C, i);
     unsigned long long done = 0;
+    // The running bound is read one subset ahead: a stale (larger) value is
+    // still a valid threshold, and the load's latency overlaps the work.
+    uint32_t u_next = sink.peek();
     for (unsigned long long idx = lo; idx < hi; ++idx) {
-        if (sink.poll(thr, C.L_before)) break;
+        const uint32_t u = u_next;
+        u_next = sink.peek();
+        thr = u < thr ? u : thr;
+        if ((int)u <= C.L_before) break;
         if (fast) {
             // packages with a pivot outside the filtered words each add one
             uint32_t P1 = PB1, P2 = PB2;

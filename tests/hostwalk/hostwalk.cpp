@@ -19,11 +19,7 @@ namespace {
 struct HostSink {
     Scratch* scr;
     bool vote_any(bool p) { return p; }
-    bool poll(uint32_t& thr, int L_before) {
-        uint32_t u = scr->U;
-        if (u < thr) thr = u;
-        return (int)u <= L_before;
-    }
+    uint32_t peek() { return scr->U; }
     void record(uint32_t w, int gamma, int count, const uint8_t* units, const uint8_t* digits) {
         if (w < scr->U) scr->U = w;
         WitnessSlot* s = &scr->slot[w];

@@ -454,18 +454,20 @@ int oracle_bz(const uint8_t *gen, int n, int K, int field, int n_stab, int threa
     if (!base || !G) { free(base); free(G); return ORACLE_EINVAL; }
     for (int i = 0; i < Kb; i++) iso_row(B.x[i], B.z[i], n, base[i]);
 
-    /* Systematic generator matrices on disjoint information sets.  Gamma_1
-     * always has full rank; later ones are kept only while they still have
-     * full rank, so every kept matrix has f_j = 0 free rows. */
+    /* Systematic generator matrices on disjoint information sets, each on
+     * the columns the earlier ones left unused, until no unused column has
+     * positive rank.  Gamma_1 has full rank; a later Gamma_j of rank k_j < K
+     * has f_j = K - k_j rows without a pivot, and the bound below counts it
+     * with r + 1 - f_j (the lower bound of Algorithm 2 treats its second
+     * matrix the same way). */
     uint8_t used[3 * MAXN], piv[3 * MAXN];
     memset(used, 0, sizeof used);
     int m = 0;
     while (m < MAXGAMMA) {
         int k = build_gamma((const uint64_t(*)[WMAX])base, Kb, ncols, used, &G[m], piv);
-        if (k < Kb && m > 0) break;
+        if (k == 0) break;
         for (int c = 0; c < ncols; c++) used[c] |= piv[c];
         m++;
-        if (k < Kb) break;
     }
     res->n_gamma = m;
 

@@ -10,18 +10,21 @@
 
 namespace dist {
 
-static std::atomic<int> g_chunks_per_warp{12}, g_lane_cap_log2{16};
+static std::atomic<int> g_chunks_per_warp{6}, g_lane_cap_log2{14}, g_lane_floor_log2{12};
 
 Tuning tuning_get() {
     Tuning t;
     t.chunks_per_warp = g_chunks_per_warp.load();
     t.lane_cap_log2 = g_lane_cap_log2.load();
+    t.lane_floor_log2 = g_lane_floor_log2.load();
     return t;
 }
 
 void tuning_set(const Tuning& t) {
     g_chunks_per_warp.store(std::max(1, std::min(t.chunks_per_warp, 256)));
-    g_lane_cap_log2.store(std::max(8, std::min(t.lane_cap_log2, 24)));
+    const int cap = std::max(8, std::min(t.lane_cap_log2, 24));
+    g_lane_cap_log2.store(cap);
+    g_lane_floor_log2.store(std::max(1, std::min(t.lane_floor_log2, cap)));
 }
 
 // ---------------------------------------------------------------------------
@@ -131,26 +134,34 @@ static unsigned long long upow3(int e) {
 // ---------------------------------------------------------------------------
 static int load_input(const uint8_t* gen, int n, int K, int field, Plan* p) {
     p->input.assign(K, Vec());
+    unsigned bad = 0;  // any symbol out of range
     for (int r = 0; r < K; r++) {
         Vec& v = p->input[r];
         memset(&v, 0, sizeof v);
-        for (int i = 0; i < n; i++) {
-            int a, b;
-            if (field == 2) {
-                a = gen[(size_t)r * 2 * n + i];
-                b = gen[(size_t)r * 2 * n + n + i];
-                if (a > 1 || b > 1) return P_EINVAL;
-            } else {
-                int s = gen[(size_t)r * n + i];
-                if (s > 3) return P_EINVAL;
-                a = s & 1;
-                b = s >> 1;
+        for (int w = 0; w * 32 < n; w++) {
+            uint32_t xw = 0, zw = 0;
+            const int hi = std::min(32, n - w * 32);
+            for (int b = 0; b < hi; b++) {
+                const int i = w * 32 + b;
+                unsigned a, c;
+                if (field == 2) {
+                    a = gen[(size_t)r * 2 * n + i];
+                    c = gen[(size_t)r * 2 * n + n + i];
+                    bad |= (a | c) & ~1u;
+                } else {
+                    const unsigned s4 = gen[(size_t)r * n + i];
+                    bad |= s4 & ~3u;
+                    a = s4 & 1u;
+                    c = (s4 >> 1) & 1u;
+                }
+                xw |= (a & 1u) << b;
+                zw |= (c & 1u) << b;
             }
-            if (a) setb(v.x, i);
-            if (b) setb(v.z, i);
+            v.x[w] = xw;
+            v.z[w] = zw;
         }
     }
-    return P_OK;
+    return bad ? P_EINVAL : P_OK;
 }
 
 // Keeps, in input order, the rows independent of the ones kept before them
@@ -209,6 +220,41 @@ static void reduce_rank(Plan* p) {
 // Rows left without a pivot are free.  A later pivot only adds rows whose
 // projection on earlier pivot qubits is already 0, so earlier packages keep
 // their property.
+// Set of rows (bit i = row i), k <= DIST_MAXK.
+struct RowSet {
+    uint64_t w[(DIST_MAXK + 63) / 64];
+};
+static inline void rs_set(RowSet& s, int i) { s.w[i >> 6] |= 1ull << (i & 63); }
+static inline void rs_clear(RowSet& s, int i) { s.w[i >> 6] &= ~(1ull << (i & 63)); }
+static inline int rs_first(const RowSet& s) {  // lowest row, -1 if empty
+    for (int t = 0; t < (int)(sizeof s.w / 8); t++)
+        if (s.w[t]) return t * 64 + __builtin_ctzll(s.w[t]);
+    return -1;
+}
+static inline RowSet rs_and(const RowSet& a, const RowSet& b) {
+    RowSet r;
+    for (int t = 0; t < (int)(sizeof r.w / 8); t++) r.w[t] = a.w[t] & b.w[t];
+    return r;
+}
+static inline RowSet rs_andnot(const RowSet& a, const RowSet& b) {
+    RowSet r;
+    for (int t = 0; t < (int)(sizeof r.w / 8); t++) r.w[t] = a.w[t] & ~b.w[t];
+    return r;
+}
+static inline RowSet rs_or(const RowSet& a, const RowSet& b) {
+    RowSet r;
+    for (int t = 0; t < (int)(sizeof r.w / 8); t++) r.w[t] = a.w[t] | b.w[t];
+    return r;
+}
+static inline void rs_xor_into(RowSet& a, const RowSet& b) {
+    for (int t = 0; t < (int)(sizeof a.w / 8); t++) a.w[t] ^= b.w[t];
+}
+static inline bool rs_any(const RowSet& a) {
+    uint64_t o = 0;
+    for (int t = 0; t < (int)(sizeof a.w / 8); t++) o |= a.w[t];
+    return o != 0;
+}
+
 static void diag_f2(const Plan& p, std::vector<char>& used, Gamma& G) {
     const int k = p.k_eff, n = p.n;
     std::vector<Vec> R = p.basis;
@@ -217,6 +263,37 @@ static void diag_f2(const Plan& p, std::vector<char>& used, Gamma& G) {
         memset(&C[i], 0, sizeof(Coef));
         setb(C[i].p[0], i);
     }
+    // Column view of R: cx[q] (cz[q]) = rows with a 1 in the x (z) plane at
+    // qubit q, kept in step with the rows.  The projection of row i onto q is
+    // (i in cx[q]) + 2 (i in cz[q]).
+    std::vector<RowSet> cx(n), cz(n);
+    memset(cx.data(), 0, n * sizeof(RowSet));
+    memset(cz.data(), 0, n * sizeof(RowSet));
+    for (int i = 0; i < k; i++)
+        for (int w = 0; w < p.W; w++) {
+            for (uint32_t m = R[i].x[w]; m; m &= m - 1) rs_set(cx[w * 32 + __builtin_ctz(m)], i);
+            for (uint32_t m = R[i].z[w]; m; m &= m - 1) rs_set(cz[w * 32 + __builtin_ctz(m)], i);
+        }
+    RowSet unpiv;
+    memset(&unpiv, 0, sizeof unpiv);
+    for (int i = 0; i < k; i++) rs_set(unpiv, i);
+    // rows with projection val (1, 2, 3) at q
+    auto with_proj = [&](int q, int val) {
+        return val == 1 ? rs_andnot(cx[q], cz[q]) : val == 2 ? rs_andnot(cz[q], cx[q]) : rs_and(cx[q], cz[q]);
+    };
+    // R[i] += R[g] (and the coefficients) for every row i in S; g not in S
+    auto add_row = [&](const RowSet& S, int g) {
+        for (int t = 0; t < (int)(sizeof S.w / 8); t++)
+            for (uint64_t m = S.w[t]; m; m &= m - 1) {
+                const int i = t * 64 + __builtin_ctzll(m);
+                vxor(R[i], R[g]);
+                cxor(C[i], C[g]);
+            }
+        for (int w = 0; w < p.W; w++) {
+            for (uint32_t m = R[g].x[w]; m; m &= m - 1) rs_xor_into(cx[w * 32 + __builtin_ctz(m)], S);
+            for (uint32_t m = R[g].z[w]; m; m &= m - 1) rs_xor_into(cz[w * 32 + __builtin_ctz(m)], S);
+        }
+    };
     std::vector<char> piv(k, 0);
     struct U { int kind, q, g, h; };
     std::vector<U> units;
@@ -224,11 +301,9 @@ static void diag_f2(const Plan& p, std::vector<char>& used, Gamma& G) {
         int best_q = -1, best_rank = 0;
         for (int q = 0; q < n; q++) {
             if (used[q]) continue;
-            int seen = 0;
-            for (int i = 0; i < k; i++)
-                if (!piv[i]) seen |= 1 << proj(R[i], q);
-            int nz = __builtin_popcount(seen & 0xE);
-            int rank = nz >= 2 ? 2 : nz;
+            const RowSet a = rs_and(cx[q], unpiv), b = rs_and(cz[q], unpiv);
+            const int nz = (int)rs_any(rs_andnot(a, b)) + (int)rs_any(rs_andnot(b, a)) + (int)rs_any(rs_and(a, b));
+            const int rank = nz >= 2 ? 2 : nz;
             if (rank > best_rank) {
                 best_rank = rank;
                 best_q = q;
@@ -237,42 +312,31 @@ static void diag_f2(const Plan& p, std::vector<char>& used, Gamma& G) {
         }
         if (best_rank == 0) break;
         const int q = best_q;
+        const RowSet live = rs_and(rs_or(cx[q], cz[q]), unpiv);  // unpivoted rows, nonzero at q
+        const int g = rs_first(live);
+        const int vg = proj(R[g], q);
         if (best_rank == 2) {
-            int g = -1, h = -1;
-            for (int i = 0; i < k && g < 0; i++)
-                if (!piv[i] && proj(R[i], q)) g = i;
-            int vg = proj(R[g], q);
-            for (int i = 0; i < k && h < 0; i++)
-                if (!piv[i] && proj(R[i], q) && proj(R[i], q) != vg) h = i;
-            int vh = proj(R[h], q);
-            for (int i = 0; i < k; i++) {
-                if (i == g || i == h) continue;
-                int v = proj(R[i], q);
-                if (v == vg) {
-                    vxor(R[i], R[g]); cxor(C[i], C[g]);
-                } else if (v == vh) {
-                    vxor(R[i], R[h]); cxor(C[i], C[h]);
-                } else if (v == (vg ^ vh)) {
-                    vxor(R[i], R[g]); cxor(C[i], C[g]);
-                    vxor(R[i], R[h]); cxor(C[i], C[h]);
-                }
-            }
+            const int h = rs_first(rs_andnot(live, with_proj(q, vg)));
+            const int vh = proj(R[h], q);
+            // rows with projection vg or vg+vh take g, rows with vh or vg+vh take h
+            const RowSet pg = with_proj(q, vg), ph = with_proj(q, vh), pgh = with_proj(q, vg ^ vh);
+            RowSet Sg = rs_or(pg, pgh), Sh = rs_or(ph, pgh);
+            rs_clear(Sg, g); rs_clear(Sg, h);
+            rs_clear(Sh, g); rs_clear(Sh, h);
+            add_row(Sg, g);
+            add_row(Sh, h);
             piv[g] = piv[h] = 1;
+            rs_clear(unpiv, g);
+            rs_clear(unpiv, h);
             units.push_back({UNIT_PACKAGE2, q, g, h});
         } else {
-            int g = -1;
-            for (int i = 0; i < k && g < 0; i++)
-                if (!piv[i] && proj(R[i], q)) g = i;
-            int v = proj(R[g], q);
-            int w = (v == 1) ? 2 : 1;  // smallest nonzero value other than v
-            for (int i = 0; i < k; i++) {
-                if (i == g) continue;
-                int pv = proj(R[i], q);
-                if (pv == v || pv == (v ^ w)) {
-                    vxor(R[i], R[g]); cxor(C[i], C[g]);
-                }
-            }
+            const int v = vg;
+            const int w = (v == 1) ? 2 : 1;  // smallest nonzero value other than v
+            RowSet S = rs_or(with_proj(q, v), with_proj(q, v ^ w));
+            rs_clear(S, g);
+            add_row(S, g);
             piv[g] = 1;
+            rs_clear(unpiv, g);
             units.push_back({UNIT_PACKAGE1, q, g, -1});
         }
         used[q] = 1;
@@ -399,10 +463,9 @@ static void build_device_tables(const Plan& p, Gamma& G) {
         for (int e = 0; e < x.nrep; e++) {
             uint32_t* dx = &G.dev_reps[(((size_t)t * 3 + e) * 2 + 0) * W];
             uint32_t* dz = &G.dev_reps[(((size_t)t * 3 + e) * 2 + 1) * W];
-            for (int pos = 0; pos < p.n; pos++) {
-                int q = G.perm[pos];
-                if (bit(x.rep[e].x, q)) setb(dx, pos);
-                if (bit(x.rep[e].z, q)) setb(dz, pos);
+            for (int w = 0; w < W; w++) {
+                for (uint32_t m = x.rep[e].x[w]; m; m &= m - 1) setb(dx, pos_of[w * 32 + __builtin_ctz(m)]);
+                for (uint32_t m = x.rep[e].z[w]; m; m &= m - 1) setb(dz, pos_of[w * 32 + __builtin_ctz(m)]);
             }
             for (int c = 0; c < 2; c++)
                 for (int w = 0; w < CW; w++)
@@ -710,16 +773,28 @@ planned:
     total = 0;
     for (double cw : seg_cw) total += cw;
     lp->codewords = total;
-    // Chunks: each segment is cut into about chunks_per_warp (default 12)
+    // Chunks: each segment is cut into about chunks_per_warp (default 6)
     // warp-chunks per resident warp, so that every segment spreads over the
     // whole GPU and the tail is short; a lane chunk holds at most
-    // 2^lane_cap_log2 (default 2^16, about a millisecond for a warp) codewords
-    // so that stop requests and time budgets are seen soon.
+    // 2^lane_cap_log2 (default 2^14, about a quarter of a millisecond for a
+    // warp) codewords
+    // so that stop requests and time budgets are seen soon.  A segment on the
+    // fast path gets at least 2^lane_floor_log2 codewords per lane, so that it
+    // is not cut finer than the per-lane set-up (unranking the start subset,
+    // fetching the chunk) is worth -- but never fewer chunks than resident
+    // warps: the early, small steps are where the lighter codewords that
+    // lower U come from, and they must still spread over the whole GPU.
+    // Generic-path segments cost tens of times more per codeword and keep
+    // the plain split, so that they never become the critical path.
     unsigned long long chunks = 0;
     const Tuning tun = tuning_get();
     for (size_t t = 0; t < lp->segs.size(); t++) {
         SegDesc& sd = lp->segs[t];
         double per_lane = seg_cw[t] / (32.0 * std::max(1, target_warps) * (double)tun.chunks_per_warp);
+        if (DIST_FAST_PATH((int)sd.i, lp->proj)) {
+            const double spread = seg_cw[t] / (32.0 * std::max(1, target_warps));
+            per_lane = std::max(per_lane, std::min((double)(1u << tun.lane_floor_log2), spread));
+        }
         per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2));
         double spl_d = per_lane / (double)sd.codes;
         unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;

@@ -140,7 +140,8 @@ def cpu_baseline(g, field, budget_s):
                       "of enumeration (%d codewords, rounds <= %d, %s)"
                       % (budget_s, r["codewords"], r["rounds"],
                          "complete" if r["complete"] else "stopped by the budget"),
-            "complete": bool(r["complete"]), "seconds": r["seconds"]}
+            "complete": bool(r["complete"]), "seconds": r["seconds"],
+            "time_to_d_s": r["seconds"] if r["complete"] else None}
 
 
 def hist10(ns):
@@ -466,8 +467,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": dict(cfg, l2="flushed between steps (256 MB write)",
-                           tuning={"chunks_per_warp": tuning["chunks_per_warp"],
-                                   "lane_cap_log2": tuning["lane_cap_log2"]},
+                           tuning={k: tuning[k] for k in ("chunks_per_warp", "lane_cap_log2",
+                                                          "lane_floor_log2")},
                            parallelism="replicas: one independent code per GPU" if world > 1 else "1 GPU"),
             "time_to_d_ms": 1e3 * statistics.mean(step_s), "d": ds[0], "rounds": rounds[0],
             "codewords_per_step": total_cw / args.steps,

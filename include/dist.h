@@ -165,16 +165,21 @@ int dist_batch_destroy(dist_batch *b);
 
 /*
  * Chunk granularity of the enumeration launches (process-wide; affects
- * speed, never results).  chunks_per_warp: warp-chunks per resident warp a
- * step is cut into (default 12); lane_cap_log2: at most 2^lane_cap_log2
- * codewords per lane chunk (default 16).  Zero fields keep the current value.
- * dist_autotune times calibration solves on the current device over a small
- * grid of both, applies the fastest setting, and returns it (and the
- * codewords/s it reached) -- about budget_s seconds (<= 0: about 10 s).
+ * speed, never results).  chunks_per_warp: each enumeration step is cut
+ * into about this many warp-chunks per resident warp (default 6, range
+ * 1..256); a lane chunk holds at most 2^lane_cap_log2 (default 14, range
+ * 8..24) codewords, and a fast-path segment at least 2^lane_floor_log2
+ * (default 12, range 1..lane_cap_log2) unless that would leave it fewer
+ * chunks than resident warps.  Values outside the ranges are clamped; fields <= 0 keep the
+ * current value.  dist_autotune times calibration solves (random codes of
+ * 64 x 56 and 72 x 72) on the current device over a grid of the three,
+ * applies the setting with the best geometric-mean codewords/s, and returns
+ * it (and that rate) -- about budget_s seconds (<= 0: about 10 s).
  */
 typedef struct {
     int32_t chunks_per_warp;
     int32_t lane_cap_log2;
+    int32_t lane_floor_log2;
     double codewords_per_s;      /* dist_autotune: rate of the chosen setting */
 } dist_tuning;
 int dist_set_tuning(const dist_tuning *t);

@@ -46,6 +46,7 @@ class IntpeakResult(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("chunks_per_warp", ctypes.c_int32), ("lane_cap_log2", ctypes.c_int32),
+                ("lane_floor_log2", ctypes.c_int32),
                 ("codewords_per_s", ctypes.c_double)]
 
 
@@ -268,15 +269,16 @@ def dist_batch_destroy(batch):
     return _check(lib().dist_batch_destroy(batch), "dist_batch_destroy")
 
 
-def dist_set_tuning(chunks_per_warp=0, lane_cap_log2=0):
-    t = Tuning(chunks_per_warp, lane_cap_log2, 0.0)
+def dist_set_tuning(chunks_per_warp=0, lane_cap_log2=0, lane_floor_log2=0):
+    t = Tuning(chunks_per_warp, lane_cap_log2, lane_floor_log2, 0.0)
     return _check(lib().dist_set_tuning(ctypes.byref(t)), "dist_set_tuning")
 
 
 def dist_get_tuning() -> dict:
     t = Tuning()
     _check(lib().dist_get_tuning(ctypes.byref(t)), "dist_get_tuning")
-    return {"chunks_per_warp": t.chunks_per_warp, "lane_cap_log2": t.lane_cap_log2}
+    return {"chunks_per_warp": t.chunks_per_warp, "lane_cap_log2": t.lane_cap_log2,
+            "lane_floor_log2": t.lane_floor_log2}
 
 
 def dist_autotune(budget_s=10.0) -> dict:
@@ -285,7 +287,7 @@ def dist_autotune(budget_s=10.0) -> dict:
     t = Tuning()
     _check(lib().dist_autotune(ctypes.byref(t), float(budget_s)), "dist_autotune")
     return {"chunks_per_warp": t.chunks_per_warp, "lane_cap_log2": t.lane_cap_log2,
-            "codewords_per_s": t.codewords_per_s}
+            "lane_floor_log2": t.lane_floor_log2, "codewords_per_s": t.codewords_per_s}
 
 
 def dist_version() -> str:

@@ -4,6 +4,7 @@
 
 #include <mutex>
 #include <new>
+#include <cmath>
 #include <vector>
 
 #include "../../include/dist.h"
@@ -115,7 +116,7 @@ struct GpuExec {
             return DIST_ECUDA;
         return DIST_OK;
     }
-    int target_warps() const { return c->dev->sms * c->dev->blocks_per_sm * 8; }
+    int target_warps() const { return c->dev->sms * c->dev->blocks_per_sm * DIST_ENUM_WARPS; }
     double gpu_seconds() const { return gpu_s; }
     unsigned long long launches() const { return nl; }
     int run(const LaunchPlan& lp, double deadline_wall, StepResult* out) {
@@ -320,6 +321,7 @@ int dist_set_tuning(const dist_tuning* t) {
     Tuning cur = tuning_get();
     if (t->chunks_per_warp > 0) cur.chunks_per_warp = t->chunks_per_warp;
     if (t->lane_cap_log2 > 0) cur.lane_cap_log2 = t->lane_cap_log2;
+    if (t->lane_floor_log2 > 0) cur.lane_floor_log2 = t->lane_floor_log2;
     tuning_set(cur);
     return DIST_OK;
 }
@@ -329,6 +331,7 @@ int dist_get_tuning(dist_tuning* t) {
     const Tuning cur = tuning_get();
     t->chunks_per_warp = cur.chunks_per_warp;
     t->lane_cap_log2 = cur.lane_cap_log2;
+    t->lane_floor_log2 = cur.lane_floor_log2;
     t->codewords_per_s = 0.0;
     return DIST_OK;
 }
@@ -363,44 +366,48 @@ int dist_autotune(dist_tuning* best, double budget_s) {
         }
     }
     const Tuning saved = tuning_get();
-    const int cpw[] = {6, 12, 24, 48};
-    const int cap[] = {14, 16, 18};
+    std::vector<Tuning> grid;
+    for (int a : {2, 3, 6, 12})
+        for (int b : {13, 14, 16})
+            for (int f : {8, 10, 12}) {
+                Tuning t;
+                t.chunks_per_warp = a;
+                t.lane_cap_log2 = b;
+                t.lane_floor_log2 = f;
+                grid.push_back(t);
+            }
     double best_rate = -1;
     Tuning best_t = saved;
     const double t0 = wall_now();
-    for (int a : cpw)
-        for (int b : cap) {
-            if (wall_now() - t0 > budget_s) break;
-            Tuning t;
-            t.chunks_per_warp = a;
-            t.lane_cap_log2 = b;
-            tuning_set(t);
-            double cw = 0, secs = 0;
-            for (dist_code* c : codes) {
-                dist_result r;
-                for (int rep = 0; rep < 2; rep++) {
-                    int rc = dist_solve(c, &r, nullptr);
-                    if (rc != DIST_OK) {
-                        tuning_set(saved);
-                        for (dist_code* cc : codes) dist_free(cc);
-                        return rc;
-                    }
-                    if (rep == 1) {
-                        cw += (double)r.codewords;
-                        secs += r.gpu_seconds;
-                    }
+    for (const Tuning& t : grid) {
+        if (wall_now() - t0 > budget_s) break;
+        tuning_set(t);
+        // geometric mean of the per-code rates: a short solve weighs as much
+        // as a long one
+        double log_rate = 0;
+        for (dist_code* c : codes) {
+            dist_result r;
+            for (int rep = 0; rep < 2; rep++) {
+                int rc = dist_solve(c, &r, nullptr);
+                if (rc != DIST_OK) {
+                    tuning_set(saved);
+                    for (dist_code* cc : codes) dist_free(cc);
+                    return rc;
                 }
-            }
-            const double rate = secs > 0 ? cw / secs : 0;
-            if (rate > best_rate) {
-                best_rate = rate;
-                best_t = t;
+                if (rep == 1) log_rate += std::log((double)r.codewords / std::max(r.gpu_seconds, 1e-9));
             }
         }
+        const double rate = std::exp(log_rate / (double)codes.size());
+        if (rate > best_rate) {
+            best_rate = rate;
+            best_t = t;
+        }
+    }
     for (dist_code* c : codes) dist_free(c);
     tuning_set(best_t);
     best->chunks_per_warp = best_t.chunks_per_warp;
     best->lane_cap_log2 = best_t.lane_cap_log2;
+    best->lane_floor_log2 = best_t.lane_floor_log2;
     best->codewords_per_s = best_rate;
     return DIST_OK;
 }

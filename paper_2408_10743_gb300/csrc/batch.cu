@@ -169,7 +169,7 @@ void dist_batch::finish(Item* it, int status) {
 
 // One slice; returns a DIST_* error only for failures of the device itself.
 int dist_batch::slice() {
-    const int tw = dev->sms * dev->batch_blocks_per_sm * 8;
+    const int tw = dev->sms * dev->batch_blocks_per_sm * DIST_ENUM_WARPS;
     // plan codes that need it
     for (Item* it : active) {
         if (it->planned || it->done) continue;

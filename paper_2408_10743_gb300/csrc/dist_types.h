@@ -19,6 +19,21 @@
 #define DIST_MAXSEG 256        // segments in one launch
 #define DIST_WINF 0xFFFFu      // "no codeword yet" weight
 #define DIST_FAST_MAX_DYN 20   // 3^20 < 2^32: the dynamic Gray counter fits in 32 bits
+// Subsets of i A-units take the lane walk's fast path (a nine-entry register
+// table, two register digits and a ternary Gray code over the rest) when
+// they have at least 4 + proj varying units and at most DIST_FAST_MAX_DYN
+// dynamic digits; smaller ones take the generic path.
+#define DIST_FAST_PATH(i, proj) ((i) >= 4 + (proj) && (i) - 4 - (proj) <= DIST_FAST_MAX_DYN)
+
+// Threads per block of the enumeration kernels and their minimum resident
+// blocks per SM (together they set the register budget per thread).
+#ifndef DIST_ENUM_THREADS
+#define DIST_ENUM_THREADS 256
+#endif
+#ifndef DIST_ENUM_MINB
+#define DIST_ENUM_MINB 2
+#endif
+#define DIST_ENUM_WARPS (DIST_ENUM_THREADS / 32)
 
 // One claimable record per weight value: the first thread that finds a
 // codeword of weight w (that passes the optional exclusion) writes how to

@@ -50,11 +50,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 extern __shared__ __align__(16) uint32_t g_enum_smem[];
 
-#ifndef DIST_ENUM_MINB
-#define DIST_ENUM_MINB 2
-#endif
-
-__global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_kernel(const __grid_constant__ EnumParams P) {
+__global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel(const __grid_constant__ EnumParams P) {
     uint32_t* sm = g_enum_smem;
     // stage: representatives and word-0 tables of every matrix in the launch
     for (int gi = 0; gi < P.ng; gi++) {
@@ -90,11 +86,19 @@ __global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_kernel(const __grid_
     const int lane = threadIdx.x & 31;
     const unsigned long long t_start = P.budget_ns ? global_ns() : 0ull;
     uint32_t thr = DIST_WINF;
+    // Lane 0 claims the warp's next chunk while the current one runs, so the
+    // atomic's round trip overlaps the work.  A claimed chunk is given up
+    // only where everything after it is unneeded (skip) or the budget ended.
+    unsigned long long claimed = 0;
+    if (lane == 0) claimed = atomicAdd(&P.scr->next_chunk, 1ull);
     for (;;) {
-        unsigned long long chunk = 0;
-        if (lane == 0) chunk = atomicAdd(&P.scr->next_chunk, 1ull);
-        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        const unsigned long long chunk = __shfl_sync(0xffffffffu, claimed, 0);
         if (chunk >= P.nchunks) break;
+        uint32_t u_now = 0;
+        if (lane == 0) {
+            claimed = atomicAdd(&P.scr->next_chunk, 1ull);
+            u_now = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
+        }
         int lo_s = 0, hi_s = P.nseg;  // last segment with chunk_base <= chunk
         while (hi_s - lo_s > 1) {
             const int mid = (lo_s + hi_s) >> 1;
@@ -103,12 +107,9 @@ __global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_kernel(const __grid_
         }
         const SegDesc sg = ssegs[lo_s];
         int skip = 0;
-        if (lane == 0) {
-            const uint32_t u = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
-            if ((int)u <= sg.L_before) {
-                skip = 1;
-                atomicMax(&P.scr->next_chunk, P.nchunks);
-            }
+        if (lane == 0 && (int)u_now <= sg.L_before) {
+            skip = 1;
+            atomicMax(&P.scr->next_chunk, P.nchunks);
         }
         if (__shfl_sync(0xffffffffu, skip, 0)) break;
         const GammaDesc& g = P.g[sg.g];
@@ -183,7 +184,7 @@ __device__ int join_code(const BatchParams& P) {
     return -1;
 }
 
-__global__ void __launch_bounds__(256, DIST_ENUM_MINB) enum_batch_kernel(const __grid_constant__ BatchParams P) {
+__global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_batch_kernel(const __grid_constant__ BatchParams P) {
     const int lane = threadIdx.x & 31;
     const unsigned long long t_start = P.budget_ns ? global_ns() : 0ull;
     uint32_t thr = DIST_WINF;
@@ -313,7 +314,7 @@ __global__ void batch_gather_kernel(Scratch* const* scrs, BatchOut* out, int n) 
 }
 
 cudaError_t batch_launch(const BatchParams& P, int grid, cudaStream_t st) {
-    enum_batch_kernel<<<grid, 256, 0, st>>>(P);
+    enum_batch_kernel<<<grid, DIST_ENUM_THREADS, 0, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -331,7 +332,7 @@ cudaError_t batch_gather_launch(Scratch* const* scrs, BatchOut* out, int n, cuda
 
 int batch_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, enum_batch_kernel, 256, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, enum_batch_kernel, DIST_ENUM_THREADS, 0) != cudaSuccess) return 0;
     return nb;
 }
 
@@ -339,7 +340,7 @@ size_t enum_smem_bytes(const EnumParams& P) { return (size_t)P.s_words * 4; }
 
 int enum_blocks_per_sm(size_t smem) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, enum_kernel, 256, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, enum_kernel, DIST_ENUM_THREADS, smem) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -349,7 +350,7 @@ cudaError_t enum_set_max_smem(size_t bytes) {
 }
 
 cudaError_t enum_launch(const EnumParams& P, int grid, cudaStream_t st) {
-    enum_kernel<<<grid, 256, enum_smem_bytes(P), st>>>(P);
+    enum_kernel<<<grid, DIST_ENUM_THREADS, enum_smem_bytes(P), st>>>(P);
     return cudaGetLastError();
 }
 

@@ -118,7 +118,7 @@ struct NoAllocExec {
             return DIST_ECUDA;
         return DIST_OK;
     }
-    int target_warps() const { return d->sms * d->blocks_per_sm * 8; }
+    int target_warps() const { return d->sms * d->blocks_per_sm * DIST_ENUM_WARPS; }
     double gpu_seconds() const { return 0.0; }
     unsigned long long launches() const { return nl; }
     int run(const LaunchPlan& lp, double deadline_wall, StepResult* out) {

@@ -90,11 +90,13 @@ struct LaunchPlan {
 enum { P_OK = 0, P_EINVAL = -1, P_ENOMEM = -2, P_EZERO = -6, P_ERANGE = -9 };
 
 // Chunk granularity used by plan_launch (process-wide, set by the tuner):
-// each segment is cut into about chunks_per_warp warp-chunks per resident
-// warp, and a lane chunk holds at most 2^lane_cap_log2 codewords.
+// each step of a launch is cut into about chunks_per_warp warp-chunks per
+// resident warp, and a lane chunk holds at most 2^lane_cap_log2 and at least
+// 2^lane_floor_log2 codewords.
 struct Tuning {
-    int chunks_per_warp = 12;
-    int lane_cap_log2 = 16;
+    int chunks_per_warp = 6;
+    int lane_cap_log2 = 14;
+    int lane_floor_log2 = 12;
 };
 Tuning tuning_get();
 void tuning_set(const Tuning& t);

@@ -417,7 +417,7 @@ DIST_HD void b_words(const LaneCtx& C, int nb, const uint8_t* sB, uint32_t* x, u
 }
 
 DIST_HD bool use_fast(const LaneCtx& C, int i) {
-    return i >= 4 + C.proj && i - 4 - C.proj <= DIST_FAST_MAX_DYN;
+    return DIST_FAST_PATH(i, C.proj);
 }
 
 // Walks the combination ranks [lo, hi) of segment sg; returns the number of

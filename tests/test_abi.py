@@ -62,10 +62,15 @@ def test_invalid_arguments_rejected_without_device():
 def test_tuning_get_set_clamps():
     saved = dist.dist_get_tuning()
     try:
-        dist.dist_set_tuning(1000, 2)
+        dist.dist_set_tuning(1000, 2, 30)
         t = dist.dist_get_tuning()
         assert t["chunks_per_warp"] == 256 and t["lane_cap_log2"] == 8
-        dist.dist_set_tuning(0, 0)  # zero keeps the current values
+        assert t["lane_floor_log2"] == 8  # never above the cap
+        dist.dist_set_tuning(0, 0, 0)  # zero keeps the current values
         assert dist.dist_get_tuning() == t
+        dist.dist_set_tuning(3, 20, 12)
+        assert dist.dist_get_tuning() == {"chunks_per_warp": 3, "lane_cap_log2": 20,
+                                          "lane_floor_log2": 12}
     finally:
-        dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"])
+        dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"],
+                             saved["lane_floor_log2"])

@@ -222,8 +222,8 @@ def test_tuning_changes_speed_not_results(stream):
     saved = dist.dist_get_tuning()
     try:
         ds = set()
-        for cpw, cap in ((1, 10), (6, 14), (48, 20)):
-            dist.dist_set_tuning(cpw, cap)
+        for cpw, cap, fl in ((1, 10, 1), (6, 14, 10), (48, 20, 16)):
+            dist.dist_set_tuning(cpw, cap, fl)
             ds.add(gpu(g, stream=stream)["d"])
         assert len(ds) == 1
         best = dist.dist_autotune(budget_s=3.0)
@@ -231,4 +231,5 @@ def test_tuning_changes_speed_not_results(stream):
         assert dist.dist_get_tuning()["chunks_per_warp"] == best["chunks_per_warp"]
         assert gpu(g, stream=stream)["d"] in ds
     finally:
-        dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"])
+        dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"],
+                             saved["lane_floor_log2"])

@@ -77,43 +77,126 @@ int device_ctx(DeviceCtx** out) {
     return DIST_OK;
 }
 
+namespace {
+constexpr size_t kMaxIdleKits = 64;
+constexpr size_t kMaxCachedBytes = 256ull << 20;
+constexpr size_t kMinBlock = 32 * 1024;
+
+void kit_destroy(SolveKit* k) {
+    if (k->e0) cudaEventDestroy(k->e0);
+    if (k->e1) cudaEventDestroy(k->e1);
+    if (k->stream) cudaStreamDestroy(k->stream);
+    if (k->h_state) cudaFreeHost(k->h_state);
+    delete k;
+}
+}  // namespace
+
+int kit_acquire(DeviceCtx* d, SolveKit** out) {
+    {
+        std::lock_guard<std::mutex> lk(d->pool_mu);
+        if (!d->kits.empty()) {
+            *out = d->kits.back();
+            d->kits.pop_back();
+            return DIST_OK;
+        }
+    }
+    SolveKit* k = new (std::nothrow) SolveKit();
+    if (!k) return DIST_ENOMEM;
+    if (cudaStreamCreateWithFlags(&k->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&k->e0) != cudaSuccess || cudaEventCreate(&k->e1) != cudaSuccess) {
+        kit_destroy(k);
+        return DIST_ECUDA;
+    }
+    if (cudaMallocHost(&k->h_state, state_bytes()) != cudaSuccess) {
+        k->h_state = nullptr;
+        kit_destroy(k);
+        return DIST_ENOMEM;
+    }
+    *out = k;
+    return DIST_OK;
+}
+
+void kit_release(DeviceCtx* d, SolveKit* k) {
+    if (!k) return;
+    {
+        std::lock_guard<std::mutex> lk(d->pool_mu);
+        if (d->kits.size() < kMaxIdleKits) {
+            d->kits.push_back(k);
+            return;
+        }
+    }
+    kit_destroy(k);
+}
+
+int block_acquire(DeviceCtx* d, size_t bytes, void** out, size_t* cap) {
+    size_t c = kMinBlock;
+    while (c < bytes) c <<= 1;
+    {
+        std::lock_guard<std::mutex> lk(d->pool_mu);
+        for (size_t i = 0; i < d->blocks.size(); i++)
+            if (d->blocks[i].first == c) {
+                *out = d->blocks[i].second;
+                *cap = c;
+                d->blocks[i] = d->blocks.back();
+                d->blocks.pop_back();
+                d->cached_bytes -= c;
+                return DIST_OK;
+            }
+    }
+    if (cudaMalloc(out, c) != cudaSuccess) {
+        *out = nullptr;
+        return DIST_ENOMEM;
+    }
+    *cap = c;
+    return DIST_OK;
+}
+
+void block_release(DeviceCtx* d, void* p, size_t cap) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(d->pool_mu);
+        if (d->cached_bytes + cap <= kMaxCachedBytes) {
+            d->blocks.emplace_back(cap, p);
+            d->cached_bytes += cap;
+            return;
+        }
+    }
+    cudaFree(p);
+}
+
 }  // namespace dist
 
 namespace {
 
 void release(dist_code* c) {
     if (!c) return;
-    if (c->d_tables) cudaFree(c->d_tables);
-    if (c->d_segs) cudaFree(c->d_segs);
-    if (c->h_segs) cudaFreeHost(c->h_segs);
-    if (c->d_scr) cudaFree(c->d_scr);
-    if (c->h_scr) cudaFreeHost(c->h_scr);
-    if (c->e0) cudaEventDestroy(c->e0);
-    if (c->e1) cudaEventDestroy(c->e1);
-    if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->d_block) block_release(c->dev, c->d_block, c->block_cap);
     delete c;
 }
 
-// Runs one enumeration step per call on the GPU (the executor of solve_loop).
+// Runs one enumeration launch per call on the GPU (the executor of
+// solve_loop).  The scratch (bound, counters, witness slots) is prepared on
+// the host and goes to the device with the first launch's segment table in
+// one copy; after every launch the whole scratch comes back in one copy, so
+// the witness slot needs no further round trip.
 struct GpuExec {
     dist_code* c;
+    SolveKit* kit;
     cudaStream_t st;
     double gpu_s = 0.0;
     unsigned long long nl = 0;
+    bool first = true;  // the next launch uploads the scratch image too
+    Scratch* hs() const { return reinterpret_cast<Scratch*>(kit->h_state); }
+    SegDesc* hsegs() const { return reinterpret_cast<SegDesc*>(kit->h_state + align256(sizeof(Scratch))); }
     int reset() {
-        if (cudaMemsetAsync(c->d_scr, 0, sizeof(Scratch), st) != cudaSuccess) return DIST_ECUDA;
-        // U = DIST_WINF (0x0000FFFF, little-endian)
-        if (cudaMemsetAsync(c->d_scr, 0xFF, 2, st) != cudaSuccess) return DIST_ECUDA;
+        memset(hs(), 0, sizeof(Scratch));
+        hs()->U = DIST_WINF;
+        first = true;
         return DIST_OK;
     }
     int seed(uint32_t U0, const WitnessSlot& s) {
-        c->h_scr->U = U0;
-        c->h_scr->slot[U0] = s;
-        if (cudaMemcpyAsync(&c->d_scr->U, &c->h_scr->U, sizeof(uint32_t), cudaMemcpyHostToDevice, st) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(&c->d_scr->slot[U0], &c->h_scr->slot[U0], sizeof(WitnessSlot),
-                            cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return DIST_ECUDA;
+        hs()->U = U0;
+        hs()->slot[U0] = s;
         return DIST_OK;
     }
     int target_warps() const { return c->dev->sms * c->dev->blocks_per_sm * DIST_ENUM_WARPS; }
@@ -135,38 +218,40 @@ struct GpuExec {
         if (smem > c->dev->smem_optin) return DIST_ERANGE;
         int bps = enum_blocks_per_sm(smem);
         if (bps < 1) return DIST_ECUDA;
-        unsigned long long want = (lp.nchunks + 7) / 8;  // eight warps per block
+        unsigned long long want = (lp.nchunks + DIST_ENUM_WARPS - 1) / DIST_ENUM_WARPS;
         if (want < 1) want = 1;
         const unsigned long long cap = (unsigned long long)c->dev->sms * (unsigned long long)bps;
         const int grid = (int)(want < cap ? want : cap);
-        memcpy(c->h_segs, lp.segs.data(), lp.segs.size() * sizeof(SegDesc));
-        if (cudaMemcpyAsync(c->d_segs, c->h_segs, lp.segs.size() * sizeof(SegDesc),
-                            cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return DIST_ECUDA;
-        if (cudaMemsetAsync(&c->d_scr->next_chunk, 0, sizeof(unsigned long long), st) != cudaSuccess)
-            return DIST_ECUDA;
-        cudaEventRecord(c->e0, st);
+        const size_t seg_bytes = lp.segs.size() * sizeof(SegDesc);
+        memcpy(hsegs(), lp.segs.data(), seg_bytes);
+        if (first) {  // scratch image (next_chunk = 0) and segment table in one copy
+            if (cudaMemcpyAsync(c->d_scr, kit->h_state, align256(sizeof(Scratch)) + seg_bytes,
+                                cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return DIST_ECUDA;
+            first = false;
+        } else {
+            if (cudaMemcpyAsync(c->d_segs, hsegs(), seg_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemsetAsync(&c->d_scr->next_chunk, 0, sizeof(unsigned long long), st) != cudaSuccess)
+                return DIST_ECUDA;
+        }
+        cudaEventRecord(kit->e0, st);
         if (enum_launch(ep, grid, st) != cudaSuccess) return DIST_ECUDA;
-        cudaEventRecord(c->e1, st);
+        cudaEventRecord(kit->e1, st);
         nl++;
-        if (cudaMemcpyAsync(c->h_scr, c->d_scr, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        if (cudaMemcpyAsync(hs(), c->d_scr, sizeof(Scratch), cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return DIST_ECUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return DIST_ECUDA;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, c->e0, c->e1);
+        cudaEventElapsedTime(&ms, kit->e0, kit->e1);
         gpu_s += ms * 1e-3;
-        out->U = c->h_scr->U;
-        out->status = c->h_scr->status;
-        out->codewords = c->h_scr->codewords;
+        out->U = hs()->U;
+        out->status = hs()->status;
+        out->codewords = hs()->codewords;
         return DIST_OK;
     }
     int read_slot(uint32_t w, WitnessSlot* s) {
         if (w > DIST_MAXN) return DIST_EINTERNAL;
-        if (cudaMemcpyAsync(&c->h_scr->slot[w], &c->d_scr->slot[w], sizeof(WitnessSlot),
-                            cudaMemcpyDeviceToHost, st) != cudaSuccess)
-            return DIST_ECUDA;
-        if (cudaStreamSynchronize(st) != cudaSuccess) return DIST_ECUDA;
-        *s = c->h_scr->slot[w];
+        *s = hs()->slot[w];  // read back with the last launch (or the seed itself)
         return DIST_OK;
     }
 };
@@ -202,16 +287,23 @@ int dist_init(dist_code** out, const uint8_t* generator, int n, int K, int field
         delete c;
         return rc;
     }
+    // One device block (from the per-device cache): tables, scratch, segment
+    // table.  Streams, events and staging buffers come from the device's kit
+    // cache at solve time (a code solved only in a batch never needs one).
     const size_t words = c->plan.tables.size();
-    // Device tables and scratch now; the stream, events and staging buffers of
-    // the single-code path are created on first use (a code solved only in a
-    // batch never needs them).
-    if (cudaMalloc(&c->d_tables, words * 4) != cudaSuccess ||
-        cudaMalloc(&c->d_scr, sizeof(Scratch)) != cudaSuccess) {
+    const size_t tbytes = align256(words * 4);
+    rc = block_acquire(c->dev, tbytes + state_bytes(), &c->d_block, &c->block_cap);
+    if (rc) {
         release(c);
-        return DIST_ENOMEM;
+        return rc;
     }
-    if (cudaMemcpy(c->d_tables, c->plan.tables.data(), words * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    c->d_tables = static_cast<uint32_t*>(c->d_block);
+    c->d_scr = reinterpret_cast<Scratch*>(static_cast<unsigned char*>(c->d_block) + tbytes);
+    c->d_segs = reinterpret_cast<SegDesc*>(reinterpret_cast<unsigned char*>(c->d_scr) + align256(sizeof(Scratch)));
+    // A copy from pageable memory may return before its DMA lands; the
+    // solves run on non-blocking streams, so wait for it here.
+    if (cudaMemcpy(c->d_tables, c->plan.tables.data(), words * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
         release(c);
         return DIST_ECUDA;
     }
@@ -229,17 +321,16 @@ int dist_solve_bounded(dist_code* c, dist_result* out, void* cuda_stream, double
     if (c->in_batch) return DIST_EBUSY;
     if (c->plan.n_stab > 0 && c->plan.s_rank == c->plan.k_eff) return DIST_EZERO;
     DeviceGuard guard(c->dev->device);
-    if (!c->stream) {  // first single-code solve: stream, events, staging buffers
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreate(&c->e0) != cudaSuccess || cudaEventCreate(&c->e1) != cudaSuccess)
-            return DIST_ECUDA;
-        if (cudaMalloc(&c->d_segs, DIST_MAXSEG * sizeof(SegDesc)) != cudaSuccess ||
-            cudaMallocHost(&c->h_segs, DIST_MAXSEG * sizeof(SegDesc)) != cudaSuccess ||
-            cudaMallocHost(&c->h_scr, sizeof(Scratch)) != cudaSuccess)
-            return DIST_ENOMEM;
-    }
-    GpuExec ex{c, cuda_stream ? (cudaStream_t)cuda_stream : c->stream};
-    return solve_loop(c->plan, ex, time_limit_s, out);
+    SolveKit* kit = nullptr;
+    int rc = kit_acquire(c->dev, &kit);
+    if (rc) return rc;
+    GpuExec ex{c, kit, cuda_stream ? (cudaStream_t)cuda_stream : kit->stream};
+    rc = solve_loop(c->plan, ex, time_limit_s, out);
+    // every launch of the solve was synchronized; on an error path, drain the
+    // stream before the kit's staging buffer can serve another solve
+    if (rc != DIST_OK && rc != DIST_EINCOMPLETE && rc != DIST_EZERO) cudaStreamSynchronize(ex.st);
+    kit_release(c->dev, kit);
+    return rc;
 }
 
 int dist_solve(dist_code* c, dist_result* out, void* cuda_stream) {
@@ -250,7 +341,6 @@ int dist_free(dist_code* c) {
     if (!c) return DIST_OK;
     if (c->in_batch) return DIST_EBUSY;
     DeviceGuard guard(c->dev ? c->dev->device : 0);
-    if (c->stream) cudaStreamSynchronize(c->stream);
     release(c);
     return DIST_OK;
 }

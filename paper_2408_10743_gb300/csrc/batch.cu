@@ -153,7 +153,7 @@ double estimated_work(const Item* it) {
         if (s > 0 && lp.step_L_before[s] >= target) break;
         const size_t e = s + 1 < lp.step_r.size() ? (size_t)lp.step_seg0[s + 1] : lp.segs.size();
         for (size_t k = (size_t)lp.step_seg0[s]; k < e; k++)
-            w += (double)lp.segs[k].NA * (double)lp.segs[k].NB * (double)lp.segs[k].codes;
+            w += (double)(lp.segs[k].rank1 - lp.segs[k].rank0) * (double)lp.segs[k].codes;
     }
     return std::max(w, 1.0);
 }

@@ -81,6 +81,8 @@ struct GammaDesc {
 struct SegDesc {
     unsigned long long NA;          // C(a, i): A-subsets
     unsigned long long NB;          // C(b, r - i): B-subsets
+    unsigned long long rank0;       // this segment covers combination ranks [rank0, rank1)
+    unsigned long long rank1;       //   of the NA * NB (subset pairs) of its (step, i)
     unsigned long long chunk_base;  // first global chunk index of this segment
     unsigned long long codes;       // representative choices per subset
     uint32_t i;

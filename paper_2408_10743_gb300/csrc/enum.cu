@@ -132,14 +132,8 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         C.proj = P.proj;
         C.exclude = P.exclude;
         C.L_before = sg.L_before;
-        const unsigned long long total = sg.NA * sg.NB;
-        const unsigned long long lo =
-            (chunk - sg.chunk_base) * 32ull * sg.spl + (unsigned long long)lane * sg.spl;
-        unsigned long long done = 0;
-        if (lo < total) {
-            const unsigned long long hi = lo + sg.spl < total ? lo + sg.spl : total;
-            done = walk_range(C, sink, thr, sg, lo, hi);
-        }
+        unsigned long long lo, hi, done = 0;
+        if (seg_lane_range(sg, chunk, lane, lo, hi)) done = walk_range(C, sink, thr, sg, lo, hi);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
         int stop = 0;
@@ -260,14 +254,8 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_batch_
         C.exclude = bc.exclude;
         C.L_before = sg.L_before;
         DevSink sink{bc.scr};
-        const unsigned long long total = sg.NA * sg.NB;
-        const unsigned long long lo =
-            (chunk - sg.chunk_base) * 32ull * sg.spl + (unsigned long long)lane * sg.spl;
-        unsigned long long done = 0;
-        if (lo < total) {
-            const unsigned long long hi = lo + sg.spl < total ? lo + sg.spl : total;
-            done = walk_range(C, sink, thr, sg, lo, hi);
-        }
+        unsigned long long lo, hi, done = 0;
+        if (seg_lane_range(sg, chunk, lane, lo, hi)) done = walk_range(C, sink, thr, sg, lo, hi);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
         int stop = 0;

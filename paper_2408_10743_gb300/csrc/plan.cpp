@@ -745,6 +745,8 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
             memset(&sd, 0, sizeof sd);
             sd.NA = NA;
             sd.NB = NB;
+            sd.rank0 = 0;
+            sd.rank1 = NA * NB;
             sd.codes = codes;
             sd.i = (uint32_t)i;
             sd.g = (uint16_t)gslot[g];
@@ -786,23 +788,52 @@ planned:
     // lower U come from, and they must still spread over the whole GPU.
     // Generic-path segments cost tens of times more per codeword and keep
     // the plain split, so that they never become the critical path.
+    //
+    // A large segment ends in smaller chunks: the work of one wave of
+    // full-size chunks (one per resident warp) is cut into quarter-size ones,
+    // which run while the last full-size chunks finish.  Whichever step turns
+    // out to be the last one needed, warps then run out of work at nearly the
+    // same time instead of waiting for the last full-size chunks.
     unsigned long long chunks = 0;
     const Tuning tun = tuning_get();
+    const unsigned long long tw = (unsigned long long)std::max(1, target_warps);
+    std::vector<SegDesc> out;
+    std::vector<int> first_piece(lp->segs.size());
+    size_t spare = DIST_MAXSEG - lp->segs.size();  // room for tail pieces
     for (size_t t = 0; t < lp->segs.size(); t++) {
-        SegDesc& sd = lp->segs[t];
-        double per_lane = seg_cw[t] / (32.0 * std::max(1, target_warps) * (double)tun.chunks_per_warp);
+        SegDesc sd = lp->segs[t];
+        double per_lane = seg_cw[t] / (32.0 * (double)tw * (double)tun.chunks_per_warp);
         if (DIST_FAST_PATH((int)sd.i, lp->proj)) {
-            const double spread = seg_cw[t] / (32.0 * std::max(1, target_warps));
+            const double spread = seg_cw[t] / (32.0 * (double)tw);
             per_lane = std::max(per_lane, std::min((double)(1u << tun.lane_floor_log2), spread));
         }
         per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2));
         double spl_d = per_lane / (double)sd.codes;
         unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
         if (spl > (1ull << 30)) spl = 1ull << 30;
+        const unsigned long long R = sd.rank1 - sd.rank0;
+        first_piece[t] = (int)out.size();
+        unsigned long long tail = 0;
+        if (spl >= 4 && (R + 32 * spl - 1) / (32 * spl) >= 2 * tw && spare > 0) {
+            tail = std::min(R / 2, tw * 32 * spl);
+            --spare;
+        }
         sd.spl = (uint32_t)spl;
         sd.chunk_base = chunks;
-        chunks += (sd.NA * sd.NB + 32 * spl - 1) / (32 * spl);
+        sd.rank1 = sd.rank0 + (R - tail);
+        chunks += (R - tail + 32 * spl - 1) / (32 * spl);
+        out.push_back(sd);
+        if (tail) {
+            sd.spl = (uint32_t)(spl / 4);
+            sd.chunk_base = chunks;
+            sd.rank0 = sd.rank1;
+            sd.rank1 = sd.rank0 + tail;
+            chunks += (tail + 32 * (spl / 4) - 1) / (32 * (spl / 4));
+            out.push_back(sd);
+        }
     }
+    for (int& s0 : lp->step_seg0) s0 = s0 < (int)first_piece.size() ? first_piece[s0] : (int)out.size();
+    lp->segs.swap(out);
     lp->nchunks = chunks;
     for (size_t s = 0; s < lp->step_r.size(); s++) {
         const int s0 = lp->step_seg0[s];

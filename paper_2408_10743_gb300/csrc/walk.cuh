@@ -420,6 +420,16 @@ DIST_HD bool use_fast(const LaneCtx& C, int i) {
     return DIST_FAST_PATH(i, C.proj);
 }
 
+// Combination ranks [lo, hi) that lane `lane` walks in warp-chunk `chunk`
+// of segment sg (chunk_base <= chunk); false if the lane has none.
+DIST_HD bool seg_lane_range(const SegDesc& sg, unsigned long long chunk, int lane, unsigned long long& lo,
+                            unsigned long long& hi) {
+    lo = sg.rank0 + ((chunk - sg.chunk_base) * 32ull + (unsigned long long)lane) * sg.spl;
+    if (lo >= sg.rank1) return false;
+    hi = lo + sg.spl < sg.rank1 ? lo + sg.spl : sg.rank1;
+    return true;
+}
+
 // Walks the combination ranks [lo, hi) of segment sg; returns the number of
 // codewords evaluated.  Sink provides peek() (current upper bound),
 // record(...) and vote_any(p) (true if p holds on any lane running in step

@@ -104,11 +104,9 @@ struct HostExec {
             C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW; C.r = sg.r;
             C.gamma = g.gamma; C.proj = ep.proj; C.exclude = ep.exclude;
             C.L_before = sg.L_before;
-            unsigned long long total = sg.NA * sg.NB;
             for (int lane = 0; lane < 32; lane++) {
-                unsigned long long lo = (chunk - sg.chunk_base) * 32ull * sg.spl + (unsigned long long)lane * sg.spl;
-                if (lo >= total) continue;
-                unsigned long long hi = lo + sg.spl < total ? lo + sg.spl : total;
+                unsigned long long lo, hi;
+                if (!seg_lane_range(sg, chunk, lane, lo, hi)) continue;
                 uint32_t thr = DIST_WINF;
                 scr.codewords += walk_range(C, sink, thr, sg, lo, hi);
             }
@@ -223,11 +221,9 @@ extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int 
                 C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW; C.r = sg.r;
                 C.gamma = g.gamma; C.proj = ep.proj; C.exclude = ep.exclude;
                 C.L_before = sg.L_before;
-                const unsigned long long total = sg.NA * sg.NB;
                 for (int lane = 0; lane < 32; lane++) {
-                    unsigned long long lo = (chunk - sg.chunk_base) * 32ull * sg.spl + (unsigned long long)lane * sg.spl;
-                    if (lo >= total) continue;
-                    unsigned long long hi = lo + sg.spl < total ? lo + sg.spl : total;
+                    unsigned long long lo, hi;
+                    if (!seg_lane_range(sg, chunk, lane, lo, hi)) continue;
                     uint32_t thr = DIST_WINF;
                     ex.scr.codewords += walk_range(C, sink, thr, sg, lo, hi);
                 }
@@ -281,4 +277,44 @@ extern "C" void hw_rd_walk(int n, int t, unsigned long long rank0, int count, ui
         memcpy(out + (size_t)c * t, s, (size_t)t);
         if (c + 1 < count) rd_next(s, t, n);
     }
+}
+
+// The first launch plan of a code at the given resident-warp count and chunk
+// tuning, one row per segment: step, i, NA, NB, rank0, rank1, chunk_base, spl,
+// codes.  Returns the number of rows (or a negative code); *nchunks gets the
+// launch's chunk count.
+extern "C" int hw_plan_segments(const uint8_t* gen, int n, int K, int field, int target_warps, int cpw,
+                                int cap_log2, int floor_log2, unsigned long long* out, int max_rows,
+                                unsigned long long* nchunks) {
+    Plan p;
+    int rc = plan_build(gen, n, K, field, &p);
+    if (rc) return rc;
+    const Tuning saved = tuning_get();
+    Tuning t;
+    t.chunks_per_warp = cpw;
+    t.lane_cap_log2 = cap_log2;
+    t.lane_floor_log2 = floor_log2;
+    tuning_set(t);
+    LaunchPlan lp;
+    rc = plan_launch(p, 1, 0, plan_initial_bound(p), p.u0, target_warps, 2e13, &lp);
+    tuning_set(saved);
+    if (rc) return rc;
+    if ((int)lp.segs.size() > max_rows) return -100;
+    for (size_t k = 0; k < lp.segs.size(); k++) {
+        int step = 0;
+        while (step + 1 < (int)lp.step_seg0.size() && lp.step_seg0[step + 1] <= (int)k) ++step;
+        const SegDesc& s = lp.segs[k];
+        unsigned long long* row = out + k * 9;
+        row[0] = (unsigned long long)step;
+        row[1] = s.i;
+        row[2] = s.NA;
+        row[3] = s.NB;
+        row[4] = s.rank0;
+        row[5] = s.rank1;
+        row[6] = s.chunk_base;
+        row[7] = s.spl;
+        row[8] = s.codes;
+    }
+    *nchunks = lp.nchunks;
+    return (int)lp.segs.size();
 }

@@ -43,6 +43,11 @@ def hw():
     L.hw_plan_bounds.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.hw_plan_segments.restype = ctypes.c_int
+    L.hw_plan_segments.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_ulonglong)]
     L.hw_solve_sliced.restype = ctypes.c_int
     L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -190,6 +195,50 @@ def test_codeword_count_full_round(hw):
     last = sum(sum(comb(info.a[j], i) * 3 ** i * comb(info.b[j], r.rounds - i)
                    for i in range(0, r.rounds + 1)) for j in J)
     assert total - last <= r.codewords <= total
+
+
+def plan_segments(L, g, warps, cpw=6, cap=14, floor=12, field=2):
+    g = np.ascontiguousarray(g, dtype=np.uint8)
+    n = g.shape[1] // 2 if field == 2 else g.shape[1]
+    buf = (ctypes.c_ulonglong * (256 * 9))()
+    nch = ctypes.c_ulonglong()
+    k = L.hw_plan_segments(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n, g.shape[0], field,
+                           warps, cpw, cap, floor, buf, 256, ctypes.byref(nch))
+    assert k > 0
+    return np.array(buf[:k * 9], dtype=np.uint64).reshape(k, 9).astype(object), int(nch.value)
+
+
+@pytest.mark.parametrize("warps", [4, 64, 2432])
+def test_plan_chunks_cover_every_rank_once(hw, warps):
+    """Segments of one (step, i) partition its NA * NB ranks; chunk bases and
+    counts add up; the (chunk, lane) ranges the kernels derive from them cover
+    every rank exactly once; large segments end in smaller chunks."""
+    split_seen = False
+    for g in (synth.single_qc(0), synth.random_f2_code(40, 30, synth.Xoshiro256ss(5)), synth.single_f2(0)):
+        rows, nchunks = plan_segments(hw, g, warps)
+        groups, nxt = {}, 0
+        for step, i, NA, NB, r0, r1, cb, spl, codes in rows:
+            assert cb == nxt and spl >= 1 and r1 > r0
+            nxt += (r1 - r0 + 32 * spl - 1) // (32 * spl)
+            groups.setdefault((step, i), []).append((r0, r1, cb, spl, NA * NB))
+        assert nxt == nchunks
+        for pieces in groups.values():
+            assert pieces[0][0] == 0 and pieces[-1][1] == pieces[0][4]
+            for a, b in zip(pieces, pieces[1:]):
+                assert a[1] == b[0] and b[3] <= a[3]
+            split_seen |= len(pieces) > 1
+            # lanes of every chunk, as seg_lane_range computes them
+            covered = 0
+            for r0, r1, cb, spl, _ in pieces:
+                nch = (r1 - r0 + 32 * spl - 1) // (32 * spl)
+                starts = r0 + (np.arange(nch * 32, dtype=object)) * spl
+                starts = [s for s in starts if s < r1]
+                ends = [min(s + spl, r1) for s in starts]
+                assert all(e2 == s2 for e2, s2 in zip(ends, starts[1:]))
+                covered += sum(e - s for s, e in zip(starts, ends))
+            assert covered == pieces[0][4]
+    if warps <= 64:
+        assert split_seen
 
 
 def solve_sliced(L, g, seed, one_step_plans, field=2, n_stab=0):

@@ -212,6 +212,29 @@ int dist_plan_unit(const uint8_t *generator, int n, int K, int field, int gamma,
                    int rep, uint8_t *vec_out, int *qubit, int *kind);
 
 /*
+ * Qubit stabilizer codes (Section 2).  The classical stabilizer code S of an
+ * [[n, k, d(Q)]] code lies in its symplectic dual N = S^{perp_s} (the
+ * classical normalizer code, dimension n + k); d(Q) = wt_s(N minus S) for
+ * k > 0 and wt_s(S) for k = 0.
+ *
+ * dist_normalizer -- host only: a normalizer matrix of the code.
+ *   stabilizers: m rows x 2n bytes in {0,1} (x | z), generators of S in any
+ *                number (dependent rows are dropped); 1 <= n <= 128.
+ *   generator_out: room for 2n rows x 2n bytes; receives *K_out rows whose
+ *                first *n_stab_out rows are a basis of S and the rest
+ *                logical operators (K = n + k, n_stab = n - k); for k = 0, a
+ *                basis of S and n_stab = 0.
+ *   DIST_EINVAL if a byte is not 0/1 or two generators anticommute;
+ *   DIST_EZERO if every row is zero.
+ * dist_init_stabilizer -- dist_normalizer, then dist_init and
+ *   dist_set_exclude with its rows: dist_solve then returns d(Q), with a
+ *   witness in N minus S (a logical operator of weight d(Q)).
+ */
+int dist_normalizer(const uint8_t *stabilizers, int n, int m, uint8_t *generator_out, int *K_out,
+                    int *n_stab_out);
+int dist_init_stabilizer(dist_code **out, const uint8_t *stabilizers, int n, int m);
+
+/*
  * dist_intpeak -- integer issue microbenchmark used as the roofline
  * denominator.  Runs a loop of `iters` iterations of the enumeration's
  * per-codeword instruction mix (2 LOP3, 1 POPC, half a 3-way min) on every SM and

@@ -2,10 +2,13 @@
 
     python -m paper_2408_10743_gb300 --workload qc72 [--index 0] [--repeat 1]
     python -m paper_2408_10743_gb300 --matrix FILE [--field 2|4] [--n-stab S]
+    python -m paper_2408_10743_gb300 --stabilizers FILE
 
 FILE holds one generator row per line: 2n digits 0/1 (x | z) for field 2, or n
 symbols 0-3 (a + 2b for a + alpha b) for field 4; blank lines and lines
-starting with '#' are ignored.
+starting with '#' are ignored.  With --stabilizers the rows generate the
+stabilizer of a qubit code and the output is d(Q), the least weight of a
+logical operator (the normalizer minus the stabilizer).
 """
 import argparse
 import json
@@ -33,6 +36,8 @@ def main(argv=None):
     src = ap.add_mutually_exclusive_group(required=True)
     src.add_argument("--workload", choices=["qc72", "f2_24", "f4_40"])
     src.add_argument("--matrix")
+    src.add_argument("--stabilizers", metavar="FILE",
+                     help="stabilizer generators (x | z) of a qubit code: report d(Q)")
     src.add_argument("--random", nargs=2, type=int, metavar=("N", "K"),
                      help="random F2 code (i.i.d. bits, full rank), seeded by --index")
     src.add_argument("--batch", type=int, metavar="COUNT",
@@ -63,6 +68,14 @@ def main(argv=None):
         g = synth.single_f2(args.index)
     elif args.workload == "f4_40":
         g, field = synth.single_f4(args.index), 4
+    elif args.stabilizers:
+        with binding.Code.from_stabilizers(read_matrix(args.stabilizers)) as code:
+            for _ in range(args.repeat):
+                r = code.solve(time_limit_s=args.time_limit)
+        out = {k: v for k, v in r.items() if k not in ("witness", "coeffs")}
+        out["logical"] = "".join(str(int(v)) for v in r["witness"])
+        print(json.dumps(out))
+        return 0
     elif args.random:
         g = synth.random_f2_code(args.random[0], args.random[1],
                                  synth.Xoshiro256ss(synth.seed_for(5, args.index)))

@@ -78,6 +78,9 @@ SIGNATURES = {
                                       ctypes.c_int, ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     "dist_intpeak": (ctypes.c_int, [ctypes.POINTER(IntpeakResult), ctypes.c_int, _VP]),
+    "dist_normalizer": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
+    "dist_init_stabilizer": (ctypes.c_int, [ctypes.POINTER(_VP), _U8P, ctypes.c_int, ctypes.c_int]),
     "dist_solve_noalloc": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(DistResult), _VP]),
     "dist_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(BatchOpts)]),
@@ -164,6 +167,31 @@ def dist_init(generator, n, K, field):
 
 def dist_set_exclude(handle, n_stab):
     return _check(lib().dist_set_exclude(handle, n_stab), "dist_set_exclude")
+
+
+def _as_stab(stabilizers):
+    s = np.ascontiguousarray(np.asarray(stabilizers, dtype=np.uint8))
+    if s.ndim != 2 or s.shape[1] % 2:
+        raise ValueError("stabilizers must be a 2-D array of rows (x | z)")
+    return s, s.shape[1] // 2, s.shape[0]
+
+
+def dist_normalizer(stabilizers):
+    """Normalizer matrix of a qubit stabilizer code: (rows, n_stab), the first
+    n_stab rows a basis of S (host only)."""
+    s, n, m = _as_stab(stabilizers)
+    out = np.zeros((2 * n, 2 * n), dtype=np.uint8)
+    K, ns = ctypes.c_int(), ctypes.c_int()
+    _check(lib().dist_normalizer(_ptr(s), n, m, _ptr(out), ctypes.byref(K), ctypes.byref(ns)),
+           "dist_normalizer")
+    return out[:K.value].copy(), ns.value
+
+
+def dist_init_stabilizer(stabilizers):
+    s, n, m = _as_stab(stabilizers)
+    h = _VP()
+    _check(lib().dist_init_stabilizer(ctypes.byref(h), _ptr(s), n, m), "dist_init_stabilizer")
+    return h
 
 
 def dist_solve(handle, stream=None, ok=(DIST_OK,)):
@@ -317,6 +345,18 @@ class Code:
         self.n, self.K, self.field = n, K, field
         self._h = dist_init(g, n, K, field)
 
+    @classmethod
+    def from_stabilizers(cls, stabilizers):
+        """The normalizer code of a qubit stabilizer code, with S excluded:
+        solve() returns d(Q)."""
+        gen, n_stab = dist_normalizer(stabilizers)
+        self = cls.__new__(cls)
+        self.n, self.K, self.field = gen.shape[1] // 2, gen.shape[0], DIST_F2
+        self._h = None
+        self._h = dist_init_stabilizer(stabilizers)
+        self.n_stab = n_stab
+        return self
+
     def set_exclude(self, n_stab: int):
         dist_set_exclude(self._h, n_stab)
 
@@ -343,6 +383,12 @@ class Code:
             self.close()
         except Exception:
             pass
+
+
+def quantum_distance(stabilizers, stream=None) -> dict:
+    """d(Q) of a qubit stabilizer code from its stabilizer generators."""
+    with Code.from_stabilizers(stabilizers) as c:
+        return c.solve(stream)
 
 
 def distance(generator, field=DIST_F2, n_stab=0, stream=None) -> dict:

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdist.so")
 
 CU_SOURCES = ["api.cu", "batch.cu", "enum.cu", "intpeak.cu", "noalloc.cu"]
-CPP_SOURCES = ["plan.cpp"]
+CPP_SOURCES = ["plan.cpp", "stab.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "-I", CSRC, "-I", INCLUDE]

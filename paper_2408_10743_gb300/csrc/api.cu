@@ -311,6 +311,39 @@ int dist_init(dist_code** out, const uint8_t* generator, int n, int K, int field
     return DIST_OK;
 }
 
+int dist_normalizer(const uint8_t* stabilizers, int n, int m, uint8_t* generator_out, int* K_out,
+                    int* n_stab_out) {
+    if (!stabilizers || !generator_out || !K_out || !n_stab_out) return DIST_EINVAL;
+    std::vector<uint8_t> gen;
+    int K = 0, s = 0;
+    const int rc = map_plan_rc(stab_normalizer(stabilizers, n, m, &gen, &K, &s));
+    if (rc) return rc;
+    memcpy(generator_out, gen.data(), gen.size());
+    *K_out = K;
+    *n_stab_out = s;
+    return DIST_OK;
+}
+
+int dist_init_stabilizer(dist_code** out, const uint8_t* stabilizers, int n, int m) {
+    if (!out || !stabilizers) return DIST_EINVAL;
+    *out = nullptr;
+    std::vector<uint8_t> gen;
+    int K = 0, s = 0;
+    int rc = map_plan_rc(stab_normalizer(stabilizers, n, m, &gen, &K, &s));
+    if (rc) return rc;
+    rc = dist_init(out, gen.data(), n, K, DIST_F2);
+    if (rc) return rc;
+    if (s > 0) {
+        rc = dist_set_exclude(*out, s);
+        if (rc) {
+            dist_free(*out);
+            *out = nullptr;
+            return rc;
+        }
+    }
+    return DIST_OK;
+}
+
 int dist_set_exclude(dist_code* c, int n_stab) {
     if (!c) return DIST_EINVAL;
     return map_plan_rc(plan_set_exclude(&c->plan, n_stab));

@@ -150,6 +150,13 @@ void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep);
 // symbols).  Checks the weight and that the coefficients reproduce it.
 int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* coeffs);
 
+// Stabilizer-code front end (stab.cpp): from m generator rows (x | z) of the
+// classical stabilizer code S of an [[n, k]] qubit code, a generator matrix
+// of its normalizer N = S^{perp_s} whose first *n_stab rows are a basis of S
+// (K = n + k rows, n_stab = n - k); for k = 0 a basis of S with n_stab = 0.
+// P_EINVAL for bad input or generators that do not commute, P_EZERO if S = 0.
+int stab_normalizer(const uint8_t* stab, int n, int m, std::vector<uint8_t>* gen, int* K, int* n_stab);
+
 // Saturating binomial table [(DIST_MAXU+1) x (DIST_MAXR+1)].
 void binom_table(unsigned long long* tab);
 

@@ -391,13 +391,15 @@ def run_ours(args):
     g, field, cfg = workload(args.workload, rank)
     K = g.shape[0]
 
-    # chunk granularity picked by the library's autotuner on this GPU
-    tuning = dist.dist_autotune(budget_s=args.autotune) if args.autotune > 0 else dist.dist_get_tuning()
+    code = dist.Code(g, field)
+    # chunk granularity picked by the library's autotuner, timed on this
+    # workload's code on this GPU (before the timed region)
+    tuning = (dist.dist_autotune_codes([code], budget_s=args.autotune) if args.autotune > 0
+              else dist.dist_get_tuning())
     # roofline denominator: the integer-issue microbenchmark on this GPU
     with torch.cuda.stream(stream):
         peak = dist.dist_intpeak(iters=20000, stream=stream)
 
-    code = dist.Code(g, field)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
 
     def one_step(timed):

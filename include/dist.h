@@ -185,6 +185,9 @@ typedef struct {
 int dist_set_tuning(const dist_tuning *t);
 int dist_get_tuning(dist_tuning *t);
 int dist_autotune(dist_tuning *best, double budget_s);
+/* Same search, timed on the caller's codes (initialised on the current
+ * device, not in a batch): tunes for a known workload. */
+int dist_autotune_codes(dist_code *const *codes, int count, double budget_s, dist_tuning *best);
 
 /*
  * dist_plan_info -- host-only view of the plan step S2-S3 built for an input

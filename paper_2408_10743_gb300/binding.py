@@ -95,6 +95,8 @@ SIGNATURES = {
     "dist_set_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
     "dist_get_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
     "dist_autotune": (ctypes.c_int, [ctypes.POINTER(Tuning), ctypes.c_double]),
+    "dist_autotune_codes": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_double,
+                                           ctypes.POINTER(Tuning)]),
     "dist_version": (ctypes.c_char_p, []),
     "dist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -314,6 +316,16 @@ def dist_autotune(budget_s=10.0) -> dict:
     device and applies the fastest; returns it with its codewords/s."""
     t = Tuning()
     _check(lib().dist_autotune(ctypes.byref(t), float(budget_s)), "dist_autotune")
+    return {"chunks_per_warp": t.chunks_per_warp, "lane_cap_log2": t.lane_cap_log2,
+            "lane_floor_log2": t.lane_floor_log2, "codewords_per_s": t.codewords_per_s}
+
+
+def dist_autotune_codes(codes, budget_s=10.0) -> dict:
+    """The autotuner's search timed on the given Code objects."""
+    arr = (_VP * len(codes))(*[c._h for c in codes])
+    t = Tuning()
+    _check(lib().dist_autotune_codes(arr, len(codes), float(budget_s), ctypes.byref(t)),
+           "dist_autotune_codes")
     return {"chunks_per_warp": t.chunks_per_warp, "lane_cap_log2": t.lane_cap_log2,
             "lane_floor_log2": t.lane_floor_log2, "codewords_per_s": t.codewords_per_s}
 

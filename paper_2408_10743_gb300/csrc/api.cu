@@ -462,32 +462,11 @@ int dist_get_tuning(dist_tuning* t) {
 // Calibration: two seeded random codes (n = 64, K = 56 and n = 72, K = 72)
 // whose solves are dominated by one large enumeration step, timed with the
 // kernels' CUDA events for each setting of the grid; best median rate wins.
-int dist_autotune(dist_tuning* best, double budget_s) {
-    if (!best) return DIST_EINVAL;
-    if (budget_s <= 0) budget_s = 10.0;
-    static const int kSizes[2][2] = {{64, 56}, {72, 72}};
-    std::vector<dist_code*> codes;
-    uint64_t x = 0x9E3779B97F4A7C15ull;  // xorshift64* stream for the calibration bits
-    for (auto& nk : kSizes) {
-        const int n = nk[0], K = nk[1];
-        for (int attempt = 0; attempt < 100; attempt++) {
-            std::vector<uint8_t> g((size_t)K * 2 * n);
-            for (auto& b : g) {
-                x ^= x >> 12;
-                x ^= x << 25;
-                x ^= x >> 27;
-                b = (uint8_t)(((x * 0x2545F4914F6CDD1Dull) >> 63) & 1u);
-            }
-            dist_code* c = nullptr;
-            int rc = dist_init(&c, g.data(), n, K, DIST_F2);
-            if (rc == DIST_OK && c->plan.k_eff == K) {
-                codes.push_back(c);
-                break;
-            }
-            if (c) dist_free(c);
-            if (rc != DIST_OK && rc != DIST_EZERO) return rc;
-        }
-    }
+namespace {
+
+// Times two solves of every code per setting of the grid (the second one
+// counts) and applies the setting with the best geometric-mean codewords/s.
+int autotune_on(const std::vector<dist_code*>& codes, double budget_s, dist_tuning* best) {
     const Tuning saved = tuning_get();
     std::vector<Tuning> grid;
     for (int a : {2, 3, 6, 12})
@@ -514,7 +493,6 @@ int dist_autotune(dist_tuning* best, double budget_s) {
                 int rc = dist_solve(c, &r, nullptr);
                 if (rc != DIST_OK) {
                     tuning_set(saved);
-                    for (dist_code* cc : codes) dist_free(cc);
                     return rc;
                 }
                 if (rep == 1) log_rate += std::log((double)r.codewords / std::max(r.gpu_seconds, 1e-9));
@@ -526,13 +504,60 @@ int dist_autotune(dist_tuning* best, double budget_s) {
             best_t = t;
         }
     }
-    for (dist_code* c : codes) dist_free(c);
     tuning_set(best_t);
     best->chunks_per_warp = best_t.chunks_per_warp;
     best->lane_cap_log2 = best_t.lane_cap_log2;
     best->lane_floor_log2 = best_t.lane_floor_log2;
     best->codewords_per_s = best_rate;
     return DIST_OK;
+}
+
+}  // namespace
+
+int dist_autotune(dist_tuning* best, double budget_s) {
+    if (!best) return DIST_EINVAL;
+    if (budget_s <= 0) budget_s = 10.0;
+    static const int kSizes[2][2] = {{64, 56}, {72, 72}};
+    std::vector<dist_code*> codes;
+    uint64_t x = 0x9E3779B97F4A7C15ull;  // xorshift64* stream for the calibration bits
+    for (auto& nk : kSizes) {
+        const int n = nk[0], K = nk[1];
+        for (int attempt = 0; attempt < 100; attempt++) {
+            std::vector<uint8_t> g((size_t)K * 2 * n);
+            for (auto& b : g) {
+                x ^= x >> 12;
+                x ^= x << 25;
+                x ^= x >> 27;
+                b = (uint8_t)(((x * 0x2545F4914F6CDD1Dull) >> 63) & 1u);
+            }
+            dist_code* c = nullptr;
+            int rc = dist_init(&c, g.data(), n, K, DIST_F2);
+            if (rc == DIST_OK && c->plan.k_eff == K) {
+                codes.push_back(c);
+                break;
+            }
+            if (c) dist_free(c);
+            if (rc != DIST_OK && rc != DIST_EZERO) {
+                for (dist_code* cc : codes) dist_free(cc);
+                return rc;
+            }
+        }
+    }
+    const int rc = autotune_on(codes, budget_s, best);
+    for (dist_code* c : codes) dist_free(c);
+    return rc;
+}
+
+int dist_autotune_codes(dist_code* const* codes, int count, double budget_s, dist_tuning* best) {
+    if (!best || !codes || count < 1) return DIST_EINVAL;
+    if (budget_s <= 0) budget_s = 10.0;
+    std::vector<dist_code*> v;
+    for (int i = 0; i < count; i++) {
+        if (!codes[i]) return DIST_EINVAL;
+        if (codes[i]->in_batch) return DIST_EBUSY;
+        v.push_back(codes[i]);
+    }
+    return autotune_on(v, budget_s, best);
 }
 
 const char* dist_version(void) { return "libdist 0.1 (sm_103a)"; }

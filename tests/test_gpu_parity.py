@@ -230,6 +230,12 @@ def test_tuning_changes_speed_not_results(stream):
         assert best["codewords_per_s"] > 0
         assert dist.dist_get_tuning()["chunks_per_warp"] == best["chunks_per_warp"]
         assert gpu(g, stream=stream)["d"] in ds
+        with dist.Code(g) as c:
+            best = dist.dist_autotune_codes([c], budget_s=2.0)
+            assert best["codewords_per_s"] > 0
+            assert dist.dist_get_tuning() == {k: best[k] for k in ("chunks_per_warp", "lane_cap_log2",
+                                                                   "lane_floor_log2")}
+            assert c.solve(stream=stream)["d"] in ds
     finally:
         dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"],
                              saved["lane_floor_log2"])

@@ -140,6 +140,8 @@ typedef struct {
 typedef struct {
     uint64_t slices, launches, codes_done, active, pending, resident_bytes;
     double gpu_seconds;          /* summed CUDA-event time of the multi-code launches */
+    double plan_seconds;         /* worker time before the launches: planning, packing, uploads */
+    double post_seconds;         /* worker time after them: read-back wait, verdicts, witnesses */
 } dist_batch_stats_t;
 
 typedef struct dist_batch dist_batch;

@@ -30,6 +30,17 @@ class DistResult(ctypes.Structure):
                 ("launches", ctypes.c_uint64)]
 
 
+# The same layout as a numpy structured dtype: an array of dist_result viewed
+# without copying (Batch.wait_array).
+RESULT_DTYPE = np.dtype({
+    "names": [f for f, _ in DistResult._fields_],
+    "formats": [{"witness": (np.uint8, 256), "coeffs": (np.uint8, 256), "codewords": np.uint64,
+                 "launches": np.uint64, "seconds": np.float64, "gpu_seconds": np.float64}.get(f, np.int32)
+                for f, _ in DistResult._fields_],
+    "offsets": [getattr(DistResult, f).offset for f, _ in DistResult._fields_],
+    "itemsize": ctypes.sizeof(DistResult)})
+
+
 class PlanInfo(ctypes.Structure):
     _fields_ = [("n_gamma_built", ctypes.c_int32), ("n_gamma_used", ctypes.c_int32),
                 ("k_eff", ctypes.c_int32), ("s_rank", ctypes.c_int32),
@@ -60,7 +71,8 @@ class BatchStats(ctypes.Structure):
     _fields_ = [("slices", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("codes_done", ctypes.c_uint64), ("active", ctypes.c_uint64),
                 ("pending", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64),
-                ("gpu_seconds", ctypes.c_double)]
+                ("gpu_seconds", ctypes.c_double), ("plan_seconds", ctypes.c_double),
+                ("post_seconds", ctypes.c_double)]
 
 
 # name -> (restype, argtypes); mirrors include/dist.h
@@ -273,10 +285,10 @@ def dist_batch_poll(batch, ticket, count):
     return list(res)
 
 
-def dist_batch_wait(batch, ticket, count, timeout_s=0.0):
+def dist_batch_wait(batch, ticket, count, timeout_s=0.0, as_array=False):
     res = (DistResult * count)()
     _check(lib().dist_batch_wait(batch, ticket, res, float(timeout_s)), "dist_batch_wait")
-    return list(res)
+    return np.frombuffer(res, dtype=RESULT_DTYPE) if as_array else list(res)
 
 
 def dist_batch_wait_any(batch, timeout_s=0.0):
@@ -438,6 +450,15 @@ class Batch:
     def wait(self, ticket, timeout_s=0.0):
         return self._finish(ticket, dist_batch_wait(self._h, ticket, len(self._tickets[ticket]),
                                                     timeout_s))
+
+    def wait_array(self, ticket, timeout_s=0.0):
+        """As wait, but all results as one numpy structured array (fields of
+        dist_result; witness and coeffs as 256-byte rows) without per-code
+        Python objects."""
+        n = len(self._tickets[ticket])
+        res = dist_batch_wait(self._h, ticket, n, timeout_s, as_array=True)
+        self._tickets.pop(ticket)
+        return res
 
     def wait_any(self, timeout_s=0.0):
         """Id of a finished ticket (collect it with poll), or None on timeout."""

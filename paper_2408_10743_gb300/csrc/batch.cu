@@ -124,6 +124,7 @@ struct dist_batch {
     uint64_t launches = 0;
     uint64_t codes_done = 0;
     double gpu_seconds = 0;
+    double plan_seconds = 0, post_seconds = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     // device arrays of one slice
     DevBuf<BatchCode> codes;
@@ -169,8 +170,13 @@ void dist_batch::finish(Item* it, int status) {
 
 // One slice; returns a DIST_* error only for failures of the device itself.
 int dist_batch::slice() {
+    const double t_plan = wall_now();
     const int tw = dev->sms * dev->batch_blocks_per_sm * DIST_ENUM_WARPS;
-    // plan codes that need it
+    // plan codes that need it: first as if each had the whole GPU, then --
+    // since the codes of a slice share the warps -- again with about four
+    // times its share of the estimated work in warps, so that a small code is
+    // cut into a few longer lane chunks instead of thousands of tiny ones
+    std::vector<Item*> fresh;
     for (Item* it : active) {
         if (it->planned || it->done) continue;
         const Plan& p = it->c->plan;
@@ -181,6 +187,18 @@ int dist_batch::slice() {
             continue;
         }
         it->planned = true;
+        fresh.push_back(it);
+    }
+    if (!fresh.empty()) {
+        double all = 0;
+        for (Item* it : active)
+            if (!it->done) all += estimated_work(it);
+        for (Item* it : fresh) {
+            const double share = estimated_work(it) / std::max(all, 1.0);
+            const int twi = (int)std::min<double>(tw, std::max(32.0, std::ceil(4.0 * share * tw)));
+            if (twi >= tw) continue;
+            plan_rechunk(&it->lp, twi);
+        }
     }
     std::vector<Item*> run;
     for (Item* it : active)
@@ -284,6 +302,8 @@ int dist_batch::slice() {
     P.norder = (int)ord.size();
     P.budget_ns = opts.slice_ms > 0 ? (unsigned long long)(opts.slice_ms * 1e6) : 0ull;
     const int grid = dev->sms * dev->batch_blocks_per_sm;
+    const double t_launch = wall_now();
+    plan_seconds += t_launch - t_plan;
     cudaEventRecord(e0, st);
     if (batch_launch(P, grid, st) != cudaSuccess) return DIST_ECUDA;
     cudaEventRecord(e1, st);
@@ -353,6 +373,7 @@ int dist_batch::slice() {
         }
         finish(it, DIST_OK);
     }
+    post_seconds += wall_now() - t_launch - ms * 1e-3;
     return DIST_OK;
 }
 
@@ -514,6 +535,8 @@ int dist_batch_stats(dist_batch* b, dist_batch_stats_t* s) {
     s->active = (uint64_t)b->active.size();
     s->pending = (uint64_t)b->pending.size();
     s->gpu_seconds = b->gpu_seconds;
+    s->plan_seconds = b->plan_seconds;
+    s->post_seconds = b->post_seconds;
     s->resident_bytes = (uint64_t)b->resident;
     return DIST_OK;
 }

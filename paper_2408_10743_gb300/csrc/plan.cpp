@@ -687,6 +687,81 @@ int plan_set_exclude(Plan* p, int n_stab) {
     return P_OK;
 }
 
+// Cuts the raw segments of a planned launch into warp-chunks for
+// target_warps resident warps (see plan_launch) and places the segment table
+// in shared memory.
+static void chunk_launch(LaunchPlan* lp, int target_warps) {
+    // Chunks: each segment is cut into about chunks_per_warp (default 6)
+    // warp-chunks per resident warp, so that every segment spreads over the
+    // whole GPU and the tail is short; a lane chunk holds at most
+    // 2^lane_cap_log2 (default 2^14, about a quarter of a millisecond for a
+    // warp) codewords so that stop requests and time budgets are seen soon.
+    // A segment on the
+    // fast path gets at least 2^lane_floor_log2 codewords per lane, so that it
+    // is not cut finer than the per-lane set-up (unranking the start subset,
+    // fetching the chunk) is worth -- but never fewer chunks than resident
+    // warps: the early, small steps are where the lighter codewords that
+    // lower U come from, and they must still spread over the whole GPU.
+    // Generic-path segments cost tens of times more per codeword and keep
+    // the plain split, so that they never become the critical path.
+    //
+    // A large segment ends in smaller chunks: the work of one wave of
+    // full-size chunks (one per resident warp) is cut into quarter-size ones,
+    // which run while the last full-size chunks finish.  Whichever step turns
+    // out to be the last one needed, warps then run out of work at nearly the
+    // same time instead of waiting for the last full-size chunks.
+    unsigned long long chunks = 0;
+    const Tuning tun = tuning_get();
+    const unsigned long long tw = (unsigned long long)std::max(1, target_warps);
+    const std::vector<SegDesc>& raw = lp->raw_segs;
+    std::vector<SegDesc> out;
+    std::vector<int> first_piece(raw.size());
+    size_t spare = DIST_MAXSEG - raw.size();  // room for tail pieces
+    for (size_t t = 0; t < raw.size(); t++) {
+        SegDesc sd = raw[t];
+        const double seg_cw = (double)sd.NA * (double)sd.NB * (double)sd.codes;
+        double per_lane = seg_cw / (32.0 * (double)tw * (double)tun.chunks_per_warp);
+        if (DIST_FAST_PATH((int)sd.i, lp->proj)) {
+            const double spread = seg_cw / (32.0 * (double)tw);
+            per_lane = std::max(per_lane, std::min((double)(1u << tun.lane_floor_log2), spread));
+        }
+        per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2));
+        double spl_d = per_lane / (double)sd.codes;
+        unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
+        if (spl > (1ull << 30)) spl = 1ull << 30;
+        const unsigned long long R = sd.rank1 - sd.rank0;
+        first_piece[t] = (int)out.size();
+        unsigned long long tail = 0;
+        if (spl >= 4 && (R + 32 * spl - 1) / (32 * spl) >= 2 * tw && spare > 0) {
+            tail = std::min(R / 2, tw * 32 * spl);
+            --spare;
+        }
+        sd.spl = (uint32_t)spl;
+        sd.chunk_base = chunks;
+        sd.rank1 = sd.rank0 + (R - tail);
+        chunks += (R - tail + 32 * spl - 1) / (32 * spl);
+        out.push_back(sd);
+        if (tail) {
+            sd.spl = (uint32_t)(spl / 4);
+            sd.chunk_base = chunks;
+            sd.rank0 = sd.rank1;
+            sd.rank1 = sd.rank0 + tail;
+            chunks += (tail + 32 * (spl / 4) - 1) / (32 * (spl / 4));
+            out.push_back(sd);
+        }
+    }
+    lp->step_seg0 = lp->raw_step_seg0;
+    for (int& s0 : lp->step_seg0) s0 = s0 < (int)first_piece.size() ? first_piece[s0] : (int)out.size();
+    lp->segs.swap(out);
+    lp->nchunks = chunks;
+    lp->step_chunk0.clear();
+    for (size_t s = 0; s < lp->step_r.size(); s++) {
+        const int s0 = lp->step_seg0[s];
+        lp->step_chunk0.push_back(s0 < (int)lp->segs.size() ? lp->segs[s0].chunk_base : chunks);
+    }
+    lp->s_words = lp->s_segs + (uint32_t)(lp->segs.size() * sizeof(SegDesc) / 4);
+}
+
 int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int target_warps,
                 double max_codewords, LaunchPlan* lp) {
     *lp = LaunchPlan();
@@ -775,72 +850,11 @@ planned:
     total = 0;
     for (double cw : seg_cw) total += cw;
     lp->codewords = total;
-    // Chunks: each segment is cut into about chunks_per_warp (default 6)
-    // warp-chunks per resident warp, so that every segment spreads over the
-    // whole GPU and the tail is short; a lane chunk holds at most
-    // 2^lane_cap_log2 (default 2^14, about a quarter of a millisecond for a
-    // warp) codewords
-    // so that stop requests and time budgets are seen soon.  A segment on the
-    // fast path gets at least 2^lane_floor_log2 codewords per lane, so that it
-    // is not cut finer than the per-lane set-up (unranking the start subset,
-    // fetching the chunk) is worth -- but never fewer chunks than resident
-    // warps: the early, small steps are where the lighter codewords that
-    // lower U come from, and they must still spread over the whole GPU.
-    // Generic-path segments cost tens of times more per codeword and keep
-    // the plain split, so that they never become the critical path.
-    //
-    // A large segment ends in smaller chunks: the work of one wave of
-    // full-size chunks (one per resident warp) is cut into quarter-size ones,
-    // which run while the last full-size chunks finish.  Whichever step turns
-    // out to be the last one needed, warps then run out of work at nearly the
-    // same time instead of waiting for the last full-size chunks.
-    unsigned long long chunks = 0;
-    const Tuning tun = tuning_get();
-    const unsigned long long tw = (unsigned long long)std::max(1, target_warps);
-    std::vector<SegDesc> out;
-    std::vector<int> first_piece(lp->segs.size());
-    size_t spare = DIST_MAXSEG - lp->segs.size();  // room for tail pieces
-    for (size_t t = 0; t < lp->segs.size(); t++) {
-        SegDesc sd = lp->segs[t];
-        double per_lane = seg_cw[t] / (32.0 * (double)tw * (double)tun.chunks_per_warp);
-        if (DIST_FAST_PATH((int)sd.i, lp->proj)) {
-            const double spread = seg_cw[t] / (32.0 * (double)tw);
-            per_lane = std::max(per_lane, std::min((double)(1u << tun.lane_floor_log2), spread));
-        }
-        per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2));
-        double spl_d = per_lane / (double)sd.codes;
-        unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
-        if (spl > (1ull << 30)) spl = 1ull << 30;
-        const unsigned long long R = sd.rank1 - sd.rank0;
-        first_piece[t] = (int)out.size();
-        unsigned long long tail = 0;
-        if (spl >= 4 && (R + 32 * spl - 1) / (32 * spl) >= 2 * tw && spare > 0) {
-            tail = std::min(R / 2, tw * 32 * spl);
-            --spare;
-        }
-        sd.spl = (uint32_t)spl;
-        sd.chunk_base = chunks;
-        sd.rank1 = sd.rank0 + (R - tail);
-        chunks += (R - tail + 32 * spl - 1) / (32 * spl);
-        out.push_back(sd);
-        if (tail) {
-            sd.spl = (uint32_t)(spl / 4);
-            sd.chunk_base = chunks;
-            sd.rank0 = sd.rank1;
-            sd.rank1 = sd.rank0 + tail;
-            chunks += (tail + 32 * (spl / 4) - 1) / (32 * (spl / 4));
-            out.push_back(sd);
-        }
-    }
-    for (int& s0 : lp->step_seg0) s0 = s0 < (int)first_piece.size() ? first_piece[s0] : (int)out.size();
-    lp->segs.swap(out);
-    lp->nchunks = chunks;
-    for (size_t s = 0; s < lp->step_r.size(); s++) {
-        const int s0 = lp->step_seg0[s];
-        lp->step_chunk0.push_back(s0 < (int)lp->segs.size() ? lp->segs[s0].chunk_base : chunks);
-    }
+    lp->raw_segs = lp->segs;
+    lp->raw_step_seg0 = lp->step_seg0;
     // Shared memory (32-bit words): representatives of every matrix, their
-    // word-0 tables, the binomials the launch can need, the segment table.
+    // word-0 tables, the binomials the launch can need, then the segment
+    // table (placed by chunk_launch).
     uint32_t off = 0;
     for (GammaDesc& d : lp->g) {
         d.s_rep = off;
@@ -863,8 +877,12 @@ planned:
     lp->bcols = maxr + 1;
     off += (uint32_t)(lp->brows * lp->bcols) * 2u;
     lp->s_segs = off;
-    off += (uint32_t)(lp->segs.size() * sizeof(SegDesc) / 4);
-    lp->s_words = off;
+    chunk_launch(lp, target_warps);
+    return P_OK;
+}
+
+int plan_rechunk(LaunchPlan* lp, int target_warps) {
+    chunk_launch(lp, target_warps);
     return P_OK;
 }
 

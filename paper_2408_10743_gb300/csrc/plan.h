@@ -85,6 +85,8 @@ struct LaunchPlan {
     unsigned long long nchunks = 0;
     double codewords = 0;         // if every step completes
     int next_r = 0, next_jpos = 0;
+    std::vector<SegDesc> raw_segs;  // one segment per (step, i) before chunking
+    std::vector<int> raw_step_seg0;
 };
 
 enum { P_OK = 0, P_EINVAL = -1, P_ENOMEM = -2, P_EZERO = -6, P_ERANGE = -9 };
@@ -124,6 +126,9 @@ double plan_round_count(const Plan& p, int g, int r);
 // before (r, jpos).  Returns P_ERANGE if r exceeds the device walk's limits.
 int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int target_warps,
                 double max_codewords, LaunchPlan* lp);
+// Re-cuts a planned launch into chunks for another resident-warp count (the
+// batch engine gives each code of a slice its share of the warps).
+int plan_rechunk(LaunchPlan* lp, int target_warps);
 
 // What a code's state means after a launch that may have stopped early
 // (time budget).  next = chunks claimed so far (all claimed chunks finished).

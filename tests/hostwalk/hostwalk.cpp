@@ -318,3 +318,19 @@ extern "C" int hw_plan_segments(const uint8_t* gen, int n, int K, int field, int
     *nchunks = lp.nchunks;
     return (int)lp.segs.size();
 }
+
+// 1 if planning for tw1 warps and re-cutting for tw2 gives the same launch as
+// planning for tw2 directly, 0 if not, negative on a planning error.
+extern "C" int hw_rechunk_same(const uint8_t* gen, int n, int K, int field, int tw1, int tw2) {
+    Plan p;
+    int rc = plan_build(gen, n, K, field, &p);
+    if (rc) return rc;
+    LaunchPlan a, b;
+    if ((rc = plan_launch(p, 1, 0, plan_initial_bound(p), p.u0, tw1, 2e13, &a))) return rc;
+    if ((rc = plan_launch(p, 1, 0, plan_initial_bound(p), p.u0, tw2, 2e13, &b))) return rc;
+    plan_rechunk(&a, tw2);
+    if (a.segs.size() != b.segs.size() || a.nchunks != b.nchunks || a.step_seg0 != b.step_seg0 ||
+        a.step_chunk0 != b.step_chunk0 || a.s_words != b.s_words)
+        return 0;
+    return memcmp(a.segs.data(), b.segs.data(), a.segs.size() * sizeof(SegDesc)) == 0 ? 1 : 0;
+}

@@ -200,3 +200,23 @@ def test_ten_thousand_tiny_codes_in_one_batch():
         assert r["d"] == oracle.bruteforce(g, threads=1)[0]
     for c in codes:
         c.close()
+
+
+def test_wait_array_matches_wait():
+    """The structured-array read-back carries the same results as the
+    per-code dictionaries."""
+    gens = mixed_codes(40, 6)
+    codes = [dist.Code(g) for g in gens]
+    with dist.Batch() as b:
+        a = b.wait_array(b.submit(codes), timeout_s=60)
+    with dist.Batch() as b:
+        ref = b.wait(b.submit(codes), timeout_s=60)
+    assert len(a) == len(ref)
+    for g, row, r in zip(gens, a, ref):
+        assert int(row["d"]) == r["d"] and int(row["status"]) == 0
+        n = g.shape[1] // 2
+        w = row["witness"][:2 * n]
+        assert sym_weight_bits(w, n) == r["d"]
+        assert np.array_equal(np.bitwise_xor.reduce(g[row["coeffs"][:g.shape[0]].astype(bool)], axis=0), w)
+    for c in codes:
+        c.close()

@@ -48,6 +48,9 @@ def hw():
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_ulonglong)]
+    L.hw_rechunk_same.restype = ctypes.c_int
+    L.hw_rechunk_same.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.hw_solve_sliced.restype = ctypes.c_int
     L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -239,6 +242,16 @@ def test_plan_chunks_cover_every_rank_once(hw, warps):
             assert covered == pieces[0][4]
     if warps <= 64:
         assert split_seen
+
+
+def test_rechunk_equals_fresh_plan(hw):
+    """Re-cutting a launch for another warp count (the batch engine's per-code
+    share) gives exactly the launch planned for that count."""
+    for g in (synth.single_qc(0), synth.random_f2_code(40, 30, synth.Xoshiro256ss(5)), synth.single_f2(0)):
+        g = np.ascontiguousarray(g, dtype=np.uint8)
+        for tw1, tw2 in ((2432, 32), (2432, 300), (64, 2432), (7, 7)):
+            assert hw.hw_rechunk_same(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), g.shape[1] // 2,
+                                      g.shape[0], 2, tw1, tw2) == 1
 
 
 def solve_sliced(L, g, seed, one_step_plans, field=2, n_stab=0):

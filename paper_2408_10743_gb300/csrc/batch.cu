@@ -47,6 +47,8 @@ namespace {
 
 // A code with at most this many chunks is served entirely from the order list.
 const unsigned long long kSmallChunks = 64;
+// Host threads that plan a large admission.
+const size_t kPlanThreads = 8;
 
 struct Item {
     dist_code* c = nullptr;
@@ -176,14 +178,35 @@ int dist_batch::slice() {
     // since the codes of a slice share the warps -- again with about four
     // times its share of the estimated work in warps, so that a small code is
     // cut into a few longer lane chunks instead of thousands of tiny ones
-    std::vector<Item*> fresh;
-    for (Item* it : active) {
-        if (it->planned || it->done) continue;
-        const Plan& p = it->c->plan;
-        const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
-        int rc = plan_launch(p, it->r_next, it->j_next, it->L, u0, tw, 1e300, &it->lp);
-        if (rc) {
-            finish(it, rc == P_ERANGE ? DIST_ERANGE : DIST_EINVAL);
+    std::vector<Item*> todo, fresh;
+    for (Item* it : active)
+        if (!it->planned && !it->done) todo.push_back(it);
+    // plans are independent: large admissions are planned on several host
+    // threads (each writes only its own items)
+    std::vector<int> prc(todo.size(), P_OK);
+    auto plan_range = [&](size_t a, size_t b) {
+        for (size_t k = a; k < b; k++) {
+            Item* it = todo[k];
+            const Plan& p = it->c->plan;
+            const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
+            prc[k] = plan_launch(p, it->r_next, it->j_next, it->L, u0, tw, 1e300, &it->lp);
+        }
+    };
+    const size_t nthreads = todo.size() >= 256 ? std::min<size_t>(kPlanThreads, todo.size() / 128) : 1;
+    if (nthreads > 1) {
+        std::vector<std::thread> pool;
+        const size_t per = (todo.size() + nthreads - 1) / nthreads;
+        for (size_t t = 1; t < nthreads; t++)
+            pool.emplace_back(plan_range, std::min(todo.size(), t * per), std::min(todo.size(), (t + 1) * per));
+        plan_range(0, std::min(todo.size(), per));
+        for (std::thread& th : pool) th.join();
+    } else {
+        plan_range(0, todo.size());
+    }
+    for (size_t k = 0; k < todo.size(); k++) {
+        Item* it = todo[k];
+        if (prc[k]) {
+            finish(it, prc[k] == P_ERANGE ? DIST_ERANGE : DIST_EINVAL);
             continue;
         }
         it->planned = true;

@@ -454,6 +454,22 @@ def run_ours(args):
         e2e_s.append(time.perf_counter() - t0)
         e2e_cw.append(r2["codewords"])
     e2e_value = sum(e2e_cw) / sum(e2e_s)
+    # the same certified distance by the isometry method (Algorithm 3) on the
+    # GPU: the work per certified d of the two algorithms, outside the timed
+    # region
+    iso_cmp = None
+    if args.isometry:
+        code.solve_isometry()
+        its = [code.solve_isometry() for _ in range(3)]
+        best = min(its, key=lambda r: r["gpu_seconds"])
+        iso_cmp = {"algorithm": "isometry (a, b, a+b) + binary Brouwer-Zimmermann, one launch per step",
+                   "d": best["d"], "d_agrees": all(r["d"] == ds[0] for r in its),
+                   "codewords": best["codewords"], "matrices": best["n_gamma"], "rounds": best["rounds"],
+                   "launches": best["launches"], "kernel_ms": 1e3 * best["gpu_seconds"],
+                   "time_to_d_ms": 1e3 * best["seconds"],
+                   "codewords_per_s": best["codewords"] / max(best["gpu_seconds"], 1e-12),
+                   "work_vs_packages": best["codewords"] / (total_cw / args.steps),
+                   "time_vs_packages": best["seconds"] / statistics.mean(step_s)}
     code.close()
 
     kernel_s = sum(kern_s)
@@ -482,6 +498,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(ctypes.sizeof(dist.DistResult)),
                     "ms_per_step": 1e3 * statistics.mean(e2e_s)},
             "gpu_launches": int(sum(launches))}
+    if iso_cmp:
+        line["isometry"] = iso_cmp
     if args.batch_codes > 0:
         line["batch"] = batch_measure(dist, args.batch_codes)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -514,6 +532,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", type=float, default=8.0,
                     help="seconds for the chunk-size autotuner before timing (0 = defaults)")
+    ap.add_argument("--isometry", type=int, default=1,
+                    help="also time the isometry method on the same code (0 = skip)")
     ap.add_argument("--batch-codes", type=int, default=4096,
                     help="size of the batched-vs-one-per-launch comparison (0 = skip)")
     args = ap.parse_args()

@@ -114,6 +114,19 @@ int dist_solve_bounded(dist_code *c, dist_result *out, void *cuda_stream, double
 int dist_free(dist_code *c);
 
 /*
+ * dist_solve_isometry -- the same distance by the paper's isometry method
+ * (Algorithm 3, Saved_isometry) on the GPU, for comparison with the package
+ * method: the image (a, b, a + b) in F2^{3n} is searched with plain binary
+ * Brouwer-Zimmermann over systematic matrices on disjoint information sets
+ * (later ones may have deficient rank), one launch per (round, matrix).  The
+ * Hamming weight of the image is twice the symplectic weight, so d = U / 2.
+ * Exclusion (dist_set_exclude) applies.  Results as dist_solve; codewords
+ * counts binary combinations (rows of the image), n_gamma its matrices.
+ * DIST_ERANGE if certification needs more than 32 rows per combination.
+ */
+int dist_solve_isometry(dist_code *c, dist_result *out, void *cuda_stream);
+
+/*
  * Batched and served solving (step S7; the paper has no counterpart -- its
  * parallel version splits one code's combinations over CPU threads).
  *

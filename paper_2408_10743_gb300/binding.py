@@ -84,6 +84,7 @@ SIGNATURES = {
     "dist_solve": (ctypes.c_int, [_VP, ctypes.POINTER(DistResult), _VP]),
     "dist_solve_bounded": (ctypes.c_int, [_VP, ctypes.POINTER(DistResult), _VP, ctypes.c_double]),
     "dist_free": (ctypes.c_int, [_VP]),
+    "dist_solve_isometry": (ctypes.c_int, [_VP, ctypes.POINTER(DistResult), _VP]),
     "dist_plan_info_get": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.POINTER(PlanInfo)]),
     "dist_plan_unit": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -219,6 +220,12 @@ def dist_solve_bounded(handle, time_limit_s, stream=None):
     _check(lib().dist_solve_bounded(handle, ctypes.byref(r), _stream_handle(stream),
                                     float(time_limit_s)),
            "dist_solve_bounded", ok=(DIST_OK, DIST_EINCOMPLETE))
+    return r
+
+
+def dist_solve_isometry(handle, stream=None):
+    r = DistResult()
+    _check(lib().dist_solve_isometry(handle, ctypes.byref(r), _stream_handle(stream)), "dist_solve_isometry")
     return r
 
 
@@ -390,6 +397,10 @@ class Code:
         else:
             r = dist_solve(self._h, stream)
         return result_dict(r, self.n, self.K, self.field)
+
+    def solve_isometry(self, stream=None) -> dict:
+        """The same distance by the isometry method (Algorithm 3) on the GPU."""
+        return result_dict(dist_solve_isometry(self._h, stream), self.n, self.K, self.field)
 
     def close(self):
         if self._h:

@@ -17,8 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdist.so")
 
-CU_SOURCES = ["api.cu", "batch.cu", "enum.cu", "intpeak.cu", "noalloc.cu"]
-CPP_SOURCES = ["plan.cpp", "stab.cpp"]
+CU_SOURCES = ["api.cu", "batch.cu", "enum.cu", "intpeak.cu", "iso.cu", "noalloc.cu"]
+CPP_SOURCES = ["plan.cpp", "stab.cpp", "iso.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "-I", CSRC, "-I", INCLUDE]

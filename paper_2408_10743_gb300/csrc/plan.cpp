@@ -935,32 +935,20 @@ void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep) {
     ep->nchunks = lp.nchunks;
 }
 
-int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* coeffs) {
-    if (s.gamma >= p.gammas.size() || s.count == 0 || s.count > DIST_MAXR) return P_EINVAL;
-    const Gamma& G = p.gammas[s.gamma];
-    Vec c;
-    Coef k;
-    memset(&c, 0, sizeof c);
-    memset(&k, 0, sizeof k);
-    for (uint32_t t = 0; t < s.count; t++) {
-        int u = s.unit[t], e = s.digit[t];
-        const Unit* x = u < (int)G.A.size() ? &G.A[u]
-                        : (u - (int)G.A.size() < (int)G.B.size() ? &G.B[u - G.A.size()] : nullptr);
-        if (!x || e >= x->nrep) return P_EINVAL;
-        vxor(c, x->rep[e]);
-        cxor(k, x->coef[e]);
-    }
-    if ((int)s.weight != vec_weight(c, p.W)) return P_EINVAL;
+int plan_decode_coef(const Plan& p, const Coef& k, int weight, uint8_t* witness, uint8_t* coeffs,
+                     const Vec* expect) {
     if (!coef_outside(p, k)) return P_EINVAL;
-    // The coefficients must rebuild the codeword from the input rows.
-    Vec chk;
-    memset(&chk, 0, sizeof chk);
+    // the codeword the coefficients build from the input rows
+    Vec c;
+    memset(&c, 0, sizeof c);
     for (int i = 0; i < p.k_eff; i++) {
         int sym = bit(k.p[0], i) | (bit(k.p[1], i) << 1);
-        if (sym) vxor(chk, p.field == 2 ? p.input[p.kept[i]] : vscale(p.input[p.kept[i]], sym));
+        if (sym) vxor(c, p.field == 2 ? p.input[p.kept[i]] : vscale(p.input[p.kept[i]], sym));
     }
-    for (int w = 0; w < DIST_MAXW; w++)
-        if (chk.x[w] != c.x[w] || chk.z[w] != c.z[w]) return P_EINVAL;
+    if (weight != vec_weight(c, p.W)) return P_EINVAL;
+    if (expect)
+        for (int w = 0; w < DIST_MAXW; w++)
+            if (expect->x[w] != c.x[w] || expect->z[w] != c.z[w]) return P_EINVAL;
     if (witness) {
         for (int i = 0; i < p.n; i++) {
             if (p.field == 2) {
@@ -977,6 +965,26 @@ int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* 
             coeffs[p.kept[i]] = (uint8_t)(bit(k.p[0], i) | (bit(k.p[1], i) << 1));
     }
     return P_OK;
+}
+
+int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* coeffs) {
+    if (s.gamma >= p.gammas.size() || s.count == 0 || s.count > DIST_MAXR) return P_EINVAL;
+    const Gamma& G = p.gammas[s.gamma];
+    Vec c;
+    Coef k;
+    memset(&c, 0, sizeof c);
+    memset(&k, 0, sizeof k);
+    for (uint32_t t = 0; t < s.count; t++) {
+        int u = s.unit[t], e = s.digit[t];
+        const Unit* x = u < (int)G.A.size() ? &G.A[u]
+                        : (u - (int)G.A.size() < (int)G.B.size() ? &G.B[u - G.A.size()] : nullptr);
+        if (!x || e >= x->nrep) return P_EINVAL;
+        vxor(c, x->rep[e]);
+        cxor(k, x->coef[e]);
+    }
+    if ((int)s.weight != vec_weight(c, p.W)) return P_EINVAL;
+    // the coefficients must rebuild the same codeword from the input rows
+    return plan_decode_coef(p, k, (int)s.weight, witness, coeffs, &c);
 }
 
 }  // namespace dist

@@ -154,6 +154,12 @@ void plan_params(const Plan& p, const LaunchPlan& lp, EnumParams* ep);
 // or n bytes (F4); coeffs: K_in bytes over the input rows (F2 bits or F4
 // symbols).  Checks the weight and that the coefficients reproduce it.
 int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* coeffs);
+// The codeword with coefficients k over the basis: checks that it lies
+// outside S (exclusion), has symplectic weight `weight` and (if given) equals
+// *expect, then writes it and its coefficients over the input rows as
+// plan_decode does.
+int plan_decode_coef(const Plan& p, const Coef& k, int weight, uint8_t* witness, uint8_t* coeffs,
+                     const Vec* expect = nullptr);
 
 // Stabilizer-code front end (stab.cpp): from m generator rows (x | z) of the
 // classical stabilizer code S of an [[n, k]] qubit code, a generator matrix

@@ -47,6 +47,8 @@ def main(argv=None):
     ap.add_argument("--n-stab", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--time-limit", type=float, default=0.0)
+    ap.add_argument("--isometry", action="store_true",
+                    help="solve by the isometry method (Algorithm 3) instead of packages")
     args = ap.parse_args(argv)
     if args.batch:
         gens = synth.batch_codes(args.batch)
@@ -85,7 +87,7 @@ def main(argv=None):
         if args.n_stab:
             code.set_exclude(args.n_stab)
         for _ in range(args.repeat):
-            r = code.solve(time_limit_s=args.time_limit)
+            r = code.solve_isometry() if args.isometry else code.solve(time_limit_s=args.time_limit)
     out = {k: v for k, v in r.items() if k not in ("witness", "coeffs")}
     out["witness"] = "".join(str(int(v)) for v in r["witness"])
     print(json.dumps(out))

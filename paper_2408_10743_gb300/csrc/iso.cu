@@ -1,15 +1,12 @@
 // iso.cu -- the isometry method (Algorithm 3, Saved_isometry) on the GPU, a
 // second algorithm beside the package method of enum.cu.  It enumerates the
 // image code iso(C) in F2^{3n} with plain binary Brouwer-Zimmermann: every
-// codeword of round r of a matrix is the sum of r of its rows, and successive
-// subsets in revolving-door order differ by one row out and one row in.
+// codeword of round r of a matrix is the sum of r of its rows.
 //
 // One launch per step (round r of matrix j).  Each block stages the matrix's
 // rows, restricted to the columns outside its information set (a pivot row
 // adds exactly 1 on the set, a free row 0), in shared memory; lanes walk
-// rank ranges of r-subsets and keep the running sum in registers.  The
-// filter popcount(word 0) + (pivot rows chosen) bounds the weight from below;
-// only candidates below the running bound get a full popcount.
+// rank ranges of r-subsets in colexicographic order.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -19,8 +16,8 @@
 #include "../../include/dist.h"
 #include "code.h"
 #include "iso.h"
+#include "colex.cuh"
 #include "solve.h"
-#include "walk.cuh"
 
 namespace dist {
 
@@ -80,18 +77,57 @@ __device__ __noinline__ void iso_record(const IsoParams& P, uint32_t w, const ui
     }
 }
 
+// Full Hamming weight of the subset s (r rows) from the staged rows.
+template <int WORDS>
+__device__ __forceinline__ uint32_t iso_full(const uint32_t* srow, const uint8_t* spiv, const uint8_t* s, int r) {
+    uint32_t v[WORDS];
+#pragma unroll
+    for (int w = 0; w < WORDS; w++) v[w] = 0;
+    uint32_t np = 0;
+    for (int t = 0; t < r; t++) {
+#pragma unroll
+        for (int w = 0; w < WORDS; w++) v[w] ^= srow[s[t] * WORDS + w];
+        np += spiv[s[t]];
+    }
+#pragma unroll
+    for (int w = 0; w < WORDS; w++) np += (uint32_t)__popc(v[w]);
+    return np;
+}
+
+// Lane walk, colexicographic order: for a fixed top c[1..r-1] the lowest
+// element c1 runs over 0..c[1]-1, and the codeword is (sum of the top rows)
+// + row c1 -- one staged row per codeword.  Only the first four words of the
+// sum and the number of pivot rows in it are formed, in two levels: np +
+// popc(words 0-1) bounds the weight from below; if it is below the running
+// threshold, words 2-3 are added; only if np + popc(words 0-3) is still below
+// it is the full weight computed from the subset.  While the threshold is
+// high the second level runs almost always (four POPCs per codeword); once
+// it is near d the first level alone rejects nearly everything.  When c1 has
+// run out, the top moves to its colex successor (rows of the changed
+// elements out, the new ones in).
 template <int WORDS>
 __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoParams P) {
     extern __shared__ __align__(16) uint32_t iso_smem[];
-    uint32_t* srow = iso_smem;                                          // [K][WORDS]
-    uint8_t* spiv = reinterpret_cast<uint8_t*>(iso_smem + P.K * WORDS);  // [K]
-    for (int t = threadIdx.x; t < P.K * WORDS; t += blockDim.x) {
+    const int K = P.K;
+    uint4* sfil = reinterpret_cast<uint4*>(iso_smem);       // [K]: words 0-3
+    uint32_t* snp = reinterpret_cast<uint32_t*>(sfil + K);  // [K]: 1 for a pivot row
+    uint32_t* srow = snp + K;                               // [K][WORDS]
+    uint8_t* spiv = reinterpret_cast<uint8_t*>(srow + K * WORDS);
+    for (int t = threadIdx.x; t < K * WORDS; t += blockDim.x) {
         const int row = t / WORDS, w = t - row * WORDS;
         srow[t] = w < P.words ? P.rows[(size_t)row * P.words + w] : 0u;
     }
-    for (int t = threadIdx.x; t < P.K; t += blockDim.x) spiv[t] = P.piv[t];
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+        spiv[t] = P.piv[t];
+        snp[t] = P.piv[t];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < K; t += blockDim.x)
+        sfil[t] = make_uint4(srow[t * WORDS], WORDS > 1 ? srow[t * WORDS + 1] : 0u,
+                             WORDS > 2 ? srow[t * WORDS + 2] : 0u, WORDS > 3 ? srow[t * WORDS + 3] : 0u);
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const int r = P.r;
     volatile uint32_t* Up = &P.scr->U;
     uint32_t thr = DIST_WINF;
     for (;;) {
@@ -99,42 +135,92 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
         if (lane == 0) chunk = atomicAdd(&P.scr->next_chunk, 1ull);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= P.nchunks) break;
-        unsigned long long done = 0;
+        // every lane of the warp runs spl iterations (lanes past the end of
+        // their range idle), so the warp stays converged and the rare carries
+        // are entered together
         const unsigned long long lo = (chunk * 32ull + (unsigned long long)lane) * P.spl;
-        if (lo < P.nsub) {
-            const unsigned long long hi = lo + P.spl < P.nsub ? lo + P.spl : P.nsub;
-            uint8_t s[DIST_MAXR];
-            rd_unrank(P.binom, DIST_MAXR + 1, P.K, lo, P.r, s);
-            uint32_t v[WORDS];
-#pragma unroll
-            for (int w = 0; w < WORDS; w++) v[w] = 0;
-            int np = 0;
-            for (int t = 0; t < P.r; t++) {
-#pragma unroll
-                for (int w = 0; w < WORDS; w++) v[w] ^= srow[s[t] * WORDS + w];
-                np += spiv[s[t]];
+        const uint32_t left = lo < P.nsub ? (uint32_t)(min(lo + P.spl, P.nsub) - lo) : 0u;
+        uint8_t c[DIST_MAXR];
+        uint4 b = make_uint4(0u, 0u, 0u, 0u);  // words 0-3 of the top c[1..r-1]
+        uint32_t npb = 0;
+        int c1 = 0, c2 = K, c3 = K;  // c[0], c[1] (K if r < 2), c[2] (K if r < 3) in registers
+        if (left) {
+            colex_unrank(P.binom, DIST_MAXR + 1, K, lo, r, c);
+            for (int t = 1; t < r; t++) {
+                const uint4 q = sfil[c[t]];
+                b.x ^= q.x;
+                b.y ^= q.y;
+                b.z ^= q.z;
+                b.w ^= q.w;
+                npb += snp[c[t]];
             }
-            thr = min(thr, *Up);
-            for (unsigned long long idx = lo; idx < hi; ++idx) {
-                const uint32_t w0 = (uint32_t)np + (uint32_t)__popc(v[0]);
-                if (w0 < thr) {
-                    uint32_t full = (uint32_t)np;
-#pragma unroll
-                    for (int w = 0; w < WORDS; w++) full += (uint32_t)__popc(v[w]);
-                    if (full < thr) iso_record(P, full, s, thr);
-                }
-                if (idx + 1 < hi) {
-                    int out, in;
-                    rd_next_delta(s, P.r, P.K, out, in);
-                    if (out < 0) break;  // no successor (cannot happen inside [lo, hi))
-#pragma unroll
-                    for (int w = 0; w < WORDS; w++) v[w] ^= srow[out * WORDS + w] ^ srow[in * WORDS + w];
-                    np += (int)spiv[in] - (int)spiv[out];
-                }
-                if (((idx - lo) & 255) == 255) thr = min(thr, *Up);
-            }
-            done = hi - lo;
+            c1 = c[0];
+            if (r >= 2) c2 = c[1];
+            if (r >= 3) c3 = c[2];
         }
+        thr = min(thr, *Up);
+        for (uint32_t k = 0; k < P.spl; k++) {
+            const bool act = k < left;
+            if (act) {
+                const uint4 q = sfil[c1];
+                uint32_t w = npb + snp[c1] + (uint32_t)__popc(b.x ^ q.x) + (uint32_t)__popc(b.y ^ q.y);
+                if (w < thr) {
+                    if (WORDS > 2) w += (uint32_t)__popc(b.z ^ q.z) + (uint32_t)__popc(b.w ^ q.w);
+                    if (w < thr) {
+                        c[0] = (uint8_t)c1;
+                        if (r >= 2) c[1] = (uint8_t)c2;
+                        if (r >= 3) c[2] = (uint8_t)c3;
+                        const uint32_t full = WORDS > 4 ? iso_full<WORDS>(srow, spiv, c, r) : w;
+                        if (full < thr) iso_record(P, full, c, thr);
+                    }
+                }
+            }
+            const bool carry = act && k + 1 < left && c1 + 1 >= c2;
+            if (act && !carry) c1++;
+            if (__any_sync(0xffffffffu, carry) && carry) {
+                // c1 ran out: the top moves to its colex successor, usually
+                // c[1] alone (one row out, one in)
+                if (c2 + 1 < c3) {
+                    const uint4 qo = sfil[c2], qi = sfil[c2 + 1];
+                    b.x ^= qo.x ^ qi.x;
+                    b.y ^= qo.y ^ qi.y;
+                    b.z ^= qo.z ^ qi.z;
+                    b.w ^= qo.w ^ qi.w;
+                    npb = npb - snp[c2] + snp[c2 + 1];
+                    c2++;
+                } else {
+                    c[0] = (uint8_t)(c2 - 1);
+                    c[1] = (uint8_t)c2;
+                    if (r >= 3) c[2] = (uint8_t)c3;
+                    int jj = 1;
+                    while (jj < r && c[jj] + 1 >= (jj + 1 < r ? (int)c[jj + 1] : K)) jj++;
+                    if (jj < r) {  // (jj = r only after the last subset: cannot happen here)
+                        for (int t = 1; t <= jj; t++) {
+                            const uint4 qq = sfil[c[t]];
+                            b.x ^= qq.x;
+                            b.y ^= qq.y;
+                            b.z ^= qq.z;
+                            b.w ^= qq.w;
+                            npb -= snp[c[t]];
+                        }
+                        colex_carry(c, r, K);
+                        for (int t = 1; t <= jj; t++) {
+                            const uint4 qq = sfil[c[t]];
+                            b.x ^= qq.x;
+                            b.y ^= qq.y;
+                            b.z ^= qq.z;
+                            b.w ^= qq.w;
+                            npb += snp[c[t]];
+                        }
+                        c2 = c[1];
+                        c3 = r >= 3 ? c[2] : K;
+                    }
+                    thr = min(thr, *Up);
+                }
+                c1 = 0;
+            }
+        }
+        unsigned long long done = left;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
         if (lane == 0 && done) atomicAdd(&P.scr->codewords, done);
@@ -143,7 +229,7 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
 
 template <int WORDS>
 cudaError_t iso_launch_w(const IsoParams& P, int sms, cudaStream_t st) {
-    const size_t smem = (size_t)P.K * WORDS * 4 + (size_t)P.K + 16;
+    const size_t smem = (size_t)P.K * 20 + (size_t)P.K * WORDS * 4 + (size_t)P.K + 16;
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, iso_kernel<WORDS>, 256, smem) != cudaSuccess)
         return cudaErrorUnknown;

@@ -88,54 +88,6 @@ DIST_HD void rd_unrank(const unsigned long long* B, int stride, int n, unsigned 
 
 // Successor in revolving-door order (Knuth's Algorithm R, steps R3-R5) of
 // the ascending t-subset s of {0..n-1}.  The caller never steps past the last.
-// rd_next that also reports the element that left the subset and the one
-// that entered it (each step of Algorithm R swaps exactly one pair; at the
-// last subset nothing changes and out = in = -1).
-DIST_HD void rd_next_delta(uint8_t* s, int t, int n, int& out, int& in) {
-#define DIST_CJ(j) ((j) <= t ? (int)s[(j)-1] : n)
-    int j;
-    out = in = -1;
-    if (t & 1) {
-        if (s[0] + 1 < DIST_CJ(2)) {
-            out = s[0];
-            in = ++s[0];
-            return;
-        }
-        j = 2;
-        goto r4;
-    } else {
-        if (s[0] > 0) {
-            out = s[0];
-            in = --s[0];
-            return;
-        }
-        j = 2;
-        goto r5;
-    }
-r4:
-    if (j > t) return;
-    if (DIST_CJ(j) >= j) {  // {c_{j-1}, c_j} -> {j - 2, c_{j-1}}
-        out = s[j - 1];
-        in = j - 2;
-        s[j - 1] = s[j - 2];
-        s[j - 2] = (uint8_t)(j - 2);
-        return;
-    }
-    j++;
-r5:
-    if (j > t) return;
-    if (DIST_CJ(j) + 1 < DIST_CJ(j + 1)) {  // {c_{j-1}, c_j} -> {c_j, c_j + 1}
-        out = s[j - 2];
-        in = s[j - 1] + 1;
-        s[j - 2] = s[j - 1];
-        s[j - 1]++;
-        return;
-    }
-    j++;
-    goto r4;
-#undef DIST_CJ
-}
-
 DIST_HD void rd_next(uint8_t* s, int t, int n) {
 #define DIST_CJ(j) ((j) <= t ? (int)s[(j)-1] : n)
     int j;

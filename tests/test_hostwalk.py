@@ -48,6 +48,8 @@ def hw():
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_ulonglong)]
+    L.hw_colex_walk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_uint8)]
     L.hw_rechunk_same.restype = ctypes.c_int
     L.hw_rechunk_same.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -242,6 +244,21 @@ def test_plan_chunks_cover_every_rank_once(hw, warps):
             assert covered == pieces[0][4]
     if warps <= 64:
         assert split_seen
+
+
+def test_colex_walk(hw):
+    """The isometry kernel's order: unranking by the combinatorial number
+    system and stepping (lowest element up, then colex_carry) visit the
+    t-subsets in colexicographic order from any start rank."""
+    from itertools import combinations
+    for n, t in ((1, 1), (6, 1), (6, 2), (7, 3), (8, 4), (9, 5), (10, 6), (12, 7), (9, 9)):
+        seq = sorted(combinations(range(n), t), key=lambda c: c[::-1])
+        for start in sorted({0, 1, len(seq) // 3, len(seq) - 1} & set(range(len(seq)))):
+            cnt = len(seq) - start
+            out = (ctypes.c_uint8 * (cnt * t))()
+            hw.hw_colex_walk(n, t, start, cnt, out)
+            got = [tuple(out[k * t:(k + 1) * t]) for k in range(cnt)]
+            assert got == seq[start:], (n, t, start)
 
 
 def test_rechunk_equals_fresh_plan(hw):

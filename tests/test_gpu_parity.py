@@ -239,3 +239,13 @@ def test_tuning_changes_speed_not_results(stream):
     finally:
         dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"],
                              saved["lane_floor_log2"])
+
+
+def test_wide_codes_four_words(stream):
+    """n = 100..128 (four words per plane: the two-word filter and pivots
+    beyond word 1) with few rows, against the oracle's brute force."""
+    for t, (n, K) in enumerate(((100, 16), (128, 18), (97, 20), (128, 24))):
+        g = synth.random_f2_code(n, K, synth.Xoshiro256ss(8100 + t))
+        r = gpu(g, stream=stream)
+        assert r["d"] == oracle.bruteforce(g)[0], (n, K)
+        check_witness(g, r)

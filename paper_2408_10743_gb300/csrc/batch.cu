@@ -212,7 +212,9 @@ int dist_batch::slice() {
         it->planned = true;
         fresh.push_back(it);
     }
-    if (!fresh.empty()) {
+    // (only for run-to-completion launches: with a slice budget, short
+    // chunks keep the slices short and the latency of new requests low)
+    if (!fresh.empty() && opts.slice_ms <= 0) {
         double all = 0;
         for (Item* it : active)
             if (!it->done) all += estimated_work(it);

@@ -690,6 +690,10 @@ int plan_set_exclude(Plan* p, int n_stab) {
 // Cuts the raw segments of a planned launch into warp-chunks for
 // target_warps resident warps (see plan_launch) and places the segment table
 // in shared memory.
+// Cost of a codeword on the generic path (full weights from scratch) in
+// fast-path codewords, for sizing chunks.
+static constexpr double kGenericCost = 32.0;
+
 static void chunk_launch(LaunchPlan* lp, int target_warps) {
     // Chunks: each segment is cut into about chunks_per_warp (default 6)
     // warp-chunks per resident warp, so that every segment spreads over the
@@ -724,8 +728,12 @@ static void chunk_launch(LaunchPlan* lp, int target_warps) {
         if (DIST_FAST_PATH((int)sd.i, lp->proj)) {
             const double spread = seg_cw / (32.0 * (double)tw);
             per_lane = std::max(per_lane, std::min((double)(1u << tun.lane_floor_log2), spread));
+            per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2));
+        } else {
+            // a generic-path codeword costs tens of fast-path ones: cap its
+            // lanes lower, so that a chunk lasts about as long either way
+            per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2) / kGenericCost);
         }
-        per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2));
         double spl_d = per_lane / (double)sd.codes;
         unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
         if (spl > (1ull << 30)) spl = 1ull << 30;

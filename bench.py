@@ -508,6 +508,11 @@ def run_ours(args):
         line["isometry"] = iso_cmp
     if args.batch_codes > 0:
         line["batch"] = batch_measure(dist, args.batch_codes)
+    if args.serve_window > 0 and rank == 0:
+        # the served workload (Poisson stream, continuous batching), short
+        # window; --workload serve runs the full-length version and sweeps
+        line["serve"] = serve_measure(dist, args.serve_rate, args.serve_window, args.slice_ms, args.drain,
+                                      args.time_limit, args.check_budget, check_total_s=10.0)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, field, args.cpu_budget)
     if rank == 0:
@@ -538,6 +543,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", type=float, default=8.0,
                     help="seconds for the chunk-size autotuner before timing (0 = defaults)")
+    ap.add_argument("--serve-window", type=float, default=1.0,
+                    help="default run: seconds of served stream to report (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=800.0,
+                    help="default run: requests per second of that stream")
     ap.add_argument("--isometry", type=int, default=1,
                     help="also time the isometry method on the same code (0 = skip)")
     ap.add_argument("--batch-codes", type=int, default=4096,

@@ -379,13 +379,13 @@ class Code:
     @classmethod
     def from_stabilizers(cls, stabilizers):
         """The normalizer code of a qubit stabilizer code, with S excluded:
-        solve() returns d(Q)."""
+        solve() returns d(Q).  The code's rows are those of dist_normalizer
+        (a basis of S first), which is what the returned coefficients index."""
         gen, n_stab = dist_normalizer(stabilizers)
         self = cls.__new__(cls)
         self.n, self.K, self.field = gen.shape[1] // 2, gen.shape[0], DIST_F2
-        self._h = None
-        self._h = dist_init_stabilizer(stabilizers)
         self.n_stab = n_stab
+        self._h = dist_init_stabilizer(stabilizers)
         return self
 
     def set_exclude(self, n_stab: int):

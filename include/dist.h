@@ -200,6 +200,15 @@ typedef struct {
 int dist_set_tuning(const dist_tuning *t);
 int dist_get_tuning(dist_tuning *t);
 int dist_autotune(dist_tuning *best, double budget_s);
+/*
+ * Information-set search of the planner (process-wide): for a code whose
+ * estimated work exceeds 5e8 codewords and whose enumerated matrices have
+ * free rows, dist_init also diagonalizes with up to `trials` seeded random
+ * qubit orders and keeps the plan with the least estimated work (0 = index
+ * order only; default 8; range 0..256).  Affects speed, never results.
+ */
+int dist_set_plan_search(int trials);
+int dist_get_plan_search(void);
 /* Same search, timed on the caller's codes (initialised on the current
  * device, not in a batch): tunes for a known workload. */
 int dist_autotune_codes(dist_code *const *codes, int count, double budget_s, dist_tuning *best);

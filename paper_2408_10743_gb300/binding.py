@@ -108,6 +108,8 @@ SIGNATURES = {
     "dist_set_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
     "dist_get_tuning": (ctypes.c_int, [ctypes.POINTER(Tuning)]),
     "dist_autotune": (ctypes.c_int, [ctypes.POINTER(Tuning), ctypes.c_double]),
+    "dist_set_plan_search": (ctypes.c_int, [ctypes.c_int]),
+    "dist_get_plan_search": (ctypes.c_int, []),
     "dist_autotune_codes": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_double,
                                            ctypes.POINTER(Tuning)]),
     "dist_version": (ctypes.c_char_p, []),
@@ -321,6 +323,14 @@ def dist_batch_destroy(batch):
 def dist_set_tuning(chunks_per_warp=0, lane_cap_log2=0, lane_floor_log2=0):
     t = Tuning(chunks_per_warp, lane_cap_log2, lane_floor_log2, 0.0)
     return _check(lib().dist_set_tuning(ctypes.byref(t)), "dist_set_tuning")
+
+
+def dist_set_plan_search(trials):
+    return _check(lib().dist_set_plan_search(int(trials)), "dist_set_plan_search")
+
+
+def dist_get_plan_search() -> int:
+    return lib().dist_get_plan_search()
 
 
 def dist_get_tuning() -> dict:

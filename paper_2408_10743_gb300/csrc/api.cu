@@ -449,6 +449,14 @@ int dist_set_tuning(const dist_tuning* t) {
     return DIST_OK;
 }
 
+int dist_set_plan_search(int trials) {
+    if (trials < 0) return DIST_EINVAL;
+    plan_set_search_trials(trials);
+    return DIST_OK;
+}
+
+int dist_get_plan_search(void) { return plan_search_trials(); }
+
 int dist_get_tuning(dist_tuning* t) {
     if (!t) return DIST_EINVAL;
     const Tuning cur = tuning_get();

@@ -38,6 +38,10 @@
 // One claimable record per weight value: the first thread that finds a
 // codeword of weight w (that passes the optional exclusion) writes how to
 // rebuild it -- generator matrix, chosen units and the representative of each.
+// WitnessSlot.gamma of a seed codeword that is not a representative of the
+// plan's matrices (kept by the planner from another diagonalization).
+#define DIST_SEED_GAMMA 0xFFFFFFFFu
+
 struct WitnessSlot {
     uint32_t claim;               // 0 = free
     uint32_t gamma;               // generator matrix index (in the plan)

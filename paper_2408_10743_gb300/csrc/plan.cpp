@@ -255,7 +255,7 @@ static inline bool rs_any(const RowSet& a) {
     return o != 0;
 }
 
-static void diag_f2(const Plan& p, std::vector<char>& used, Gamma& G) {
+static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<char>& used, Gamma& G) {
     const int k = p.k_eff, n = p.n;
     std::vector<Vec> R = p.basis;
     std::vector<Coef> C(k);
@@ -299,7 +299,8 @@ static void diag_f2(const Plan& p, std::vector<char>& used, Gamma& G) {
     std::vector<U> units;
     for (;;) {
         int best_q = -1, best_rank = 0;
-        for (int q = 0; q < n; q++) {
+        for (int t = 0; t < n; t++) {
+            const int q = qorder[t];
             if (used[q]) continue;
             const RowSet a = rs_and(cx[q], unpiv), b = rs_and(cz[q], unpiv);
             const int nz = (int)rs_any(rs_andnot(a, b)) + (int)rs_any(rs_andnot(b, a)) + (int)rs_any(rs_and(a, b));
@@ -377,7 +378,7 @@ static void diag_f2(const Plan& p, std::vector<char>& used, Gamma& G) {
 // coordinates, lowest coordinate first.  Every row becomes a unit with the
 // representatives g, alpha g, alpha^2 g; pivot rows are packages (weight >= 1
 // on their pivot coordinate in any combination that uses them), the rest free.
-static void diag_f4(const Plan& p, std::vector<char>& used, Gamma& G) {
+static void diag_f4(const Plan& p, const std::vector<int>& qorder, std::vector<char>& used, Gamma& G) {
     const int k = p.k_eff, n = p.n;
     std::vector<Vec> R = p.basis;
     std::vector<Coef> C(k);
@@ -388,7 +389,8 @@ static void diag_f4(const Plan& p, std::vector<char>& used, Gamma& G) {
     std::vector<char> piv(k, 0);
     std::vector<std::pair<int, int>> order;  // (row, qubit)
     int npiv = 0;
-    for (int q = 0; q < n && npiv < k; q++) {
+    for (int t = 0; t < n && npiv < k; t++) {
+        const int q = qorder[t];
         if (used[q]) continue;
         int g = -1;
         for (int i = 0; i < k && g < 0; i++)
@@ -565,7 +567,7 @@ int plan_initial_bound(const Plan& p) { return std::max(1, bound_for(p, p.J, 0, 
 // Choice of J: among the matrices sorted by free rows, the prefix whose
 // estimated work to lift the bound to d_est is smallest.  Any nonempty J is
 // correct; this only decides speed.
-static void choose_J(Plan* p) {
+static double choose_J(Plan* p) {
     std::vector<int> cand;
     for (size_t g = 0; g < p->gammas.size(); g++) cand.push_back((int)g);
     std::stable_sort(cand.begin(), cand.end(),
@@ -588,6 +590,86 @@ static void choose_J(Plan* p) {
         }
     }
     p->J = bestJ;
+    return best;
+}
+
+// Estimated work (codewords) above which plan_build tries other qubit
+// orders, and how many: a search trial costs about one diagonalization (tens
+// of microseconds), a round it saves often tens of millions of codewords.
+static constexpr double kSearchWork = 5e8;
+static std::atomic<int> g_plan_search_trials{8};
+
+int plan_search_trials() { return g_plan_search_trials.load(); }
+void plan_set_search_trials(int t) { g_plan_search_trials.store(std::max(0, std::min(t, 256))); }
+
+// Does some matrix of J have free rows (a round that adds less than 1 to L)?
+static bool free_rows_in_J(const Plan& p) {
+    for (int g : p.J)
+        if (p.gammas[g].f > 0) return true;
+    return false;
+}
+
+// The codeword a seed slot names (a representative, or the plan's seed).
+static void slot_codeword(const Plan& p, const WitnessSlot& s, Vec* v, Coef* k) {
+    if (s.gamma == DIST_SEED_GAMMA) {
+        *v = p.seed_vec;
+        *k = p.seed_coef;
+        return;
+    }
+    const Gamma& G = p.gammas[s.gamma];
+    const Unit& x = s.unit[0] < G.A.size() ? G.A[s.unit[0]] : G.B[s.unit[0] - G.A.size()];
+    *v = x.rep[s.digit[0]];
+    *k = x.coef[s.digit[0]];
+}
+
+// S2 with the unused qubits considered in qorder, then the seed U, d_est and
+// J (no device tables yet).  A known codeword lighter than every
+// representative of this diagonalization becomes the seed.  *work = the
+// estimated codewords to lift the bound to d_est.
+static int diagonalize(Plan* p, const std::vector<int>& qorder, double* work, int known_w = DIST_WINF,
+                       const Vec* known_v = nullptr, const Coef* known_k = nullptr) {
+    const int n = p->n, field = p->field;
+    p->gammas.clear();
+    std::vector<char> used(n, 0);
+    for (int j = 0; j < DIST_MAXGAMMA; j++) {
+        Gamma G;
+        std::vector<char> u2 = used;
+        if (field == 2) diag_f2(*p, qorder, u2, G);
+        else diag_f4(*p, qorder, u2, G);
+        if (G.npack == 0) break;
+        if (G.A.size() > 255 || G.units() > DIST_MAXU) return P_ERANGE;
+        used = u2;
+        p->gammas.push_back(std::move(G));
+    }
+    if (p->gammas.empty()) return P_EZERO;
+    // The lightest representative is a codeword: it seeds the upper bound.
+    p->u0 = DIST_WINF;
+    lightest_rep(*p, false, &p->u0, &p->u0_slot);
+    if (known_v && known_w < p->u0) {
+        p->u0 = known_w;
+        memset(&p->u0_slot, 0, sizeof p->u0_slot);
+        p->u0_slot.claim = 1;
+        p->u0_slot.gamma = DIST_SEED_GAMMA;
+        p->u0_slot.weight = (uint32_t)known_w;
+        p->seed_vec = *known_v;
+        p->seed_coef = *known_k;
+    }
+    // Expected number of nonzero codewords of weight <= w in a random code of
+    // the same size: 2^(K2 - 2n) * sum_v C(n, v) 3^v.  d_est = first w where it
+    // reaches 1, capped by the lightest known codeword.
+    const int K2 = field == 2 ? p->k_eff : 2 * p->k_eff;
+    double acc = 0;
+    p->d_est = n;
+    for (int w = 1; w <= n; w++) {
+        acc += dbinom(n, w) * pow(3.0, w);
+        if (log2(acc) + K2 - 2.0 * n >= 0) {
+            p->d_est = w;
+            break;
+        }
+    }
+    p->d_est = std::max(1, std::min(p->d_est, p->u0));
+    *work = choose_J(p);
+    return P_OK;
 }
 
 int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
@@ -606,19 +688,56 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
     if (p->k_eff == 0) return P_EZERO;
     p->CW = (p->k_eff + 31) / 32;
 
-    std::vector<char> used(n, 0);
-    for (int j = 0; j < DIST_MAXGAMMA; j++) {
-        Gamma G;
-        std::vector<char> u2 = used;
-        if (field == 2) diag_f2(*p, u2, G);
-        else diag_f4(*p, u2, G);
-        if (G.npack == 0) break;
-        if (G.A.size() > 255 || G.units() > DIST_MAXU) return P_ERANGE;
-        used = u2;
-        build_device_tables(*p, G);
-        p->gammas.push_back(std::move(G));
+    // S2 with the qubits in index order; for a code whose estimated work is
+    // large, also with a few seeded random qubit orders (information sets can
+    // be chosen freely: only speed depends on them), keeping the plan with
+    // the least estimated work.  A later matrix on the leftover qubits often
+    // has free rows, and each free row costs a whole round; another order
+    // can leave it none.
+    std::vector<int> qorder(n);
+    for (int q = 0; q < n; q++) qorder[q] = q;
+    double work = 0;
+    rc = diagonalize(p, qorder, &work);
+    if (rc) return rc;
+    const int trials = plan_search_trials();
+    if (trials > 0 && work > kSearchWork && free_rows_in_J(*p)) {
+        // the lightest codeword seen so far is an upper bound for every plan
+        int kw = p->u0;
+        Vec kv;
+        Coef kk;
+        slot_codeword(*p, p->u0_slot, &kv, &kk);
+        uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)n * 0x100000001B3ull ^ (uint64_t)K;
+        for (int t = 0; t < trials && free_rows_in_J(*p); t++) {
+            for (int q = n - 1; q > 0; q--) {  // Fisher-Yates with xorshift64*
+                x ^= x >> 12;
+                x ^= x << 25;
+                x ^= x >> 27;
+                const int j = (int)(((x * 0x2545F4914F6CDD1Dull) >> 33) % (uint64_t)(q + 1));
+                std::swap(qorder[q], qorder[j]);
+            }
+            Plan alt;
+            alt.n = p->n;
+            alt.field = p->field;
+            alt.K_in = p->K_in;
+            alt.W = p->W;
+            alt.CW = p->CW;
+            alt.k_eff = p->k_eff;
+            alt.input = p->input;
+            alt.kept = p->kept;
+            alt.basis = p->basis;
+            double w2 = 0;
+            if (diagonalize(&alt, qorder, &w2, kw, &kv, &kk) != P_OK) continue;
+            if (alt.u0 < kw) {  // a lighter representative: the new best seed
+                kw = alt.u0;
+                slot_codeword(alt, alt.u0_slot, &kv, &kk);
+            }
+            if (w2 < work) {
+                work = w2;
+                *p = std::move(alt);
+            }
+        }
     }
-    if (p->gammas.empty()) return P_EZERO;
+    for (Gamma& G : p->gammas) build_device_tables(*p, G);
 
     size_t off = 0;
     for (Gamma& G : p->gammas) {
@@ -643,27 +762,8 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
         std::copy(G.dev_r0.begin(), G.dev_r0.end(), p->tables.begin() + G.r0_off);
         std::copy(G.dev_r1.begin(), G.dev_r1.end(), p->tables.begin() + G.r1_off);
     }
-
-    // The lightest representative is a codeword: it seeds the upper bound.
-    p->u0 = DIST_WINF;
-    lightest_rep(*p, false, &p->u0, &p->u0_slot);
-    // Expected number of nonzero codewords of weight <= w in a random code of
-    // the same size: 2^(K2 - 2n) * sum_v C(n, v) 3^v.  d_est = first w where it
-    // reaches 1, capped by the lightest representative.
-    const int K2 = field == 2 ? p->k_eff : 2 * p->k_eff;
-    double acc = 0;
-    p->d_est = n;
-    for (int w = 1; w <= n; w++) {
-        acc += dbinom(n, w) * pow(3.0, w);
-        if (log2(acc) + K2 - 2.0 * n >= 0) {
-            p->d_est = w;
-            break;
-        }
-    }
-    p->d_est = std::max(1, std::min(p->d_est, p->u0));
     p->u0_excl = p->u0;
     p->u0_excl_slot = p->u0_slot;
-    choose_J(p);
     return P_OK;
 }
 
@@ -682,6 +782,10 @@ int plan_set_exclude(Plan* p, int n_stab) {
     if (n_stab > 0) {
         p->u0_excl = DIST_WINF;
         lightest_rep(*p, true, &p->u0_excl, &p->u0_excl_slot);
+        if (p->u0_slot.gamma == DIST_SEED_GAMMA && p->u0 < p->u0_excl && coef_outside(*p, p->seed_coef)) {
+            p->u0_excl = p->u0;
+            p->u0_excl_slot = p->u0_slot;
+        }
     }
     if (n_stab > 0 && p->s_rank == p->k_eff) return P_EZERO;
     return P_OK;
@@ -976,6 +1080,10 @@ int plan_decode_coef(const Plan& p, const Coef& k, int weight, uint8_t* witness,
 }
 
 int plan_decode(const Plan& p, const WitnessSlot& s, uint8_t* witness, uint8_t* coeffs) {
+    if (s.gamma == DIST_SEED_GAMMA) {  // the planner's seed codeword
+        if ((int)s.weight != vec_weight(p.seed_vec, p.W)) return P_EINVAL;
+        return plan_decode_coef(p, p.seed_coef, (int)s.weight, witness, coeffs, &p.seed_vec);
+    }
     if (s.gamma >= p.gammas.size() || s.count == 0 || s.count > DIST_MAXR) return P_EINVAL;
     const Gamma& G = p.gammas[s.gamma];
     Vec c;

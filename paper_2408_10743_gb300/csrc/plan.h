@@ -69,6 +69,8 @@ struct Plan {
     int u0 = 0;                   // smallest weight among all representatives
     int u0_excl = 0;              // same, among representatives outside S (exclusion)
     WitnessSlot u0_slot{}, u0_excl_slot{};  // which representative reaches them
+    Vec seed_vec{};               // a slot with gamma DIST_SEED_GAMMA names this codeword
+    Coef seed_coef{};
     int d_est = 0;                // random-code estimate used to choose J
 };
 
@@ -101,6 +103,12 @@ struct Tuning {
     int lane_floor_log2 = 12;
 };
 Tuning tuning_get();
+
+// Qubit orders plan_build tries for a code whose estimated work exceeds
+// 5e8 codewords and whose matrices in J have free rows (0 = index order
+// only; default 8, range 0..256; process-wide).
+int plan_search_trials();
+void plan_set_search_trials(int t);
 void tuning_set(const Tuning& t);
 
 // S1 + S2 + choice of J.  gen layout: field 2 -> K x 2n bytes {0,1} (x | z);

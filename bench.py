@@ -8,9 +8,9 @@ rounds, all generator matrices, witness) through the C ABI.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload qc72|f2_24|f4_40]
 
-Multi-GPU: one process per GPU (torchrun); rank r solves its own code of the
-same workload (seed index r) -- independent problems, no collective on the data
-path ("scaling": "weak").  Rank 0 prints one JSON line.
+Multi-GPU: one process per GPU (torchrun); every rank solves the workload
+code as an independent replica -- no collective on the data path ("scaling":
+"weak").  Rank 0 prints one JSON line.
 
 --impl reference times the CPU oracle (isometry + plain Brouwer-Zimmermann) on
 the host cores, a bounded sample per step.
@@ -411,13 +411,13 @@ def run_ours(args):
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
 
-    def one_step(timed):
+    def one_step(timed, c=code):
         with torch.cuda.stream(stream):
             flush.fill_(7)  # evict L2 between steps (outside the timed events)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res = code.solve(stream=stream)
+            res = c.solve(stream=stream)
             e1.record(stream)
         e1.synchronize()
         return res, e0.elapsed_time(e1) * 1e-3
@@ -476,6 +476,31 @@ def run_ours(args):
                    "codewords_per_s": best["codewords"] / max(best["gpu_seconds"], 1e-12),
                    "work_vs_packages": best["codewords"] / (total_cw / args.steps),
                    "time_vs_packages": best["seconds"] / statistics.mean(step_s)}
+    # the same code planned on the identity qubit order only (no
+    # information-set search): a longer enumeration of the same kernel, the
+    # single-code roofline on a launch long enough to fill the GPU
+    greedy = None
+    if args.greedy_plan:
+        trials = dist.dist_get_plan_search()
+        dist.dist_set_plan_search(0)
+        try:
+            with dist.Code(g, field) as cg:
+                for _ in range(args.warmup):
+                    one_step(False, cg)
+                gr = [one_step(True, cg) for _ in range(max(3, args.steps // 2))]
+        finally:
+            dist.dist_set_plan_search(trials)
+        g_cw = sum(r["codewords"] for r, _ in gr)
+        g_ks = sum(r["gpu_seconds"] for r, _ in gr)
+        g_rate = g_cw / g_ks if g_ks > 0 else 0.0
+        greedy = {"plan": "identity qubit order, greedy information sets (search trials 0)",
+                  "d": gr[0][0]["d"], "d_agrees": all(r["d"] == ds[0] for r, _ in gr),
+                  "rounds": gr[0][0]["rounds"], "codewords_per_step": g_cw / len(gr),
+                  "value": g_cw / sum(s for _, s in gr), "unit": METRIC,
+                  "time_to_d_ms": 1e3 * statistics.mean(s for _, s in gr),
+                  "kernel_ms_per_step": 1e3 * g_ks / len(gr),
+                  "kernel_Gcodewords_per_s": g_rate / 1e9,
+                  "frac": g_rate / peak.mix_per_s if peak.mix_per_s else None}
     code.close()
 
     kernel_s = sum(kern_s)
@@ -504,6 +529,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(ctypes.sizeof(dist.DistResult)),
                     "ms_per_step": 1e3 * statistics.mean(e2e_s)},
             "gpu_launches": int(sum(launches))}
+    if greedy:
+        line["greedy_plan"] = greedy
     if iso_cmp:
         line["isometry"] = iso_cmp
     if args.batch_codes > 0:
@@ -549,6 +576,8 @@ def main():
                     help="default run: requests per second of that stream")
     ap.add_argument("--isometry", type=int, default=1,
                     help="also time the isometry method on the same code (0 = skip)")
+    ap.add_argument("--greedy-plan", type=int, default=1,
+                    help="also time the same code planned without the information-set search (0 = skip)")
     ap.add_argument("--batch-codes", type=int, default=4096,
                     help="size of the batched-vs-one-per-launch comparison (0 = skip)")
     args = ap.parse_args()

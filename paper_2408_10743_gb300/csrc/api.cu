@@ -16,6 +16,7 @@ namespace dist {
 cudaError_t enum_launch(const EnumParams& P, int grid, cudaStream_t st);
 size_t enum_smem_bytes(const EnumParams& P);
 int enum_blocks_per_sm(size_t smem);
+size_t enum_max_dynamic_smem(size_t optin);
 cudaError_t enum_set_max_smem(size_t bytes);
 int batch_blocks_per_sm();
 struct IntpeakRaw {
@@ -66,8 +67,8 @@ int device_ctx(DeviceCtx** out) {
         int optin = 0;
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
             return DIST_ECUDA;
-        d.smem_optin = (size_t)optin;
-        if (enum_set_max_smem(d.smem_optin) != cudaSuccess) return DIST_ECUDA;
+        d.smem_optin = enum_max_dynamic_smem((size_t)optin);
+        if (d.smem_optin == 0 || enum_set_max_smem(d.smem_optin) != cudaSuccess) return DIST_ECUDA;
         d.blocks_per_sm = enum_blocks_per_sm(16 * 1024);
         d.batch_blocks_per_sm = batch_blocks_per_sm();
         if (d.blocks_per_sm < 1 || d.batch_blocks_per_sm < 1) return DIST_ECUDA;

@@ -28,7 +28,7 @@ struct DeviceCtx {
     int sms = 0;
     int blocks_per_sm = 0;          // single-code kernel at a small shared-memory footprint
     int batch_blocks_per_sm = 0;    // multi-code kernel
-    size_t smem_optin = 0;          // largest dynamic shared memory per block
+    size_t smem_optin = 0;          // largest dynamic shared memory per enumeration block
     unsigned long long* d_binom = nullptr;
     std::mutex pool_mu;
     std::vector<SolveKit*> kits;                     // idle kits

@@ -53,6 +53,30 @@ extern __shared__ __align__(16) uint32_t g_enum_smem[];
 __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel(const __grid_constant__ EnumParams P) {
     uint32_t* sm = g_enum_smem;
     // stage: representatives and word-0 tables of every matrix in the launch
+    // Per-matrix lane context, read by reference from shared memory so that
+    // none of it stays in registers across the inner loop.
+    __shared__ LaneCtx s_ctx[DIST_MAXGAMMA];
+    unsigned long long* sbin = reinterpret_cast<unsigned long long*>(sm + P.s_binom);
+    if (threadIdx.x < (unsigned)P.ng) {
+        const GammaDesc& g = P.g[threadIdx.x];
+        LaneCtx& C = s_ctx[threadIdx.x];
+        C.reps = sm + g.s_rep;
+        C.r0 = reinterpret_cast<const U2*>(sm + g.s_r0);
+        C.r1 = reinterpret_cast<const U2*>(sm + g.s_r1);
+        C.flags = sm + g.s_flag;
+        C.t1 = g.t1;
+        C.coefs = P.tables + g.coef_off;
+        C.binom = sbin;
+        C.bstride = P.bcols;
+        C.outside = P.outside;
+        C.a = g.a;
+        C.b = g.b;
+        C.W = P.W;
+        C.CW = P.CW;
+        C.gamma = g.gamma;
+        C.proj = P.proj;
+        C.exclude = P.exclude;
+    }
     for (int gi = 0; gi < P.ng; gi++) {
         const GammaDesc& g = P.g[gi];
         const uint32_t* src = P.tables + g.rep_off;
@@ -68,7 +92,6 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         }
         for (int t = threadIdx.x; t < g.a + g.b; t += blockDim.x) sm[g.s_flag + t] = P.tables[g.flag_off + t];
     }
-    unsigned long long* sbin = reinterpret_cast<unsigned long long*>(sm + P.s_binom);
     for (int t = threadIdx.x; t < P.brows * P.bcols; t += blockDim.x) {
         const int n = t / P.bcols, k = t - n * P.bcols;
         sbin[t] = P.binom[n * (DIST_MAXR + 1) + k];
@@ -105,33 +128,14 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
             if (ssegs[mid].chunk_base <= chunk) lo_s = mid;
             else hi_s = mid;
         }
-        const SegDesc sg = ssegs[lo_s];
+        const SegDesc& sg = ssegs[lo_s];
         int skip = 0;
         if (lane == 0 && (int)u_now <= sg.L_before) {
             skip = 1;
             atomicMax(&P.scr->next_chunk, P.nchunks);
         }
         if (__shfl_sync(0xffffffffu, skip, 0)) break;
-        const GammaDesc& g = P.g[sg.g];
-        LaneCtx C;
-        C.reps = sm + g.s_rep;
-        C.r0 = reinterpret_cast<const U2*>(sm + g.s_r0);
-        C.r1 = reinterpret_cast<const U2*>(sm + g.s_r1);
-        C.flags = sm + g.s_flag;
-        C.t1 = g.t1;
-        C.coefs = P.tables + g.coef_off;
-        C.binom = sbin;
-        C.bstride = P.bcols;
-        C.outside = P.outside;
-        C.a = g.a;
-        C.b = g.b;
-        C.W = P.W;
-        C.CW = P.CW;
-        C.r = sg.r;
-        C.gamma = g.gamma;
-        C.proj = P.proj;
-        C.exclude = P.exclude;
-        C.L_before = sg.L_before;
+        const LaneCtx& C = s_ctx[sg.g];
         unsigned long long lo, hi, done = 0;
         if (seg_lane_range(sg, chunk, lane, lo, hi)) done = walk_range(C, sink, thr, sg, lo, hi);
 #pragma unroll
@@ -248,11 +252,9 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_batch_
         C.b = g.b;
         C.W = bc.W;
         C.CW = bc.CW;
-        C.r = sg.r;
         C.gamma = g.gamma;
         C.proj = bc.proj;
         C.exclude = bc.exclude;
-        C.L_before = sg.L_before;
         DevSink sink{bc.scr};
         unsigned long long lo, hi, done = 0;
         if (seg_lane_range(sg, chunk, lane, lo, hi)) done = walk_range(C, sink, thr, sg, lo, hi);
@@ -331,6 +333,14 @@ int enum_blocks_per_sm(size_t smem) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, enum_kernel, DIST_ENUM_THREADS, smem) != cudaSuccess)
         return 0;
     return nb;
+}
+
+// Largest dynamic shared memory a launch may ask for: the per-block opt-in
+// limit less the kernel's static shared memory (the lane contexts).
+size_t enum_max_dynamic_smem(size_t optin) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, enum_kernel) != cudaSuccess || a.sharedSizeBytes >= optin) return 0;
+    return optin - a.sharedSizeBytes;
 }
 
 cudaError_t enum_set_max_smem(size_t bytes) {

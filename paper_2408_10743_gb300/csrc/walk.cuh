@@ -137,8 +137,7 @@ struct LaneCtx {
     const unsigned long long* binom;   // [rows][bstride]
     const uint32_t* outside;
     int bstride;
-    int a, b, W, CW, r, gamma, proj, exclude;
-    int L_before;
+    int a, b, W, CW, gamma, proj, exclude;
     int t1;                            // two-word filter when thr - P exceeds this
 };
 
@@ -203,22 +202,71 @@ DIST_HD_COLD void consider(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, c
     sink.record(wt, C.gamma, i + nb, units, digits);
 }
 
-// Every representative choice of one subset, each weighed exactly (small i).
+// Every representative choice of one subset, each weighed on all W words
+// (small i, where the fast path's table does not apply).  The sum starts with
+// every unit at representative 0 and then follows a modular ternary Gray
+// code over the free digits: the digit that changes is the first one of a
+// ternary counter that does not wrap, and changing digit p from e to e+1
+// XORs the unit's representative (e+2) mod 3.  The sum stays in registers;
+// consider() re-weighs and records only a combination lighter than thr.
+template <int W, class Sink>
+DIST_HD void eval_generic_w(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
+                            int nb, const uint8_t* sB) {
+    uint32_t x[W], z[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) x[w] = z[w] = 0;
+    for (int p = 0; p < i; p++) {
+        const uint32_t* r = C.reps + (sA[p] * 3) * 2 * W;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            x[w] ^= r[w];
+            z[w] ^= r[W + w];
+        }
+    }
+    for (int q = 0; q < nb; q++) {
+        const uint32_t* r = C.reps + ((C.a + sB[q]) * 3) * 2 * W;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            x[w] ^= r[w];
+            z[w] ^= r[W + w];
+        }
+    }
+    uint8_t e[DIST_MAXR], cnt[DIST_MAXR];
+    for (int p = 0; p < i; p++) e[p] = cnt[p] = 0;
+    const int first = C.proj ? 1 : 0;
+    const int nd = i - first;
+    for (;;) {
+        uint32_t wt = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) wt += (uint32_t)popc32(x[w] | z[w]);
+        if (wt < thr) consider(C, sink, thr, i, sA, e, nb, sB);
+        int q = 0;
+        while (q < nd && cnt[q] == 2) {
+            cnt[q] = 0;
+            ++q;
+        }
+        if (q >= nd) break;
+        ++cnt[q];
+        const int p = first + q;
+        const int ee = e[p];
+        const uint32_t* r = C.reps + (sA[p] * 3 + (ee == 0 ? 2 : ee - 1)) * 2 * W;
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            x[w] ^= r[w];
+            z[w] ^= r[W + w];
+        }
+        e[p] = (uint8_t)(ee == 2 ? 0 : ee + 1);
+    }
+}
+
 template <class Sink>
 DIST_HD_COLD void eval_generic(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
                                int nb, const uint8_t* sB) {
-    uint8_t e[DIST_MAXR];
-    for (int p = 0; p < i; p++) e[p] = 0;
-    const int first = C.proj ? 1 : 0;
-    for (;;) {
-        consider(C, sink, thr, i, sA, e, nb, sB);
-        int p = first;
-        while (p < i && e[p] == 2) {
-            e[p] = 0;
-            ++p;
-        }
-        if (p >= i) break;
-        ++e[p];
+    switch (C.W) {
+        case 1: eval_generic_w<1>(C, sink, thr, i, sA, nb, sB); break;
+        case 2: eval_generic_w<2>(C, sink, thr, i, sA, nb, sB); break;
+        case 3: eval_generic_w<3>(C, sink, thr, i, sA, nb, sB); break;
+        default: eval_generic_w<4>(C, sink, thr, i, sA, nb, sB); break;
     }
 }
 
@@ -437,7 +485,7 @@ DIST_HD bool seg_lane_range(const SegDesc& sg, unsigned long long chunk, int lan
 template <class Sink>
 DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& thr, const SegDesc& sg,
                                       unsigned long long lo, unsigned long long hi) {
-    const int i = (int)sg.i, nb = C.r - i;
+    const int i = (int)sg.i, nb = (int)sg.r - i;
     uint8_t sA[DIST_MAXR], sB[DIST_MAXR], dig[DIST_MAXR];
     for (int p = 0; p < DIST_MAXR; p++) dig[p] = 0;
     unsigned long long tB = lo / sg.NA, tA = lo - tB * sg.NA;
@@ -454,7 +502,7 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
         const uint32_t u = u_next;
         u_next = sink.peek();
         thr = u < thr ? u : thr;
-        if ((int)u <= C.L_before) break;
+        if ((int)u <= sg.L_before) break;
         if (fast) {
             // packages with a pivot outside the filtered words each add one
             uint32_t P1 = PB1, P2 = PB2;

@@ -102,9 +102,8 @@ struct HostExec {
             C.binom = sbin;
             C.bstride = lp.bcols;
             C.outside = ep.outside;
-            C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW; C.r = sg.r;
+            C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW;
             C.gamma = g.gamma; C.proj = ep.proj; C.exclude = ep.exclude;
-            C.L_before = sg.L_before;
             for (int lane = 0; lane < 32; lane++) {
                 unsigned long long lo, hi;
                 if (!seg_lane_range(sg, chunk, lane, lo, hi)) continue;
@@ -219,10 +218,9 @@ extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int 
                 C.binom = sbin;
                 C.bstride = lp.bcols;
                 C.outside = ep.outside;
-                C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW; C.r = sg.r;
+                C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW;
                 C.gamma = g.gamma; C.proj = ep.proj; C.exclude = ep.exclude;
-                C.L_before = sg.L_before;
-                for (int lane = 0; lane < 32; lane++) {
+                    for (int lane = 0; lane < 32; lane++) {
                     unsigned long long lo, hi;
                     if (!seg_lane_range(sg, chunk, lane, lo, hi)) continue;
                     uint32_t thr = DIST_WINF;

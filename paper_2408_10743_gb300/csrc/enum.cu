@@ -109,48 +109,50 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
     const int lane = threadIdx.x & 31;
     const unsigned long long t_start = P.budget_ns ? global_ns() : 0ull;
     uint32_t thr = DIST_WINF;
-    // Lane 0 claims the warp's next chunk while the current one runs, so the
-    // atomic's round trip overlaps the work.  A claimed chunk is given up
-    // only where everything after it is unneeded (skip) or the budget ended.
+    // Lane 0 claims the warp's next chunk, and reads U, while the current
+    // chunk runs, so neither round trip stalls the warp between chunks.  The
+    // skip test of a chunk therefore sees U as it was one chunk earlier; a
+    // stale (larger) U only skips less, and the walk reads U afresh before
+    // its first subset.  A claimed chunk is given up only where everything
+    // after it is unneeded (skip) or the budget ended.
     unsigned long long claimed = 0;
-    if (lane == 0) claimed = atomicAdd(&P.scr->next_chunk, 1ull);
+    uint32_t u_claim = DIST_WINF;
+    if (lane == 0) {
+        claimed = atomicAdd(&P.scr->next_chunk, 1ull);
+        u_claim = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
+    }
+    int seg = 0;                  // chunks are claimed in increasing order
+    unsigned long long done = 0;  // this lane's codewords over all its chunks
     for (;;) {
         const unsigned long long chunk = __shfl_sync(0xffffffffu, claimed, 0);
         if (chunk >= P.nchunks) break;
-        uint32_t u_now = 0;
+        const uint32_t u_now = __shfl_sync(0xffffffffu, u_claim, 0);
         if (lane == 0) {
             claimed = atomicAdd(&P.scr->next_chunk, 1ull);
-            u_now = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
+            u_claim = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
         }
-        int lo_s = 0, hi_s = P.nseg;  // last segment with chunk_base <= chunk
-        while (hi_s - lo_s > 1) {
-            const int mid = (lo_s + hi_s) >> 1;
-            if (ssegs[mid].chunk_base <= chunk) lo_s = mid;
-            else hi_s = mid;
+        while (seg + 1 < P.nseg && ssegs[seg + 1].chunk_base <= chunk) ++seg;
+        const SegDesc& sg = ssegs[seg];
+        if ((int)u_now <= sg.L_before) {
+            if (lane == 0) atomicMax(&P.scr->next_chunk, P.nchunks);
+            break;
         }
-        const SegDesc& sg = ssegs[lo_s];
-        int skip = 0;
-        if (lane == 0 && (int)u_now <= sg.L_before) {
-            skip = 1;
-            atomicMax(&P.scr->next_chunk, P.nchunks);
-        }
-        if (__shfl_sync(0xffffffffu, skip, 0)) break;
         const LaneCtx& C = s_ctx[sg.g];
-        unsigned long long lo, hi, done = 0;
-        if (seg_lane_range(sg, chunk, lane, lo, hi)) done = walk_range(C, sink, thr, sg, lo, hi);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
-        int stop = 0;
-        if (lane == 0) {
-            if (done) atomicAdd(&P.scr->codewords, done);
-            if (P.budget_ns && global_ns() - t_start > P.budget_ns) {
+        unsigned long long lo, hi;
+        if (seg_lane_range(sg, chunk, lane, lo, hi)) done += walk_range(C, sink, thr, sg, lo, hi);
+        if (P.budget_ns) {
+            int stop = 0;
+            if (lane == 0 && global_ns() - t_start > P.budget_ns) {
                 atomicOr(&P.scr->status, 2u);
                 atomicMax(&P.scr->next_chunk, P.nchunks);
                 stop = 1;
             }
+            if (__shfl_sync(0xffffffffu, stop, 0)) break;
         }
-        if (__shfl_sync(0xffffffffu, stop, 0)) break;
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
+    if (lane == 0 && done) atomicAdd(&P.scr->codewords, done);
 }
 
 // ---------------------------------------------------------------------------

@@ -812,6 +812,10 @@ static void chunk_launch(LaunchPlan* lp, int target_warps) {
     // lower U come from, and they must still spread over the whole GPU.
     // Generic-path segments cost tens of times more per codeword and keep
     // the plain split, so that they never become the critical path.
+    // Outside the launch's last step a fast-path lane chunk holds at least
+    // eight subsets: a chunk costs about as much to start (claim, segment
+    // search, unranking) as a few subsets of 81 to 243 codewords cost to
+    // walk, and later steps keep every warp busy meanwhile.
     //
     // A large segment ends in smaller chunks: the work of one wave of
     // full-size chunks (one per resident warp) is cut into quarter-size ones,
@@ -839,6 +843,8 @@ static void chunk_launch(LaunchPlan* lp, int target_warps) {
             per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2) / kGenericCost);
         }
         double spl_d = per_lane / (double)sd.codes;
+        if (DIST_FAST_PATH((int)sd.i, lp->proj) && (int)t < lp->raw_step_seg0.back() && spl_d < 8.0)
+            spl_d = 8.0;
         unsigned long long spl = spl_d < 1.0 ? 1ull : (unsigned long long)spl_d;
         if (spl > (1ull << 30)) spl = 1ull << 30;
         const unsigned long long R = sd.rank1 - sd.rank0;

@@ -220,7 +220,7 @@ extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int 
                 C.outside = ep.outside;
                 C.a = g.a; C.b = g.b; C.W = ep.W; C.CW = ep.CW;
                 C.gamma = g.gamma; C.proj = ep.proj; C.exclude = ep.exclude;
-                    for (int lane = 0; lane < 32; lane++) {
+                for (int lane = 0; lane < 32; lane++) {
                     unsigned long long lo, hi;
                     if (!seg_lane_range(sg, chunk, lane, lo, hi)) continue;
                     uint32_t thr = DIST_WINF;

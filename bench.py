@@ -111,7 +111,7 @@ class ClockSampler:
 def source_digest():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2408_10743_gb300", "csrc")
-    for name in ("walk.cuh", "enum.cu", "dist_types.h"):
+    for name in ("walk.cuh", "enum.cu", "dist_types.h", "plan.cpp"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

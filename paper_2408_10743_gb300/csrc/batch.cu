@@ -36,9 +36,10 @@
 #include "solve.h"
 
 namespace dist {
-cudaError_t batch_launch(const BatchParams& P, int grid, cudaStream_t st);
-cudaError_t batch_init_launch(const BatchInit* items, int n, cudaStream_t st);
-cudaError_t batch_gather_launch(Scratch* const* scrs, BatchOut* out, int n, cudaStream_t st);
+cudaError_t slice_graph_build(unsigned char* d_arena, unsigned char* h_arena, const unsigned long long* binom,
+                              int grid, int aux_grid, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st,
+                              cudaGraph_t* graph, cudaGraphExec_t* exec, cudaGraphNode_t* h2d,
+                              cudaGraphNode_t* d2h);
 }  // namespace dist
 
 using namespace dist;
@@ -128,16 +129,18 @@ struct dist_batch {
     double gpu_seconds = 0;
     double plan_seconds = 0, post_seconds = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    // device arrays of one slice
-    DevBuf<BatchCode> codes;
-    DevBuf<SegDesc> segs;
-    DevBuf<GammaDesc> gammas;
-    DevBuf<int32_t> order;
-    DevBuf<int32_t> ring;
-    DevBuf<unsigned long long> sched;
-    DevBuf<BatchInit> inits;
-    DevBuf<Scratch*> scrs;
-    DevBuf<BatchOut> outs;
+    // One slice's arena (SliceHeader, then its arrays), pinned on the host
+    // and on the device, and the slice graph captured for this allocation.
+    DevBuf<unsigned char> arena;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphNode_t n_h2d = nullptr, n_d2h = nullptr;
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+    }
 
     void run();
     int slice();
@@ -230,57 +233,19 @@ int dist_batch::slice() {
         if (!it->done) run.push_back(it);
     if (run.empty()) return DIST_OK;
     const int n = (int)run.size();
-    // scratch set-up of new and re-planned codes
-    int ninit = 0;
-    if (!inits.ensure(n)) return DIST_ENOMEM;
-    for (Item* it : run) {
-        if (!it->init_mode) continue;
-        BatchInit& bi = inits.h[ninit++];
-        memset(&bi, 0, sizeof bi);
-        bi.scr = it->c->d_scr;
-        bi.mode = (uint32_t)it->init_mode;
-        const Plan& p = it->c->plan;
-        const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
-        bi.U0 = (uint32_t)std::min<int>(u0, DIST_WINF);
-        bi.slot = p.n_stab > 0 ? p.u0_excl_slot : p.u0_slot;
-        it->init_mode = 0;
-    }
-    if (!inits.upload(ninit, st) || batch_init_launch(inits.d, ninit, st) != cudaSuccess) return DIST_ECUDA;
-    // pack the launch
+    // the slice's arrays, packed one after another into the arena behind
+    // its header (offsets 256-byte aligned)
     size_t nseg = 0, ngam = 0;
+    int ninit = 0;
     for (Item* it : run) {
         nseg += it->lp.segs.size();
         ngam += it->lp.g.size();
+        if (it->init_mode) ninit++;
     }
-    if (!codes.ensure(n) || !segs.ensure(nseg + 1) || !gammas.ensure(ngam + 1) || !scrs.ensure(n) ||
-        !outs.ensure(n) || !sched.ensure(2))
-        return DIST_ENOMEM;
     std::vector<double> work(n);
     double total = 0;
-    size_t so = 0, go = 0;
     for (int i = 0; i < n; i++) {
-        Item* it = run[i];
-        const Plan& p = it->c->plan;
-        BatchCode& bc = codes.h[i];
-        memset(&bc, 0, sizeof bc);
-        bc.tables = it->c->d_tables;
-        bc.scr = it->c->d_scr;
-        for (int w = 0; w < DIST_MAXCW; w++) bc.outside[w] = p.outside[w];
-        bc.W = p.W;
-        bc.CW = p.CW;
-        bc.proj = p.field == 4 ? 1 : 0;
-        bc.exclude = p.n_stab > 0 ? 1 : 0;
-        bc.seg0 = (uint32_t)so;
-        bc.nseg = (uint32_t)it->lp.segs.size();
-        bc.g0 = (uint32_t)go;
-        bc.ng = (uint32_t)it->lp.g.size();
-        bc.nchunks = it->lp.nchunks;
-        memcpy(segs.h + so, it->lp.segs.data(), it->lp.segs.size() * sizeof(SegDesc));
-        memcpy(gammas.h + go, it->lp.g.data(), it->lp.g.size() * sizeof(GammaDesc));
-        so += it->lp.segs.size();
-        go += it->lp.g.size();
-        scrs.h[i] = it->c->d_scr;
-        work[i] = estimated_work(it);
+        work[i] = estimated_work(run[i]);
         total += work[i];
     }
     // Order list (phase 1, one chunk per entry), shortest job first so that
@@ -305,37 +270,94 @@ int dist_batch::slice() {
     for (auto it = idx.rbegin(); it != idx.rend(); ++it)
         if (run[*it]->lp.nchunks > kSmallChunks) rng.push_back(*it);
     if (rng.empty()) rng.push_back(idx.back());
-    if (!order.ensure(ord.size()) || !ring.ensure(rng.size())) return DIST_ENOMEM;
-    memcpy(order.h, ord.data(), ord.size() * sizeof(int32_t));
-    memcpy(ring.h, rng.data(), rng.size() * sizeof(int32_t));
-    sched.h[0] = sched.h[1] = 0;
-    if (!codes.upload(n, st) || !segs.upload(nseg, st) || !gammas.upload(ngam, st) ||
-        !order.upload(ord.size(), st) || !ring.upload(rng.size(), st) || !sched.upload(2, st) ||
-        !scrs.upload(n, st))
-        return DIST_ECUDA;
-    BatchParams P;
-    memset(&P, 0, sizeof P);
-    P.codes = codes.d;
-    P.segs = segs.d;
-    P.gammas = gammas.d;
-    P.order = order.d;
-    P.ring = ring.d;
-    P.nring = (int)rng.size();
-    P.sched = sched.d;
-    P.binom = dev->d_binom;
-    P.ncodes = n;
-    P.norder = (int)ord.size();
-    P.budget_ns = opts.slice_ms > 0 ? (unsigned long long)(opts.slice_ms * 1e6) : 0ull;
+    SliceHeader hd;
+    memset(&hd, 0, sizeof hd);
+    size_t off = align256(sizeof(SliceHeader));
+    auto place = [&](unsigned long long* o, size_t bytes) {
+        *o = off;
+        off = align256(off + bytes);
+    };
+    place(&hd.off_inits, (size_t)ninit * sizeof(BatchInit));
+    place(&hd.off_codes, (size_t)n * sizeof(BatchCode));
+    place(&hd.off_segs, nseg * sizeof(SegDesc));
+    place(&hd.off_gammas, ngam * sizeof(GammaDesc));
+    place(&hd.off_order, ord.size() * sizeof(int32_t));
+    place(&hd.off_ring, rng.size() * sizeof(int32_t));
+    place(&hd.off_sched, 2 * sizeof(unsigned long long));
+    place(&hd.off_scrs, (size_t)n * sizeof(Scratch*));
+    const size_t up_bytes = off;
+    place(&hd.off_outs, (size_t)n * sizeof(BatchOut));
+    if (off > arena.cap) {  // a new allocation: the graph is captured again
+        drop_graph();
+        if (!arena.ensure(off)) return DIST_ENOMEM;
+    }
+    unsigned char* const h = arena.h;
+    hd.ncodes = n;
+    hd.ninit = ninit;
+    hd.norder = (int32_t)ord.size();
+    hd.nring = (int32_t)rng.size();
+    hd.budget_ns = opts.slice_ms > 0 ? (unsigned long long)(opts.slice_ms * 1e6) : 0ull;
+    memcpy(h, &hd, sizeof hd);
+    // scratch set-up of new and re-planned codes
+    BatchInit* inits = reinterpret_cast<BatchInit*>(h + hd.off_inits);
+    int k_init = 0;
+    for (Item* it : run) {
+        if (!it->init_mode) continue;
+        BatchInit& bi = inits[k_init++];
+        memset(&bi, 0, sizeof bi);
+        bi.scr = it->c->d_scr;
+        bi.mode = (uint32_t)it->init_mode;
+        const Plan& p = it->c->plan;
+        const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
+        bi.U0 = (uint32_t)std::min<int>(u0, DIST_WINF);
+        bi.slot = p.n_stab > 0 ? p.u0_excl_slot : p.u0_slot;
+        it->init_mode = 0;
+    }
+    BatchCode* codes = reinterpret_cast<BatchCode*>(h + hd.off_codes);
+    SegDesc* segs = reinterpret_cast<SegDesc*>(h + hd.off_segs);
+    GammaDesc* gammas = reinterpret_cast<GammaDesc*>(h + hd.off_gammas);
+    Scratch** scrs = reinterpret_cast<Scratch**>(h + hd.off_scrs);
+    size_t so = 0, go = 0;
+    for (int i = 0; i < n; i++) {
+        Item* it = run[i];
+        const Plan& p = it->c->plan;
+        BatchCode& bc = codes[i];
+        memset(&bc, 0, sizeof bc);
+        bc.tables = it->c->d_tables;
+        bc.scr = it->c->d_scr;
+        for (int w = 0; w < DIST_MAXCW; w++) bc.outside[w] = p.outside[w];
+        bc.W = p.W;
+        bc.CW = p.CW;
+        bc.proj = p.field == 4 ? 1 : 0;
+        bc.exclude = p.n_stab > 0 ? 1 : 0;
+        bc.seg0 = (uint32_t)so;
+        bc.nseg = (uint32_t)it->lp.segs.size();
+        bc.g0 = (uint32_t)go;
+        bc.ng = (uint32_t)it->lp.g.size();
+        bc.nchunks = it->lp.nchunks;
+        memcpy(segs + so, it->lp.segs.data(), it->lp.segs.size() * sizeof(SegDesc));
+        memcpy(gammas + go, it->lp.g.data(), it->lp.g.size() * sizeof(GammaDesc));
+        so += it->lp.segs.size();
+        go += it->lp.g.size();
+        scrs[i] = it->c->d_scr;
+    }
+    memcpy(h + hd.off_order, ord.data(), ord.size() * sizeof(int32_t));
+    memcpy(h + hd.off_ring, rng.data(), rng.size() * sizeof(int32_t));
+    memset(h + hd.off_sched, 0, 2 * sizeof(unsigned long long));
     const int grid = dev->sms * dev->batch_blocks_per_sm;
+    if (!gexec && slice_graph_build(arena.d, arena.h, dev->d_binom, grid, 2 * dev->sms, e0, e1, st, &graph,
+                                    &gexec, &n_h2d, &n_d2h) != cudaSuccess)
+        return DIST_ECUDA;
     const double t_launch = wall_now();
     plan_seconds += t_launch - t_plan;
-    cudaEventRecord(e0, st);
-    if (batch_launch(P, grid, st) != cudaSuccess) return DIST_ECUDA;
-    cudaEventRecord(e1, st);
-    if (batch_gather_launch(scrs.d, outs.d, n, st) != cudaSuccess) return DIST_ECUDA;
-    if (cudaMemcpyAsync(outs.h, outs.d, n * sizeof(BatchOut), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
+    // one upload, the slice graph, one read-back
+    if (cudaGraphExecMemcpyNodeSetParams1D(gexec, n_h2d, arena.d, arena.h, up_bytes, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaGraphExecMemcpyNodeSetParams1D(gexec, n_d2h, arena.h + hd.off_outs, arena.d + hd.off_outs,
+                                           (size_t)n * sizeof(BatchOut), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaGraphLaunch(gexec, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
         return DIST_ECUDA;
+    const BatchOut* outs = reinterpret_cast<const BatchOut*>(arena.h + hd.off_outs);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     gpu_seconds += ms * 1e-3;
@@ -345,7 +367,7 @@ int dist_batch::slice() {
     for (int i = 0; i < n; i++) {
         Item* it = run[i];
         it->slices++;
-        const BatchOut& o = outs.h[i];
+        const BatchOut& o = outs[i];
         const LaunchPlan& lp = it->lp;
         const Plan& p = it->c->plan;
         const uint32_t U = o.U;
@@ -580,15 +602,8 @@ int dist_batch_destroy(dist_batch* b) {
             it->c->in_batch = 0;
             delete it;
         }
-    b->codes.release();
-    b->segs.release();
-    b->gammas.release();
-    b->order.release();
-    b->ring.release();
-    b->sched.release();
-    b->inits.release();
-    b->scrs.release();
-    b->outs.release();
+    b->drop_graph();
+    b->arena.release();
     if (b->e0) cudaEventDestroy(b->e0);
     if (b->e1) cudaEventDestroy(b->e1);
     if (b->st) cudaStreamDestroy(b->st);

@@ -137,6 +137,17 @@ struct BatchParams {
     unsigned long long budget_ns;       // stop after this long (per block); 0 = none
 };
 
+// What one slice of the batch engine sends to the device, at byte 0 of its
+// arena: the counts, the slice's time budget and the byte offsets (from the
+// arena's start) of its arrays.  The kernels of a slice take only the arena,
+// so that the slice's launch sequence is one graph with fixed arguments.
+struct SliceHeader {
+    int32_t ncodes, norder, nring, ninit;
+    unsigned long long budget_ns;       // stop after this long (per block); 0 = none
+    unsigned long long off_inits, off_codes, off_segs, off_gammas, off_order, off_ring, off_sched, off_scrs,
+        off_outs;
+};
+
 // Per-code scratch set-up before a multi-code launch.
 struct BatchInit {
     Scratch* scr;

@@ -16,6 +16,8 @@
 // budget is spent.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "walk.cuh"
 
 namespace dist {
@@ -184,7 +186,30 @@ __device__ int join_code(const BatchParams& P) {
     return -1;
 }
 
-__global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_batch_kernel(const __grid_constant__ BatchParams P) {
+// The launch's parameters, rebuilt from the slice header at the start of the
+// arena (one thread per block; read from shared memory afterwards).
+__device__ __forceinline__ void slice_params(const unsigned char* arena, const unsigned long long* binom,
+                                             BatchParams* P) {
+    const SliceHeader* H = reinterpret_cast<const SliceHeader*>(arena);
+    P->codes = reinterpret_cast<const BatchCode*>(arena + H->off_codes);
+    P->segs = reinterpret_cast<const SegDesc*>(arena + H->off_segs);
+    P->gammas = reinterpret_cast<const GammaDesc*>(arena + H->off_gammas);
+    P->order = reinterpret_cast<const int32_t*>(arena + H->off_order);
+    P->ring = reinterpret_cast<const int32_t*>(arena + H->off_ring);
+    P->sched = reinterpret_cast<unsigned long long*>(const_cast<unsigned char*>(arena) + H->off_sched);
+    P->binom = binom;
+    P->ncodes = H->ncodes;
+    P->norder = H->norder;
+    P->nring = H->nring;
+    P->budget_ns = H->budget_ns;
+}
+
+__global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB)
+    enum_batch_kernel(const unsigned char* __restrict__ arena, const unsigned long long* binom) {
+    __shared__ BatchParams sP;
+    if (threadIdx.x == 0) slice_params(arena, binom, &sP);
+    __syncthreads();
+    const BatchParams& P = sP;
     const int lane = threadIdx.x & 31;
     const unsigned long long t_start = P.budget_ns ? global_ns() : 0ull;
     uint32_t thr = DIST_WINF;
@@ -272,54 +297,100 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_batch_
 }
 
 // Scratch set-up of many codes: block i serves item i.
-__global__ void batch_init_kernel(const BatchInit* items, int n) {
-    const int i = blockIdx.x;
-    if (i >= n) return;
-    const BatchInit it = items[i];
-    if (it.mode == 1) {
-        uint32_t* w = reinterpret_cast<uint32_t*>(it.scr);
-        for (int t = threadIdx.x; t < (int)(sizeof(Scratch) / 4); t += blockDim.x) w[t] = 0u;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            it.scr->U = it.U0;
-            if (it.U0 <= DIST_MAXN) it.scr->slot[it.U0] = it.slot;
+// Scratch set-up of the slice's new and re-planned codes (one block per code,
+// the grid strides over them).
+__global__ void batch_init_kernel(const unsigned char* __restrict__ arena) {
+    const SliceHeader* H = reinterpret_cast<const SliceHeader*>(arena);
+    const BatchInit* items = reinterpret_cast<const BatchInit*>(arena + H->off_inits);
+    const int n = H->ninit;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const BatchInit it = items[i];
+        if (it.mode == 1) {
+            uint32_t* w = reinterpret_cast<uint32_t*>(it.scr);
+            for (int t = threadIdx.x; t < (int)(sizeof(Scratch) / 4); t += blockDim.x) w[t] = 0u;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                it.scr->U = it.U0;
+                if (it.U0 <= DIST_MAXN) it.scr->slot[it.U0] = it.slot;
+            }
+            __syncthreads();
+        } else if (it.mode == 2 && threadIdx.x == 0) {
+            it.scr->next_chunk = 0ull;
         }
-    } else if (it.mode == 2 && threadIdx.x == 0) {
-        it.scr->next_chunk = 0ull;
     }
 }
 
 // Read-back of many codes: thread i gathers code i's bound, counters and the
 // witness slot of its bound.
-__global__ void batch_gather_kernel(Scratch* const* scrs, BatchOut* out, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const Scratch* s = scrs[i];
-    BatchOut o;
-    o.U = s->U;
-    o.status = s->status;
-    o.next_chunk = s->next_chunk;
-    o.codewords = s->codewords;
-    if (o.U <= DIST_MAXN) o.slot = s->slot[o.U];
-    else memset(&o.slot, 0, sizeof o.slot);
-    out[i] = o;
+// Every code's bound, counters and witness slot into the arena's results.
+__global__ void batch_gather_kernel(unsigned char* __restrict__ arena) {
+    const SliceHeader* H = reinterpret_cast<const SliceHeader*>(arena);
+    Scratch* const* scrs = reinterpret_cast<Scratch* const*>(arena + H->off_scrs);
+    BatchOut* out = reinterpret_cast<BatchOut*>(arena + H->off_outs);
+    const int n = H->ncodes;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Scratch* s = scrs[i];
+        BatchOut o;
+        o.U = s->U;
+        o.status = s->status;
+        o.next_chunk = s->next_chunk;
+        o.codewords = s->codewords;
+        if (o.U <= DIST_MAXN) o.slot = s->slot[o.U];
+        else memset(&o.slot, 0, sizeof o.slot);
+        out[i] = o;
+    }
 }
 
-cudaError_t batch_launch(const BatchParams& P, int grid, cudaStream_t st) {
-    enum_batch_kernel<<<grid, DIST_ENUM_THREADS, 0, st>>>(P);
-    return cudaGetLastError();
-}
-
-cudaError_t batch_init_launch(const BatchInit* items, int n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    batch_init_kernel<<<n, 128, 0, st>>>(items, n);
-    return cudaGetLastError();
-}
-
-cudaError_t batch_gather_launch(Scratch* const* scrs, BatchOut* out, int n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    batch_gather_kernel<<<(n + 127) / 128, 128, 0, st>>>(scrs, out, n);
-    return cudaGetLastError();
+// The graph of one batch slice: the arena upload, the scratch set-up, the
+// multi-code launch between the two timing events, the gather and the
+// read-back of the results.  It is captured once per arena allocation (the
+// kernels' arguments are the arena and the binomial table); before each
+// replay the two copies get the slice's sizes (*h2d, *d2h: their nodes).
+cudaError_t slice_graph_build(unsigned char* d_arena, unsigned char* h_arena, const unsigned long long* binom,
+                              int grid, int aux_grid, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st,
+                              cudaGraph_t* graph, cudaGraphExec_t* exec, cudaGraphNode_t* h2d,
+                              cudaGraphNode_t* d2h) {
+    *graph = nullptr;
+    *exec = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return err;
+    // placeholder sizes; every replay sets the real ones
+    cudaMemcpyAsync(d_arena, h_arena, sizeof(SliceHeader), cudaMemcpyHostToDevice, st);
+    batch_init_kernel<<<aux_grid, 128, 0, st>>>(d_arena);
+    cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);
+    enum_batch_kernel<<<grid, DIST_ENUM_THREADS, 0, st>>>(d_arena, binom);
+    cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
+    batch_gather_kernel<<<aux_grid, 128, 0, st>>>(d_arena);
+    cudaMemcpyAsync(h_arena, d_arena, sizeof(SliceHeader), cudaMemcpyDeviceToHost, st);
+    const cudaError_t launch_err = cudaGetLastError();
+    err = cudaStreamEndCapture(st, graph);
+    if (err == cudaSuccess) err = launch_err;
+    if (err != cudaSuccess) {
+        if (*graph) cudaGraphDestroy(*graph);
+        *graph = nullptr;
+        return err;
+    }
+    size_t nn = 0;
+    err = cudaGraphGetNodes(*graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (err == cudaSuccess) err = cudaGraphGetNodes(*graph, nodes.data(), &nn);
+    *h2d = *d2h = nullptr;
+    for (size_t k = 0; err == cudaSuccess && k < nn; k++) {
+        cudaGraphNodeType t;
+        if ((err = cudaGraphNodeGetType(nodes[k], &t)) != cudaSuccess || t != cudaGraphNodeTypeMemcpy) continue;
+        cudaMemcpy3DParms mp;
+        if ((err = cudaGraphMemcpyNodeGetParams(nodes[k], &mp)) != cudaSuccess) break;
+        if (mp.dstPtr.ptr == static_cast<void*>(d_arena)) *h2d = nodes[k];
+        else if (mp.dstPtr.ptr == static_cast<void*>(h_arena)) *d2h = nodes[k];
+    }
+    if (err == cudaSuccess && (!*h2d || !*d2h)) err = cudaErrorUnknown;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(exec, *graph, 0);
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(*graph);
+        *graph = nullptr;
+        *exec = nullptr;
+    }
+    return err;
 }
 
 int batch_blocks_per_sm() {

@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
     extern __shared__ __align__(16) uint32_t iso_smem[];
     const int K = P.K;
     uint4* sfil = reinterpret_cast<uint4*>(iso_smem);       // [K]: words 0-3
-    uint32_t* snp = reinterpret_cast<uint32_t*>(sfil + K);  // [K]: 1 for a pivot row
-    uint32_t* srow = snp + K;                               // [K][WORDS]
+    uint4* sdel = sfil + K;                                 // [K]: words 0-3 of rows c and c + 1, XORed
+    uint32_t* snp = reinterpret_cast<uint32_t*>(sdel + K);  // [K]: 1 for a pivot row
+    int32_t* sdnp = reinterpret_cast<int32_t*>(snp + K);    // [K]: snp[c + 1] - snp[c]
+    uint32_t* srow = reinterpret_cast<uint32_t*>(sdnp + K); // [K][WORDS]
     uint8_t* spiv = reinterpret_cast<uint8_t*>(srow + K * WORDS);
     for (int t = threadIdx.x; t < K * WORDS; t += blockDim.x) {
         const int row = t / WORDS, w = t - row * WORDS;
@@ -125,6 +127,14 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
     for (int t = threadIdx.x; t < K; t += blockDim.x)
         sfil[t] = make_uint4(srow[t * WORDS], WORDS > 1 ? srow[t * WORDS + 1] : 0u,
                              WORDS > 2 ? srow[t * WORDS + 2] : 0u, WORDS > 3 ? srow[t * WORDS + 3] : 0u);
+    __syncthreads();
+    // the common carry (c[1] moves up by one) XORs rows c and c + 1 out and
+    // in: one staged delta instead of two rows
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+        const uint4 a = sfil[t], b = t + 1 < K ? sfil[t + 1] : make_uint4(0u, 0u, 0u, 0u);
+        sdel[t] = make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
+        sdnp[t] = (t + 1 < K ? (int32_t)snp[t + 1] : 0) - (int32_t)snp[t];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int r = P.r;
@@ -181,12 +191,12 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
                 // c1 ran out: the top moves to its colex successor, usually
                 // c[1] alone (one row out, one in)
                 if (c2 + 1 < c3) {
-                    const uint4 qo = sfil[c2], qi = sfil[c2 + 1];
-                    b.x ^= qo.x ^ qi.x;
-                    b.y ^= qo.y ^ qi.y;
-                    b.z ^= qo.z ^ qi.z;
-                    b.w ^= qo.w ^ qi.w;
-                    npb = npb - snp[c2] + snp[c2 + 1];
+                    const uint4 dq = sdel[c2];
+                    b.x ^= dq.x;
+                    b.y ^= dq.y;
+                    b.z ^= dq.z;
+                    b.w ^= dq.w;
+                    npb = (uint32_t)((int32_t)npb + sdnp[c2]);
                     c2++;
                 } else {
                     c[0] = (uint8_t)(c2 - 1);
@@ -229,7 +239,7 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
 
 template <int WORDS>
 cudaError_t iso_launch_w(const IsoParams& P, int sms, cudaStream_t st) {
-    const size_t smem = (size_t)P.K * 20 + (size_t)P.K * WORDS * 4 + (size_t)P.K + 16;
+    const size_t smem = (size_t)P.K * 40 + (size_t)P.K * WORDS * 4 + (size_t)P.K + 16;
     int bps = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, iso_kernel<WORDS>, 256, smem) != cudaSuccess)
         return cudaErrorUnknown;

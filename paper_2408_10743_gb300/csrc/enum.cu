@@ -52,9 +52,21 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 extern __shared__ __align__(16) uint32_t g_enum_smem[];
 
+// Asynchronous global-to-shared copies (cp.async): a block issues every copy
+// of its prologue at once and waits once, so that on a cold L2 the staging
+// costs about one DRAM round trip instead of one per loop step.
+__device__ __forceinline__ void cp_async4(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel(const __grid_constant__ EnumParams P) {
     uint32_t* sm = g_enum_smem;
-    // stage: representatives and word-0 tables of every matrix in the launch
     // Per-matrix lane context, read by reference from shared memory so that
     // none of it stays in registers across the inner loop.
     __shared__ LaneCtx s_ctx[DIST_MAXGAMMA];
@@ -79,31 +91,40 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         C.proj = P.proj;
         C.exclude = P.exclude;
     }
+    // stage: representatives and flags of every matrix in the launch, the
+    // binomials and the segment table
     for (int gi = 0; gi < P.ng; gi++) {
         const GammaDesc& g = P.g[gi];
         const uint32_t* src = P.tables + g.rep_off;
         const int nw = (g.a + g.b) * 6 * P.W;
-        for (int t = threadIdx.x; t < nw; t += blockDim.x) sm[g.s_rep + t] = src[t];
-        U2* r0 = reinterpret_cast<U2*>(sm + g.s_r0);
-        U2* r1 = reinterpret_cast<U2*>(sm + g.s_r1);
-        for (int t = threadIdx.x; t < g.a * 3; t += blockDim.x) {
-            r0[t].x = src[(t * 2 + 0) * P.W];
-            r0[t].z = src[(t * 2 + 1) * P.W];
-            r1[t].x = P.W >= 2 ? src[(t * 2 + 0) * P.W + 1] : 0u;
-            r1[t].z = P.W >= 2 ? src[(t * 2 + 1) * P.W + 1] : 0u;
-        }
-        for (int t = threadIdx.x; t < g.a + g.b; t += blockDim.x) sm[g.s_flag + t] = P.tables[g.flag_off + t];
+        for (int t = threadIdx.x; t < nw; t += blockDim.x) cp_async4(&sm[g.s_rep + t], &src[t]);
+        for (int t = threadIdx.x; t < g.a + g.b; t += blockDim.x) cp_async4(&sm[g.s_flag + t], &P.tables[g.flag_off + t]);
     }
     for (int t = threadIdx.x; t < P.brows * P.bcols; t += blockDim.x) {
         const int n = t / P.bcols, k = t - n * P.bcols;
-        sbin[t] = P.binom[n * (DIST_MAXR + 1) + k];
+        cp_async8(&sbin[t], &P.binom[n * (DIST_MAXR + 1) + k]);
     }
     SegDesc* ssegs = reinterpret_cast<SegDesc*>(sm + P.s_segs);
     {
         const uint32_t* src = reinterpret_cast<const uint32_t*>(P.segs);
         uint32_t* dst = reinterpret_cast<uint32_t*>(ssegs);
         const int nw = P.nseg * (int)(sizeof(SegDesc) / 4);
-        for (int t = threadIdx.x; t < nw; t += blockDim.x) dst[t] = src[t];
+        for (int t = threadIdx.x; t < nw; t += blockDim.x) cp_async4(&dst[t], &src[t]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // word-0 and word-1 tables of the A-units, from the staged representatives
+    for (int gi = 0; gi < P.ng; gi++) {
+        const GammaDesc& g = P.g[gi];
+        const uint32_t* rep = sm + g.s_rep;
+        U2* r0 = reinterpret_cast<U2*>(sm + g.s_r0);
+        U2* r1 = reinterpret_cast<U2*>(sm + g.s_r1);
+        for (int t = threadIdx.x; t < g.a * 3; t += blockDim.x) {
+            r0[t].x = rep[(t * 2 + 0) * P.W];
+            r0[t].z = rep[(t * 2 + 1) * P.W];
+            r1[t].x = P.W >= 2 ? rep[(t * 2 + 0) * P.W + 1] : 0u;
+            r1[t].z = P.W >= 2 ? rep[(t * 2 + 1) * P.W + 1] : 0u;
+        }
     }
     __syncthreads();
 

@@ -246,6 +246,27 @@ def test_plan_chunks_cover_every_rank_once(hw, warps):
         assert split_seen
 
 
+def test_plan_chunk_sizes(hw):
+    """Chunk sizing rules on the QC n = 72 launch (2432 resident warps):
+    fast-path segments outside the last step give each lane at least eight
+    subsets (a chunk costs about as much to start as a few subsets cost to
+    walk), and the last step still spreads over every warp."""
+    warps = 2432
+    rows, nchunks = plan_segments(hw, synth.single_qc(0), warps)
+    last_step = max(r[0] for r in rows)
+    fast_before_last = 0
+    for step, i, NA, NB, r0, r1, cb, spl, codes in rows:
+        if i < 4:  # generic path (fewer than four varying units)
+            continue
+        subsets = r1 - r0
+        if step < last_step:
+            fast_before_last += 1
+            assert spl >= 8 or 32 * spl >= subsets, (step, i, spl)
+        else:
+            assert (subsets + 32 * spl - 1) // (32 * spl) >= min(warps, (subsets + 31) // 32) // 2, (step, i, spl)
+    assert fast_before_last > 0
+
+
 def test_colex_walk(hw):
     """The isometry kernel's order: unranking by the combinatorial number
     system and stepping (lowest element up, then colex_carry) visit the

@@ -281,13 +281,14 @@ static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<c
     auto with_proj = [&](int q, int val) {
         return val == 1 ? rs_andnot(cx[q], cz[q]) : val == 2 ? rs_andnot(cz[q], cx[q]) : rs_and(cx[q], cz[q]);
     };
-    // R[i] += R[g] (and the coefficients) for every row i in S; g not in S
+    // R[i] += R[g] (and the coefficients: plane 0 only, F2 coefficients)
+    // for every row i in S; g not in S
     auto add_row = [&](const RowSet& S, int g) {
         for (int t = 0; t < (int)(sizeof S.w / 8); t++)
             for (uint64_t m = S.w[t]; m; m &= m - 1) {
                 const int i = t * 64 + __builtin_ctzll(m);
                 vxor(R[i], R[g]);
-                cxor(C[i], C[g]);
+                for (int w = 0; w < DIST_MAXCW; w++) C[i].p[0][w] ^= C[g].p[0][w];
             }
         for (int w = 0; w < p.W; w++) {
             for (uint32_t m = R[g].x[w]; m; m &= m - 1) rs_xor_into(cx[w * 32 + __builtin_ctz(m)], S);

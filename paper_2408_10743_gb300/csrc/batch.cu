@@ -2,11 +2,13 @@
 //
 // A dist_batch owns one worker thread and one stream.  The worker runs
 // "slices": it admits pending codes (up to a count and a device-footprint
-// limit), plans the new ones, seeds their scratch, packs every active code's
-// segments into one multi-code launch (enum_batch_kernel), runs it with a
-// time budget, gathers every code's bound, counters and witness slot in one
-// read-back, and then, per code, either certifies d, lets it resume in the
-// next slice, or plans its next steps.  A code's chunk counter and bound stay
+// limit), plans the new ones, and packs the scratch set-ups and every active
+// code's segments into one arena.  One replay of the slice graph uploads the
+// arena, seeds the new codes' scratch, runs the multi-code launch
+// (enum_batch_kernel) with a time budget and gathers every code's bound,
+// counters and witness slot into one read-back; then, per code, the worker
+// either certifies d, lets it resume in the next slice, or plans its next
+// steps.  A code's chunk counter and bound stay
 // on the device between slices, so a slice boundary loses no work.  Codes
 // submitted while others are running join at the next slice: their work
 // overlaps on the device with the codes already admitted.
@@ -72,7 +74,7 @@ struct Ticket {
     int remaining = 0;
 };
 
-// Device array with a pinned host staging copy; grows on demand.
+// Device buffer with a pinned host mirror; grows on demand.
 template <class T>
 struct DevBuf {
     T* d = nullptr;
@@ -92,9 +94,6 @@ struct DevBuf {
         h = nh;
         cap = nc;
         return true;
-    }
-    bool upload(size_t n, cudaStream_t st) {
-        return n == 0 || cudaMemcpyAsync(d, h, n * sizeof(T), cudaMemcpyHostToDevice, st) == cudaSuccess;
     }
     void release() {
         if (d) cudaFree(d);

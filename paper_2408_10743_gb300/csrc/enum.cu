@@ -2,14 +2,15 @@
 //
 // One launch runs a run of consecutive enumeration steps (round r of one
 // generator matrix each), described by a segment table.  Every block stages
-// the representatives of the matrices involved, their word-0 tables, the
-// binomials the unranking needs and the segment table into shared memory
-// (tens of KB at most); after that the kernel reads nothing from HBM except
-// the running upper bound U.  Warps pull chunks of combination ranks from a
-// global counter (persistent grid); every lane walks its ranks with
-// walk_range(); warps sum their codeword counts with shuffles; a lane that
-// finds a lighter codeword publishes it with atomicMin on U and claims the
-// witness slot of that weight.  A chunk whose segment has L_before >= U is
+// the representatives of the matrices involved, their flags, the binomials
+// the unranking needs and the segment table into shared memory (tens of KB
+// at most, cp.async copies), and builds the word-0/1 tables from them; after
+// that the kernel reads nothing from HBM except the running upper bound U.
+// Warps pull chunks of combination ranks from a global counter (persistent
+// grid); every lane walks its ranks with walk_range(); a warp sums its
+// codeword count with shuffles once, when it exits; a lane that finds a
+// lighter codeword publishes it with atomicMin on U and claims the witness
+// slot of that weight.  A chunk whose segment has L_before >= U is
 // not needed, and neither is anything after it (L_before only grows), so the
 // warp that sees it pushes the counter to the end and the grid drains.
 // There is no spin-wait: the kernel ends when the chunks run out or its time

@@ -133,8 +133,10 @@ int dist_solve_isometry(dist_code *c, dist_result *out, void *cuda_stream);
  * A dist_batch runs many dist_codes on one device together: one launch of
  * the multi-code enumeration kernel serves every admitted code, each code
  * keeping its bound, chunk counter and witness slots on the device between
- * launches.  A worker thread owned by the batch runs time-bounded "slices";
- * codes submitted while others run are admitted at the next slice boundary
+ * launches.  A worker thread owned by the batch runs time-bounded "slices",
+ * each one replay of a captured CUDA graph (one upload of the slice's arena,
+ * scratch set-up, the multi-code launch, gather, one read-back); codes
+ * submitted while others run are admitted at the next slice boundary
  * (continuous batching), subject to max_active and max_resident_bytes (the
  * codes' device footprint: tables + scratch).  A dist_batch is internally
  * synchronized: any thread may submit, poll or wait.  A submitted dist_code
@@ -153,7 +155,7 @@ typedef struct {
 typedef struct {
     uint64_t slices, launches, codes_done, active, pending, resident_bytes;
     double gpu_seconds;          /* summed CUDA-event time of the multi-code launches */
-    double plan_seconds;         /* worker time before the launches: planning, packing, uploads */
+    double plan_seconds;         /* worker time before the launches: planning and packing */
     double post_seconds;         /* worker time after them: read-back wait, verdicts, witnesses */
 } dist_batch_stats_t;
 

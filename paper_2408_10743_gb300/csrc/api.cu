@@ -206,6 +206,8 @@ struct GpuExec {
     int run(const LaunchPlan& lp, double deadline_wall, StepResult* out) {
         EnumParams ep;
         plan_params(c->plan, lp, &ep);
+        // U already at the random-code estimate of d: certification work
+        ep.first_static = hs()->U <= (uint32_t)c->plan.d_est ? 1 : 0;
         ep.tables = c->d_tables;
         ep.segs = c->d_segs;
         ep.binom = c->dev->d_binom;

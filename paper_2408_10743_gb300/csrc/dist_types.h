@@ -109,6 +109,7 @@ struct EnumParams {
     uint32_t s_binom, s_segs, s_words;  // shared-memory layout (32-bit word offsets, total)
     unsigned long long nchunks;
     unsigned long long budget_ns;       // stop after this long (per block, %globaltimer); 0 = none
+    int first_static;                   // 1: the first wave of chunks goes by warp index
     GammaDesc g[DIST_MAXGAMMA];
 };
 

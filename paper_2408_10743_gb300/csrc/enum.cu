@@ -139,10 +139,20 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
     // stale (larger) U only skips less, and the walk reads U afresh before
     // its first subset.  A claimed chunk is given up only where everything
     // after it is unneeded (skip) or the budget ended.
-    unsigned long long claimed = 0;
+    // With first_static (set by the host when U already meets the estimate
+    // of d, so that the launch is certification work and no early chunk is
+    // more urgent than another) the grid's first wave of chunks is assigned:
+    // warp w of block b takes chunk w * gridDim + b, consecutive chunks on
+    // different SMs, and the launch does not open with every warp's atomic
+    // on one counter; later claims are then the counter plus the number of
+    // warps.  Otherwise every chunk is claimed, so that the chunks of the
+    // early steps, where a lighter U is found, go to the warps that start
+    // first.
+    const unsigned long long first_off = P.first_static ? (unsigned long long)gridDim.x * (blockDim.x >> 5) : 0ull;
+    unsigned long long claimed = (unsigned long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     uint32_t u_claim = DIST_WINF;
     if (lane == 0) {
-        claimed = atomicAdd(&P.scr->next_chunk, 1ull);
+        if (!P.first_static) claimed = atomicAdd(&P.scr->next_chunk, 1ull);
         u_claim = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
     }
     int seg = 0;                  // chunks are claimed in increasing order
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         if (chunk >= P.nchunks) break;
         const uint32_t u_now = __shfl_sync(0xffffffffu, u_claim, 0);
         if (lane == 0) {
-            claimed = atomicAdd(&P.scr->next_chunk, 1ull);
+            claimed = atomicAdd(&P.scr->next_chunk, 1ull) + first_off;
             u_claim = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
         }
         while (seg + 1 < P.nseg && ssegs[seg + 1].chunk_base <= chunk) ++seg;

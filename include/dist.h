@@ -16,6 +16,15 @@
  * of Gamma_j; Section 2.3's bound for two matrices, generalised) rises after
  * every round; d = U once L >= U.
  *
+ * Steps of the path (the labels S1-S7 used in the sources):
+ *   S1 ingest: validate the rows, pack the bit-planes, reduce to full rank;
+ *   S2 diagonalize: the matrices Gamma_j and their units;
+ *   S3 bounds: L after every (round, matrix) step, the matrices included;
+ *   S4 enumerate: every combination of a round, on the GPU;
+ *   S5 reduce: the running minimum U and the witness slot of each weight;
+ *   S6 certify: stop once L >= U, rebuild and check the witness;
+ *   S7 batch and serve: many codes per launch, continuous admission.
+ *
  * Conventions:
  *   - Every function returns DIST_OK (0) or a negative DIST_E* code; nothing
  *     throws across the ABI.  dist_strerror() names a code.

@@ -318,6 +318,36 @@ extern "C" int hw_plan_segments(const uint8_t* gen, int n, int K, int field, int
     return (int)lp.segs.size();
 }
 
+// Decodes a witness slot that names the plan's seed codeword (the path a
+// codeword kept from another search trial takes): the seed is the sum of the
+// given basis rows.  Returns its weight, or a negative value on failure.
+extern "C" int hw_seed_decode(const uint8_t* gen, int n, int K, const int* rows, int nrows, uint8_t* witness,
+                              uint8_t* coeffs) {
+    Plan p;
+    if (plan_build(gen, n, K, 2, &p)) return -1;
+    Vec v;
+    Coef k;
+    memset(&v, 0, sizeof v);
+    memset(&k, 0, sizeof k);
+    for (int t = 0; t < nrows; t++) {
+        const int i = rows[t];
+        if (i < 0 || i >= p.k_eff) return -2;
+        for (int w = 0; w < DIST_MAXW; w++) {
+            v.x[w] ^= p.basis[i].x[w];
+            v.z[w] ^= p.basis[i].z[w];
+        }
+        k.p[0][i >> 5] ^= 1u << (i & 31);
+    }
+    p.seed_vec = v;
+    p.seed_coef = k;
+    WitnessSlot s;
+    memset(&s, 0, sizeof s);
+    s.claim = 1;
+    s.gamma = DIST_SEED_GAMMA;
+    s.weight = (uint32_t)vec_weight(v, p.W);
+    return plan_decode(p, s, witness, coeffs) == P_OK ? (int)s.weight : -3;
+}
+
 // 1 if planning for tw1 warps and re-cutting for tw2 gives the same launch as
 // planning for tw2 directly, 0 if not, negative on a planning error.
 extern "C" int hw_rechunk_same(const uint8_t* gen, int n, int K, int field, int tw1, int tw2) {

@@ -53,6 +53,10 @@ def hw():
     L.hw_rechunk_same.restype = ctypes.c_int
     L.hw_rechunk_same.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hw_seed_decode.restype = ctypes.c_int
+    L.hw_seed_decode.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
+                                 ctypes.POINTER(ctypes.c_uint8)]
     L.hw_solve_sliced.restype = ctypes.c_int
     L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -265,6 +269,26 @@ def test_plan_chunk_sizes(hw):
         else:
             assert (subsets + 32 * spl - 1) // (32 * spl) >= min(warps, (subsets + 31) // 32) // 2, (step, i, spl)
     assert fast_before_last > 0
+
+
+def test_seed_codeword_decodes(hw):
+    """A witness slot naming the plan's seed codeword (one kept from another
+    search trial) decodes to that codeword: the returned coefficients over
+    the input rows rebuild the witness, and its weight is popcount(x | z)."""
+    rng = np.random.default_rng(7)
+    for n, K in ((12, 10), (30, 24), (72, 72)):
+        g = np.ascontiguousarray(synth.random_f2_code(n, K, synth.Xoshiro256ss(n * 131 + K)), dtype=np.uint8)
+        for _ in range(5):
+            rows = sorted(rng.choice(K, size=int(rng.integers(1, min(K, 6) + 1)), replace=False).tolist())
+            arr = (ctypes.c_int * len(rows))(*rows)
+            wit = (ctypes.c_uint8 * (2 * n))()
+            cof = (ctypes.c_uint8 * K)()
+            w = hw.hw_seed_decode(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n, K, arr, len(rows), wit, cof)
+            assert w > 0
+            wv = np.array(wit[:], dtype=np.uint8)
+            cv = np.array(cof[:], dtype=np.uint8)
+            assert np.array_equal((cv.astype(np.int64) @ g.astype(np.int64)) % 2, wv)
+            assert w == int(np.count_nonzero(wv[:n] | wv[n:]))
 
 
 def test_colex_walk(hw):

@@ -160,3 +160,37 @@ def test_exclusion_rank():
     with pytest.raises(dist.DistError) as e:
         dist.dist_plan_info_get(N, n_stab=N.shape[0])
     assert e.value.code == -6
+
+
+def test_information_set_search():
+    """The qubit-order search (reading C14) on the QC n = 72 code: the index
+    order leaves the second matrix one free row, a searched order leaves none
+    (so the bound gains one per matrix from the first round on); the estimate
+    of d does not depend on the order, and the same code always gets the same
+    plan."""
+    g = synth.single_qc(0)
+    prev = dist.dist_get_plan_search()
+    try:
+        dist.dist_set_plan_search(0)
+        a = dist.dist_plan_info_get(g)
+        dist.dist_set_plan_search(8)
+        b = dist.dist_plan_info_get(g)
+        c = dist.dist_plan_info_get(g)
+    finally:
+        dist.dist_set_plan_search(prev)
+    fa = list(a.f[:a.n_gamma_built])
+    fb = list(b.f[:b.n_gamma_built])
+    assert sum(fa) > 0 and sum(fb) == 0
+    assert a.d_est == b.d_est and b.u0 <= a.u0
+    assert list(b.a[:b.n_gamma_built]) == list(c.a[:c.n_gamma_built])
+    assert fb == list(c.f[:c.n_gamma_built]) and b.u0 == c.u0
+    # a small code (little estimated work) is planned on the index order only
+    s = synth.random_f2_code(16, 12, synth.Xoshiro256ss(3))
+    dist.dist_set_plan_search(0)
+    try:
+        x = dist.dist_plan_info_get(s)
+    finally:
+        dist.dist_set_plan_search(prev)
+    y = dist.dist_plan_info_get(s)
+    assert list(x.a[:x.n_gamma_built]) == list(y.a[:y.n_gamma_built])
+    assert list(x.f[:x.n_gamma_built]) == list(y.f[:y.n_gamma_built])

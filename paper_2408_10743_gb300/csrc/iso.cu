@@ -6,7 +6,7 @@
 // One launch per step (round r of matrix j).  Each block stages the matrix's
 // rows, restricted to the columns outside its information set (a pivot row
 // adds exactly 1 on the set, a free row 0), in shared memory; lanes walk
-// rank ranges of r-subsets in colexicographic order.
+// rank ranges of r-subsets in revolving-door order.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -16,8 +16,8 @@
 #include "../../include/dist.h"
 #include "code.h"
 #include "iso.h"
-#include "colex.cuh"
 #include "solve.h"
+#include "walk.cuh"
 
 namespace dist {
 
@@ -94,19 +94,14 @@ __device__ __forceinline__ uint32_t iso_full(const uint32_t* srow, const uint8_t
     return np;
 }
 
-// Lane walk, colexicographic order: for a fixed top c[1..r-1] the lowest
-// element c1 runs over 0..c[1]-1, and the codeword is (sum of the top rows)
-// + row c1 -- one staged row per codeword.  Only the first four words of the
-// sum and the number of pivot rows in it are formed, in two levels: np +
-// popc(words 0-1) bounds the weight from below; if it is below the running
-// threshold, words 2-3 are added; only if np + popc(words 0-3) is still below
-// it is the full weight computed from the subset.  While the threshold is
-// high the second level runs almost always (four POPCs per codeword); once
-// it is near d the first level alone rejects nearly everything.  When c1 has
-// run out, the top moves to its colex successor (rows of the changed
-// elements out, the new ones in).
+// Lane walk in revolving-door order: every step takes one row out of the
+// running sum and one in, so the cost of a step does not depend on how many
+// positions move (a colex carry re-adds every reset row).  The two lowest
+// positions live in registers; the common step (the lowest row one up or
+// down) applies one staged neighbour delta, the others go through
+// rd_next_delta on the subset in local memory.
 template <int WORDS>
-__global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoParams P) {
+__global__ void __launch_bounds__(256) iso_rd_kernel(const __grid_constant__ IsoParams P) {
     extern __shared__ __align__(16) uint32_t iso_smem[];
     const int K = P.K;
     uint4* sfil = reinterpret_cast<uint4*>(iso_smem);       // [K]: words 0-3
@@ -128,8 +123,6 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
         sfil[t] = make_uint4(srow[t * WORDS], WORDS > 1 ? srow[t * WORDS + 1] : 0u,
                              WORDS > 2 ? srow[t * WORDS + 2] : 0u, WORDS > 3 ? srow[t * WORDS + 3] : 0u);
     __syncthreads();
-    // the common carry (c[1] moves up by one) XORs rows c and c + 1 out and
-    // in: one staged delta instead of two rows
     for (int t = threadIdx.x; t < K; t += blockDim.x) {
         const uint4 a = sfil[t], b = t + 1 < K ? sfil[t + 1] : make_uint4(0u, 0u, 0u, 0u);
         sdel[t] = make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
@@ -145,89 +138,69 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
         if (lane == 0) chunk = atomicAdd(&P.scr->next_chunk, 1ull);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= P.nchunks) break;
-        // every lane of the warp runs spl iterations (lanes past the end of
-        // their range idle), so the warp stays converged and the rare carries
-        // are entered together
         const unsigned long long lo = (chunk * 32ull + (unsigned long long)lane) * P.spl;
         const uint32_t left = lo < P.nsub ? (uint32_t)(min(lo + P.spl, P.nsub) - lo) : 0u;
-        uint8_t c[DIST_MAXR];
-        uint4 b = make_uint4(0u, 0u, 0u, 0u);  // words 0-3 of the top c[1..r-1]
+        uint8_t s[DIST_MAXR];
+        uint4 b = make_uint4(0u, 0u, 0u, 0u);
         uint32_t npb = 0;
-        int c1 = 0, c2 = K, c3 = K;  // c[0], c[1] (K if r < 2), c[2] (K if r < 3) in registers
+        int c0 = 0, c1 = K;  // s[0], and s[1] (K if r < 2)
         if (left) {
-            colex_unrank(P.binom, DIST_MAXR + 1, K, lo, r, c);
-            for (int t = 1; t < r; t++) {
-                const uint4 q = sfil[c[t]];
+            rd_unrank(P.binom, DIST_MAXR + 1, K, lo, r, s);
+            for (int t = 0; t < r; t++) {
+                const uint4 q = sfil[s[t]];
                 b.x ^= q.x;
                 b.y ^= q.y;
                 b.z ^= q.z;
                 b.w ^= q.w;
-                npb += snp[c[t]];
+                npb += snp[s[t]];
             }
-            c1 = c[0];
-            if (r >= 2) c2 = c[1];
-            if (r >= 3) c3 = c[2];
+            c0 = s[0];
+            if (r >= 2) c1 = s[1];
         }
-        thr = min(thr, *Up);
+        uint32_t u_next = *Up;
         for (uint32_t k = 0; k < P.spl; k++) {
-            const bool act = k < left;
-            if (act) {
-                const uint4 q = sfil[c1];
-                uint32_t w = npb + snp[c1] + (uint32_t)__popc(b.x ^ q.x) + (uint32_t)__popc(b.y ^ q.y);
-                if (w < thr) {
-                    if (WORDS > 2) w += (uint32_t)__popc(b.z ^ q.z) + (uint32_t)__popc(b.w ^ q.w);
-                    if (w < thr) {
-                        c[0] = (uint8_t)c1;
-                        if (r >= 2) c[1] = (uint8_t)c2;
-                        if (r >= 3) c[2] = (uint8_t)c3;
-                        const uint32_t full = WORDS > 4 ? iso_full<WORDS>(srow, spiv, c, r) : w;
-                        if (full < thr) iso_record(P, full, c, thr);
-                    }
-                }
+            if ((k & 31u) == 0u) {  // the running bound, read 32 steps ahead
+                thr = min(thr, u_next);
+                u_next = *Up;
             }
-            const bool carry = act && k + 1 < left && c1 + 1 >= c2;
-            if (act && !carry) c1++;
-            if (__any_sync(0xffffffffu, carry) && carry) {
-                // c1 ran out: the top moves to its colex successor, usually
-                // c[1] alone (one row out, one in)
-                if (c2 + 1 < c3) {
-                    const uint4 dq = sdel[c2];
-                    b.x ^= dq.x;
-                    b.y ^= dq.y;
-                    b.z ^= dq.z;
-                    b.w ^= dq.w;
-                    npb = (uint32_t)((int32_t)npb + sdnp[c2]);
-                    c2++;
-                } else {
-                    c[0] = (uint8_t)(c2 - 1);
-                    c[1] = (uint8_t)c2;
-                    if (r >= 3) c[2] = (uint8_t)c3;
-                    int jj = 1;
-                    while (jj < r && c[jj] + 1 >= (jj + 1 < r ? (int)c[jj + 1] : K)) jj++;
-                    if (jj < r) {  // (jj = r only after the last subset: cannot happen here)
-                        for (int t = 1; t <= jj; t++) {
-                            const uint4 qq = sfil[c[t]];
-                            b.x ^= qq.x;
-                            b.y ^= qq.y;
-                            b.z ^= qq.z;
-                            b.w ^= qq.w;
-                            npb -= snp[c[t]];
-                        }
-                        colex_carry(c, r, K);
-                        for (int t = 1; t <= jj; t++) {
-                            const uint4 qq = sfil[c[t]];
-                            b.x ^= qq.x;
-                            b.y ^= qq.y;
-                            b.z ^= qq.z;
-                            b.w ^= qq.w;
-                            npb += snp[c[t]];
-                        }
-                        c2 = c[1];
-                        c3 = r >= 3 ? c[2] : K;
+            if (k < left) {
+                uint32_t w = npb + (uint32_t)__popc(b.x) + (uint32_t)__popc(b.y);
+                if (w < thr) {
+                    if (WORDS > 2) w += (uint32_t)__popc(b.z) + (uint32_t)__popc(b.w);
+                    if (w < thr) {
+                        s[0] = (uint8_t)c0;
+                        const uint32_t full = WORDS > 4 ? iso_full<WORDS>(srow, spiv, s, r) : w;
+                        if (full < thr) iso_record(P, full, s, thr);
                     }
-                    thr = min(thr, *Up);
                 }
-                c1 = 0;
+                if (k + 1 < left) {
+                    int o = -1;
+                    if (r & 1) {
+                        if (c0 + 1 < c1) o = c0++;
+                    } else if (c0 > 0) {
+                        o = --c0;
+                    }
+                    if (o >= 0) {  // the lowest row moves by one: rows o and o + 1 swap places
+                        const uint4 dq = sdel[o];
+                        b.x ^= dq.x;
+                        b.y ^= dq.y;
+                        b.z ^= dq.z;
+                        b.w ^= dq.w;
+                        npb = (uint32_t)((int32_t)npb + ((r & 1) ? sdnp[o] : -sdnp[o]));
+                    } else {
+                        s[0] = (uint8_t)c0;
+                        int out, in;
+                        rd_next_delta(s, r, K, &out, &in);
+                        const uint4 qo = sfil[out], qi = sfil[in];
+                        b.x ^= qo.x ^ qi.x;
+                        b.y ^= qo.y ^ qi.y;
+                        b.z ^= qo.z ^ qi.z;
+                        b.w ^= qo.w ^ qi.w;
+                        npb = npb - snp[out] + snp[in];
+                        c0 = s[0];
+                        if (r >= 2) c1 = s[1];
+                    }
+                }
             }
         }
         unsigned long long done = left;
@@ -238,32 +211,32 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
 }
 
 template <int WORDS>
-cudaError_t iso_launch_w(const IsoParams& P, int sms, cudaStream_t st) {
+cudaError_t iso_rd_launch_w(const IsoParams& P, int sms, cudaStream_t st) {
     const size_t smem = (size_t)P.K * 40 + (size_t)P.K * WORDS * 4 + (size_t)P.K + 16;
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, iso_kernel<WORDS>, 256, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, iso_rd_kernel<WORDS>, 256, smem) != cudaSuccess)
         return cudaErrorUnknown;
     bps = std::max(1, bps);
     const unsigned long long want = (P.nchunks + 7) / 8;
     const int grid = (int)std::min<unsigned long long>(want, (unsigned long long)sms * bps);
-    iso_kernel<WORDS><<<std::max(1, grid), 256, smem, st>>>(P);
+    iso_rd_kernel<WORDS><<<std::max(1, grid), 256, smem, st>>>(P);
     return cudaGetLastError();
 }
 
-cudaError_t iso_launch(const IsoParams& P, int words, int sms, cudaStream_t st) {
+cudaError_t iso_rd_launch(const IsoParams& P, int words, int sms, cudaStream_t st) {
     switch (words) {
-        case 1: return iso_launch_w<1>(P, sms, st);
-        case 2: return iso_launch_w<2>(P, sms, st);
-        case 3: return iso_launch_w<3>(P, sms, st);
-        case 4: return iso_launch_w<4>(P, sms, st);
-        case 5: return iso_launch_w<5>(P, sms, st);
-        case 6: return iso_launch_w<6>(P, sms, st);
-        case 7: return iso_launch_w<7>(P, sms, st);
-        case 8: return iso_launch_w<8>(P, sms, st);
-        case 9: return iso_launch_w<9>(P, sms, st);
-        case 10: return iso_launch_w<10>(P, sms, st);
-        case 11: return iso_launch_w<11>(P, sms, st);
-        default: return iso_launch_w<12>(P, sms, st);
+        case 1: return iso_rd_launch_w<1>(P, sms, st);
+        case 2: return iso_rd_launch_w<2>(P, sms, st);
+        case 3: return iso_rd_launch_w<3>(P, sms, st);
+        case 4: return iso_rd_launch_w<4>(P, sms, st);
+        case 5: return iso_rd_launch_w<5>(P, sms, st);
+        case 6: return iso_rd_launch_w<6>(P, sms, st);
+        case 7: return iso_rd_launch_w<7>(P, sms, st);
+        case 8: return iso_rd_launch_w<8>(P, sms, st);
+        case 9: return iso_rd_launch_w<9>(P, sms, st);
+        case 10: return iso_rd_launch_w<10>(P, sms, st);
+        case 11: return iso_rd_launch_w<11>(P, sms, st);
+        default: return iso_rd_launch_w<12>(P, sms, st);
     }
 }
 
@@ -389,7 +362,7 @@ extern "C" int dist_solve_isometry(dist_code* c, dist_result* out, void* cuda_st
             for (int w = 0; w < DIST_MAXCW; w++) P.outside[w] = p.outside[w];
             if (cudaMemsetAsync(&dscr->next_chunk, 0, sizeof(unsigned long long), st) != cudaSuccess ||
                 cudaEventRecord(kit->e0, st) != cudaSuccess ||
-                iso_launch(P, ip.words, c->dev->sms, st) != cudaSuccess ||
+                iso_rd_launch(P, ip.words, c->dev->sms, st) != cudaSuccess ||
                 cudaEventRecord(kit->e1, st) != cudaSuccess ||
                 cudaMemcpyAsync(hs, dscr, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess) {

@@ -10,7 +10,6 @@
 
 #include "plan.h"
 #include "solve.h"
-#include "colex.cuh"
 #include "walk.cuh"
 
 using namespace dist;
@@ -364,20 +363,16 @@ extern "C" int hw_rechunk_same(const uint8_t* gen, int n, int K, int field, int 
     return memcmp(a.segs.data(), b.segs.data(), a.segs.size() * sizeof(SegDesc)) == 0 ? 1 : 0;
 }
 
-// Colexicographic walk as the isometry kernel takes it: unrank rank0, then
-// the lowest element counts up to the next one, then colex_carry.
-extern "C" void hw_colex_walk(int n, int t, unsigned long long rank0, int count, uint8_t* out) {
+// Walks count subsets of {0..n-1} in revolving-door order from rank rank0
+// with rd_next_delta, recording each subset and the element that left and
+// the one that entered at each step.
+extern "C" void hw_rd_delta_walk(int n, int t, unsigned long long rank0, int count, uint8_t* out, int* moves) {
     std::vector<unsigned long long> B((DIST_MAXU + 1) * (DIST_MAXR + 1));
     binom_table(B.data());
-    uint8_t c[DIST_MAXR];
-    colex_unrank(B.data(), DIST_MAXR + 1, n, rank0, t, c);
+    uint8_t s[DIST_MAXR];
+    rd_unrank(B.data(), DIST_MAXR + 1, n, rank0, t, s);
     for (int k = 0; k < count; k++) {
-        for (int p = 0; p < t; p++) out[k * t + p] = c[p];
-        const int lim = t >= 2 ? c[1] : n;
-        if (c[0] + 1 < lim) {
-            c[0]++;
-        } else if (t < 2 || colex_carry(c, t, n) < 0) {
-            break;
-        }
+        memcpy(out + (size_t)k * t, s, t);
+        if (k + 1 < count) rd_next_delta(s, t, n, &moves[2 * k], &moves[2 * k + 1]);
     }
 }

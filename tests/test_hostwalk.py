@@ -48,8 +48,8 @@ def hw():
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_ulonglong)]
-    L.hw_colex_walk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int,
-                                ctypes.POINTER(ctypes.c_uint8)]
+    L.hw_rd_delta_walk.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int)]
     L.hw_rechunk_same.restype = ctypes.c_int
     L.hw_rechunk_same.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -291,19 +291,29 @@ def test_seed_codeword_decodes(hw):
             assert w == int(np.count_nonzero(wv[:n] | wv[n:]))
 
 
-def test_colex_walk(hw):
-    """The isometry kernel's order: unranking by the combinatorial number
-    system and stepping (lowest element up, then colex_carry) visit the
-    t-subsets in colexicographic order from any start rank."""
-    from itertools import combinations
-    for n, t in ((1, 1), (6, 1), (6, 2), (7, 3), (8, 4), (9, 5), (10, 6), (12, 7), (9, 9)):
-        seq = sorted(combinations(range(n), t), key=lambda c: c[::-1])
-        for start in sorted({0, 1, len(seq) // 3, len(seq) - 1} & set(range(len(seq)))):
-            cnt = len(seq) - start
+def test_rd_delta_walk(hw):
+    """The isometry kernel's step: rd_next_delta follows the same revolving-
+    door order as rd_next (the package walk) from any start rank, and at
+    every step exactly the element it reports leaving leaves and the one it
+    reports entering enters, so the kernel's running sum needs one row out
+    and one row in."""
+    from math import comb
+    for n, t in ((1, 1), (6, 1), (6, 2), (7, 3), (8, 4), (9, 5), (10, 6), (12, 7), (9, 9), (14, 4)):
+        total = comb(n, t)
+        ref = (ctypes.c_uint8 * (total * t))()
+        hw.hw_rd_walk(n, t, 0, total, ref)
+        seq = [tuple(ref[k * t:(k + 1) * t]) for k in range(total)]
+        assert len(set(seq)) == total
+        for start in sorted({0, 1, total // 3, total - 1} & set(range(total))):
+            cnt = total - start
             out = (ctypes.c_uint8 * (cnt * t))()
-            hw.hw_colex_walk(n, t, start, cnt, out)
+            mv = (ctypes.c_int * (2 * max(cnt, 1)))()
+            hw.hw_rd_delta_walk(n, t, start, cnt, out, mv)
             got = [tuple(out[k * t:(k + 1) * t]) for k in range(cnt)]
             assert got == seq[start:], (n, t, start)
+            for k in range(cnt - 1):
+                a, b = set(got[k]), set(got[k + 1])
+                assert a - b == {mv[2 * k]} and b - a == {mv[2 * k + 1]}, (n, t, k)
 
 
 def test_rechunk_equals_fresh_plan(hw):

@@ -17,6 +17,7 @@
 #include "code.h"
 #include "iso.h"
 #include "solve.h"
+#include "rdorder.cuh"
 #include "walk.cuh"
 
 namespace dist {

@@ -10,6 +10,7 @@
 
 #include "plan.h"
 #include "solve.h"
+#include "rdorder.cuh"
 #include "walk.cuh"
 
 using namespace dist;

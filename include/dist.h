@@ -196,8 +196,9 @@ int dist_batch_destroy(dist_batch *b);
  * 1..256); a lane chunk holds at most 2^lane_cap_log2 (default 14, range
  * 8..24) codewords, and a fast-path segment at least 2^lane_floor_log2
  * (default 12, range 1..lane_cap_log2) unless that would leave it fewer
- * chunks than resident warps.  Values outside the ranges are clamped; fields <= 0 keep the
- * current value.  dist_autotune times calibration solves (random codes of
+ * chunks than resident warps; outside a launch's last step a fast-path lane
+ * chunk also holds at least eight subsets.  Values outside the ranges are
+ * clamped; fields <= 0 keep the current value.  dist_autotune times calibration solves (random codes of
  * 64 x 56 and 72 x 72) on the current device over a grid of the three,
  * applies the setting with the best geometric-mean codewords/s, and returns
  * it (and that rate) -- about budget_s seconds (<= 0: about 10 s).
@@ -211,6 +212,10 @@ typedef struct {
 int dist_set_tuning(const dist_tuning *t);
 int dist_get_tuning(dist_tuning *t);
 int dist_autotune(dist_tuning *best, double budget_s);
+/* The tuning search of dist_autotune, timed on the caller's codes
+ * (initialised on the current device, not in a batch): tunes for a known
+ * workload. */
+int dist_autotune_codes(dist_code *const *codes, int count, double budget_s, dist_tuning *best);
 /*
  * Information-set search of the planner (process-wide): for a code whose
  * estimated work exceeds 5e8 codewords and whose enumerated matrices have
@@ -220,9 +225,6 @@ int dist_autotune(dist_tuning *best, double budget_s);
  */
 int dist_set_plan_search(int trials);
 int dist_get_plan_search(void);
-/* Same search, timed on the caller's codes (initialised on the current
- * device, not in a batch): tunes for a known workload. */
-int dist_autotune_codes(dist_code *const *codes, int count, double budget_s, dist_tuning *best);
 
 /*
  * dist_plan_info -- host-only view of the plan step S2-S3 built for an input

@@ -513,6 +513,13 @@ def run_ours(args):
             "popc_peak_Gops": peak.popc_per_s / 1e9, "lop3_peak_Gops": peak.lop3_per_s / 1e9,
             "intpeak_sm_mhz": peak.sm_mhz,
             "kernel_ms_per_step": 1e3 * kernel_s / len(kern_s)}
+    # the ceiling derived from unit counts and clocks: one POPC per codeword,
+    # 16 POPC lanes per clock per SM, every SM, the maximum SM clock
+    max_mhz = clk.get("sm_max_mhz") or 2070.0
+    derived = 16.0 * float(peak.sms) * float(max_mhz) * 1e6
+    roof["derived_peak"] = derived / 1e9
+    roof["frac_of_derived"] = achieved / derived if derived > 0 else None
+    roof["derived_peak_source"] = "POPC 16/clk/SM x %d SMs x %.0f MHz (one POPC per codeword)" % (peak.sms, max_mhz)
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,

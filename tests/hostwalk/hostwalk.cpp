@@ -318,6 +318,28 @@ extern "C" int hw_plan_segments(const uint8_t* gen, int n, int K, int field, int
     return (int)lp.segs.size();
 }
 
+// The steps of one launch planned from round 1 (bound U_bound, at most
+// max_codewords): for step k, (r, jpos, L_before) in steps[3k..3k+2]; the
+// L_before of every segment in seg_L.  Returns the number of steps (and
+// *nseg), or a negative value on failure.
+extern "C" int hw_plan_steps(const uint8_t* gen, int n, int K, int field, int U_bound, double max_codewords,
+                             int* steps, int max_steps, int* seg_L, int max_segs, int* nseg) {
+    Plan p;
+    if (plan_build(gen, n, K, field, &p)) return -1;
+    LaunchPlan lp;
+    if (plan_launch(p, 1, 0, plan_initial_bound(p), U_bound, 2432, max_codewords, &lp)) return -2;
+    const int ns = (int)lp.step_r.size();
+    if (ns > max_steps || (int)lp.segs.size() > max_segs) return -3;
+    for (int k = 0; k < ns; k++) {
+        steps[3 * k] = lp.step_r[k];
+        steps[3 * k + 1] = lp.step_jpos[k];
+        steps[3 * k + 2] = lp.step_L_before[k];
+    }
+    for (size_t t = 0; t < lp.segs.size(); t++) seg_L[t] = lp.segs[t].L_before;
+    *nseg = (int)lp.segs.size();
+    return ns;
+}
+
 // Decodes a witness slot that names the plan's seed codeword (the path a
 // codeword kept from another search trial takes): the seed is the sum of the
 // given basis rows.  Returns its weight, or a negative value on failure.

@@ -53,6 +53,10 @@ def hw():
     L.hw_rechunk_same.restype = ctypes.c_int
     L.hw_rechunk_same.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hw_plan_steps.restype = ctypes.c_int
+    L.hw_plan_steps.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.hw_seed_decode.restype = ctypes.c_int
     L.hw_seed_decode.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
@@ -269,6 +273,39 @@ def test_plan_chunk_sizes(hw):
         else:
             assert (subsets + 32 * spl - 1) // (32 * spl) >= min(warps, (subsets + 31) // 32) // 2, (step, i, spl)
     assert fast_before_last > 0
+
+
+def test_launch_bounds_follow_the_package_bound(hw):
+    """The bound in force before every planned step is the package bound of
+    Section 2.3, generalised: with J's matrices in order, once J[0..jpos-1]
+    have finished round r and the others round r - 1, every unseen codeword
+    weighs at least sum max(0, r + 1 - f) over the first plus sum
+    max(0, r - f) over the others.  It never decreases through a launch,
+    which the kernel's skip and the certification rely on."""
+    import paper_2408_10743_gb300 as dist
+    codes = [(synth.single_qc(0), 2), (synth.random_f2_code(40, 30, synth.Xoshiro256ss(5)), 2),
+             (synth.random_f2_code(24, 20, synth.Xoshiro256ss(8)), 2), (synth.single_f4(0), 4)]
+    for g, field in codes:
+        g = np.ascontiguousarray(g, dtype=np.uint8)
+        n = g.shape[1] // 2 if field == 2 else g.shape[1]
+        info = dist.dist_plan_info_get(g, field=field)
+        J = list(info.order[:info.n_gamma_used])
+        f = [info.f[j] for j in J]
+        steps = (ctypes.c_int * (3 * 256))()
+        segL = (ctypes.c_int * 512)()
+        nseg = ctypes.c_int()
+        k = hw.hw_plan_steps(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n, g.shape[0], field,
+                             1 << 20, 1e11, steps, 256, segL, 512, ctypes.byref(nseg))
+        assert k > 1
+        prev = 0
+        for i in range(k):
+            r, jpos, Lb = steps[3 * i], steps[3 * i + 1], steps[3 * i + 2]
+            want = sum(max(0, r + 1 - f[t]) for t in range(jpos)) + sum(max(0, r - f[t]) for t in range(jpos, len(J)))
+            assert Lb == max(1, want) if i == 0 else Lb == want, (i, r, jpos, Lb, want)
+            assert Lb >= prev
+            prev = Lb
+        sl = list(segL[:nseg.value])
+        assert all(a <= b for a, b in zip(sl, sl[1:]))
 
 
 def test_seed_codeword_decodes(hw):

@@ -133,6 +133,37 @@ def test_tiny_vs_oracle(hw, kind):
         check_witness(g, r)
 
 
+def test_dependent_rows_vs_oracle(hw):
+    """More generator rows than 2n (dependent by counting): the planner
+    reduces them to a basis, and d is that of their span."""
+    rng = np.random.default_rng(41)
+    for _ in range(60):
+        n = int(rng.integers(1, 7))
+        K = 2 * n + int(rng.integers(1, 5))
+        g = tiny_random_code(rng, n, K, ["iid", "css", "sparse"][int(rng.integers(0, 3))])
+        if not g.any():
+            continue
+        rc, r = solve(hw, g, warps=int(rng.integers(1, 4)))
+        assert rc == 0
+        assert r.d == oracle.bz(g)["d"], (n, K)
+        assert r.k_eff <= 2 * n
+        check_witness(g, r)
+
+
+def test_qc72_on_the_search_plan(hw):
+    """The QC n = 72 code solved by the exact lane code on the CPU, planned
+    with the information-set search (the library default): d matches the
+    stored oracle value."""
+    golden = os.path.join(os.path.dirname(__file__), "golden", "qc72_seed0.txt")
+    want = next(int(l.split()[1]) for l in open(golden) if l.startswith("d "))
+    g = synth.single_qc(0)
+    rc, r = solve(hw, g, warps=2432)
+    assert rc == 0
+    assert r.d == want
+    assert r.codewords == 193157838  # rounds 1-5 of both matrices, 36 + 36 units, no free rows
+    check_witness(g, r)
+
+
 def test_medium_vs_oracle(hw):
     """n up to 48 (two words per plane): fast path, word-0 filter, slow path."""
     for t in range(30):

@@ -108,26 +108,37 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_digest():
+def kernel_digest():
+    """Digest of the enumeration kernel's sources."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2408_10743_gb300", "csrc")
-    for name in ("walk.cuh", "enum.cu", "dist_types.h", "plan.cpp"):
+    for name in ("walk.cuh", "enum.cu", "dist_types.h"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(dist, g, field):
     """DRAM bytes per launch of the enumeration kernel from the committed ncu
-    summary, or None if the kernel source changed since it was captured."""
+    summary, and a note saying why it applies or not: it applies only when
+    both the kernel's sources and what its first launch reads for this code
+    on this device, under the tuning in force (tables, segment table,
+    parameters: dist_launch_digest), are the ones the capture ran."""
     try:
         with open(PROFILE_JSON) as fh:
             p = json.load(fh)
     except (OSError, ValueError):
-        return None
-    if p.get("source_digest") != source_digest():
-        return None
-    return p.get("dram_bytes_per_launch")
+        return None, "no committed profile"
+    if p.get("kernel_digest") != kernel_digest():
+        return None, "kernel sources changed since the capture"
+    try:
+        launch = "%016x" % dist.dist_launch_digest(g, field)
+    except Exception as e:
+        return None, "launch digest unavailable: %s" % e
+    if p.get("launch_digest") != launch:
+        return None, "launch %s differs from the captured %s" % (launch, p.get("launch_digest"))
+    return p.get("dram_bytes_per_launch"), "ncu capture in profiles/enum_kernel_qc72.json (kernel %s, launch %s)" % (
+        p.get("kernel_digest"), launch)
 
 
 def cpu_baseline(g, field, budget_s):
@@ -505,9 +516,11 @@ def run_ours(args):
 
     kernel_s = sum(kern_s)
     achieved = total_cw / kernel_s if kernel_s > 0 else 0.0
+    traffic, traffic_note = profiled_traffic(dist, g, field)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak.mix_per_s / 1e9,
             "unit": "Gcodewords/s", "frac": achieved / peak.mix_per_s if peak.mix_per_s else None,
-            "traffic": profiled_traffic(),
+            "traffic": traffic,
+            "traffic_source": traffic_note,
             "kernel": "dist::enum_kernel",
             "peak_source": "dist_intpeak mix (2 LOP3 + POPC + min per codeword), measured in this run",
             "popc_peak_Gops": peak.popc_per_s / 1e9, "lop3_peak_Gops": peak.lop3_per_s / 1e9,

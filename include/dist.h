@@ -252,6 +252,23 @@ int dist_plan_unit(const uint8_t *generator, int n, int K, int field, int gamma,
                    int rep, uint8_t *vec_out, int *qubit, int *kind);
 
 /*
+ * dist_launch_digest -- a 64-bit FNV-1a digest of what the first enumeration
+ * launch of dist_solve reads for this input: the device tables, the seed
+ * bound and its witness slot, the launch parameters (device pointers and the
+ * time budget left out) and the segment table, under the current tuning.
+ *   generator, n, K, field, n_stab: as dist_init and dist_set_exclude.
+ *   target_warps: resident warps the launch is planned for (SMs x blocks per
+ *                 SM x 8); > 0 needs no device, <= 0 takes the current
+ *                 device's (a CUDA call, DIST_ECUDA without one).
+ *   digest: written on success, 0 on failure.
+ * Equal digests hand the kernel byte-identical work, so a hardware-counter
+ * profile of that launch (its DRAM traffic) stays valid for as long as the
+ * kernel sources are unchanged too.  Errors: as dist_init.
+ */
+int dist_launch_digest(const uint8_t *generator, int n, int K, int field, int n_stab, int target_warps,
+                       uint64_t *digest);
+
+/*
  * Qubit stabilizer codes (Section 2).  The classical stabilizer code S of an
  * [[n, k, d(Q)]] code lies in its symplectic dual N = S^{perp_s} (the
  * classical normalizer code, dimension n + k); d(Q) = wt_s(N minus S) for

@@ -407,6 +407,27 @@ int dist_plan_info_get(const uint8_t* generator, int n, int K, int field, int n_
     return DIST_OK;
 }
 
+int dist_launch_digest(const uint8_t* generator, int n, int K, int field, int n_stab, int target_warps,
+                       uint64_t* digest) {
+    if (!digest) return DIST_EINVAL;
+    *digest = 0;
+    Plan p;
+    int rc = map_plan_rc(plan_build(generator, n, K, field, &p));
+    if (rc) return rc;
+    if (n_stab) {
+        rc = map_plan_rc(plan_set_exclude(&p, n_stab));
+        if (rc) return rc;
+    }
+    if (target_warps <= 0) {  // this device's, as a solve computes it
+        DeviceCtx* d = nullptr;
+        rc = device_ctx(&d);
+        if (rc) return rc;
+        target_warps = d->sms * d->blocks_per_sm * DIST_ENUM_WARPS;
+    }
+    *digest = first_launch_digest(p, target_warps);
+    return DIST_OK;
+}
+
 int dist_plan_unit(const uint8_t* generator, int n, int K, int field, int gamma, int unit, int rep,
                    uint8_t* vec_out, int* qubit, int* kind) {
     if (!vec_out) return DIST_EINVAL;

@@ -132,33 +132,41 @@ static unsigned long long upow3(int e) {
 // ---------------------------------------------------------------------------
 // S1: ingest and rank reduction.
 // ---------------------------------------------------------------------------
+// Eight bytes, each 0 or 1, packed into eight bits (byte t -> bit t): the
+// multiplier moves byte t's low bit to bit 56 + t, and no two partial products
+// meet, so nothing carries.
+static inline uint32_t pack8(uint64_t b) { return (uint32_t)(((b & 0x0101010101010101ull) * 0x0102040810204080ull) >> 56); }
+
 static int load_input(const uint8_t* gen, int n, int K, int field, Plan* p) {
     p->input.assign(K, Vec());
-    unsigned bad = 0;  // any symbol out of range
+    uint64_t bad = 0;  // any symbol out of range
     for (int r = 0; r < K; r++) {
         Vec& v = p->input[r];
         memset(&v, 0, sizeof v);
-        for (int w = 0; w * 32 < n; w++) {
-            uint32_t xw = 0, zw = 0;
-            const int hi = std::min(32, n - w * 32);
-            for (int b = 0; b < hi; b++) {
-                const int i = w * 32 + b;
-                unsigned a, c;
-                if (field == 2) {
-                    a = gen[(size_t)r * 2 * n + i];
-                    c = gen[(size_t)r * 2 * n + n + i];
-                    bad |= (a | c) & ~1u;
-                } else {
-                    const unsigned s4 = gen[(size_t)r * n + i];
-                    bad |= s4 & ~3u;
-                    a = s4 & 1u;
-                    c = (s4 >> 1) & 1u;
-                }
-                xw |= (a & 1u) << b;
-                zw |= (c & 1u) << b;
+        if (field == 2) {
+            const uint8_t* xs = gen + (size_t)r * 2 * n;
+            const uint8_t* zs = xs + n;
+            int i = 0;
+            for (; i + 8 <= n; i += 8) {
+                uint64_t a, c;
+                memcpy(&a, xs + i, 8);
+                memcpy(&c, zs + i, 8);
+                bad |= (a | c) & ~0x0101010101010101ull;
+                v.x[i >> 5] |= pack8(a) << (i & 31);
+                v.z[i >> 5] |= pack8(c) << (i & 31);
             }
-            v.x[w] = xw;
-            v.z[w] = zw;
+            for (; i < n; i++) {
+                bad |= (xs[i] | zs[i]) & ~1u;
+                v.x[i >> 5] |= (uint32_t)(xs[i] & 1u) << (i & 31);
+                v.z[i >> 5] |= (uint32_t)(zs[i] & 1u) << (i & 31);
+            }
+        } else {
+            const uint8_t* s4 = gen + (size_t)r * n;
+            for (int i = 0; i < n; i++) {
+                bad |= s4[i] & ~3u;
+                v.x[i >> 5] |= (uint32_t)(s4[i] & 1u) << (i & 31);
+                v.z[i >> 5] |= (uint32_t)((s4[i] >> 1) & 1u) << (i & 31);
+            }
         }
     }
     return bad ? P_EINVAL : P_OK;
@@ -220,41 +228,6 @@ static void reduce_rank(Plan* p) {
 // Rows left without a pivot are free.  A later pivot only adds rows whose
 // projection on earlier pivot qubits is already 0, so earlier packages keep
 // their property.
-// Set of rows (bit i = row i), k <= DIST_MAXK.
-struct RowSet {
-    uint64_t w[(DIST_MAXK + 63) / 64];
-};
-static inline void rs_set(RowSet& s, int i) { s.w[i >> 6] |= 1ull << (i & 63); }
-static inline void rs_clear(RowSet& s, int i) { s.w[i >> 6] &= ~(1ull << (i & 63)); }
-static inline int rs_first(const RowSet& s) {  // lowest row, -1 if empty
-    for (int t = 0; t < (int)(sizeof s.w / 8); t++)
-        if (s.w[t]) return t * 64 + __builtin_ctzll(s.w[t]);
-    return -1;
-}
-static inline RowSet rs_and(const RowSet& a, const RowSet& b) {
-    RowSet r;
-    for (int t = 0; t < (int)(sizeof r.w / 8); t++) r.w[t] = a.w[t] & b.w[t];
-    return r;
-}
-static inline RowSet rs_andnot(const RowSet& a, const RowSet& b) {
-    RowSet r;
-    for (int t = 0; t < (int)(sizeof r.w / 8); t++) r.w[t] = a.w[t] & ~b.w[t];
-    return r;
-}
-static inline RowSet rs_or(const RowSet& a, const RowSet& b) {
-    RowSet r;
-    for (int t = 0; t < (int)(sizeof r.w / 8); t++) r.w[t] = a.w[t] | b.w[t];
-    return r;
-}
-static inline void rs_xor_into(RowSet& a, const RowSet& b) {
-    for (int t = 0; t < (int)(sizeof a.w / 8); t++) a.w[t] ^= b.w[t];
-}
-static inline bool rs_any(const RowSet& a) {
-    uint64_t o = 0;
-    for (int t = 0; t < (int)(sizeof a.w / 8); t++) o |= a.w[t];
-    return o != 0;
-}
-
 static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<char>& used, Gamma& G) {
     const int k = p.k_eff, n = p.n;
     std::vector<Vec> R = p.basis;
@@ -263,49 +236,35 @@ static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<c
         memset(&C[i], 0, sizeof(Coef));
         setb(C[i].p[0], i);
     }
-    // Column view of R: cx[q] (cz[q]) = rows with a 1 in the x (z) plane at
-    // qubit q, kept in step with the rows.  The projection of row i onto q is
-    // (i in cx[q]) + 2 (i in cz[q]).
-    std::vector<RowSet> cx(n), cz(n);
-    memset(cx.data(), 0, n * sizeof(RowSet));
-    memset(cz.data(), 0, n * sizeof(RowSet));
-    for (int i = 0; i < k; i++)
-        for (int w = 0; w < p.W; w++) {
-            for (uint32_t m = R[i].x[w]; m; m &= m - 1) rs_set(cx[w * 32 + __builtin_ctz(m)], i);
-            for (uint32_t m = R[i].z[w]; m; m &= m - 1) rs_set(cz[w * 32 + __builtin_ctz(m)], i);
-        }
-    RowSet unpiv;
-    memset(&unpiv, 0, sizeof unpiv);
-    for (int i = 0; i < k; i++) rs_set(unpiv, i);
-    // rows with projection val (1, 2, 3) at q
-    auto with_proj = [&](int q, int val) {
-        return val == 1 ? rs_andnot(cx[q], cz[q]) : val == 2 ? rs_andnot(cz[q], cx[q]) : rs_and(cx[q], cz[q]);
+    // R[i] += R[g] and C[i] += C[g] (F2 coefficients: plane 0 only)
+    auto add_row = [&](int i, const Vec& v, const Coef& c) {  // fixed widths: vectorized
+        vxor(R[i], v);
+        for (int w = 0; w < DIST_MAXCW; w++) C[i].p[0][w] ^= c.p[0][w];
     };
-    // R[i] += R[g] (and the coefficients: plane 0 only, F2 coefficients)
-    // for every row i in S; g not in S
-    auto add_row = [&](const RowSet& S, int g) {
-        for (int t = 0; t < (int)(sizeof S.w / 8); t++)
-            for (uint64_t m = S.w[t]; m; m &= m - 1) {
-                const int i = t * 64 + __builtin_ctzll(m);
-                vxor(R[i], R[g]);
-                for (int w = 0; w < DIST_MAXCW; w++) C[i].p[0][w] ^= C[g].p[0][w];
-            }
-        for (int w = 0; w < p.W; w++) {
-            for (uint32_t m = R[g].x[w]; m; m &= m - 1) rs_xor_into(cx[w * 32 + __builtin_ctz(m)], S);
-            for (uint32_t m = R[g].z[w]; m; m &= m - 1) rs_xor_into(cz[w * 32 + __builtin_ctz(m)], S);
-        }
-    };
+    // unpivoted rows in increasing order
+    std::vector<int> live(k);
+    for (int i = 0; i < k; i++) live[i] = i;
     std::vector<char> piv(k, 0);
+    std::vector<int> lg(k), lh(k), lgh(k);  // rows that take g, h, g+h at the current pivot
     struct U { int kind, q, g, h; };
     std::vector<U> units;
+    units.reserve(k);
     for (;;) {
+        // rank of the unpivoted rows' projections at q: how many distinct
+        // nonzero values they take, 2 for two or three
         int best_q = -1, best_rank = 0;
         for (int t = 0; t < n; t++) {
             const int q = qorder[t];
             if (used[q]) continue;
-            const RowSet a = rs_and(cx[q], unpiv), b = rs_and(cz[q], unpiv);
-            const int nz = (int)rs_any(rs_andnot(a, b)) + (int)rs_any(rs_andnot(b, a)) + (int)rs_any(rs_and(a, b));
-            const int rank = nz >= 2 ? 2 : nz;
+            unsigned seen = 0;
+            int rank = 0;
+            for (int i : live) {
+                const int v = proj(R[i], q);
+                if (v && !(seen & (1u << v))) {
+                    seen |= 1u << v;
+                    if (++rank == 2) break;
+                }
+            }
             if (rank > best_rank) {
                 best_rank = rank;
                 best_q = q;
@@ -314,33 +273,60 @@ static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<c
         }
         if (best_rank == 0) break;
         const int q = best_q;
-        const RowSet live = rs_and(rs_or(cx[q], cz[q]), unpiv);  // unpivoted rows, nonzero at q
-        const int g = rs_first(live);
+        int g = -1, h = -1;
+        for (int i : live)
+            if (proj(R[i], q)) {
+                g = i;
+                break;
+            }
         const int vg = proj(R[g], q);
         if (best_rank == 2) {
-            const int h = rs_first(rs_andnot(live, with_proj(q, vg)));
+            for (int i : live) {
+                const int v = proj(R[i], q);
+                if (v && v != vg) {
+                    h = i;
+                    break;
+                }
+            }
             const int vh = proj(R[h], q);
-            // rows with projection vg or vg+vh take g, rows with vh or vg+vh take h
-            const RowSet pg = with_proj(q, vg), ph = with_proj(q, vh), pgh = with_proj(q, vg ^ vh);
-            RowSet Sg = rs_or(pg, pgh), Sh = rs_or(ph, pgh);
-            rs_clear(Sg, g); rs_clear(Sg, h);
-            rs_clear(Sh, g); rs_clear(Sh, h);
-            add_row(Sg, g);
-            add_row(Sh, h);
+            // rows with projection vg take g, vh take h, vg+vh take g+h (R[g]
+            // and R[h] are not changed, so the order is free)
+            int ng = 0, nh = 0, ngh = 0;
+            for (int i = 0; i < k; i++) {  // branch-free lists
+                const int v = proj(R[i], q), other = (i != g) & (i != h);
+                lg[ng] = i;
+                ng += other & (v == vg);
+                lh[nh] = i;
+                nh += other & (v == vh);
+                lgh[ngh] = i;
+                ngh += other & (v == (vg ^ vh));
+            }
+            for (int t = 0; t < ng; t++) add_row(lg[t], R[g], C[g]);
+            for (int t = 0; t < nh; t++) add_row(lh[t], R[h], C[h]);
+            if (ngh) {
+                Vec sv = R[g];
+                vxor(sv, R[h]);
+                Coef sc = C[g];
+                for (int w = 0; w < DIST_MAXCW; w++) sc.p[0][w] ^= C[h].p[0][w];
+                for (int t = 0; t < ngh; t++) add_row(lgh[t], sv, sc);
+            }
             piv[g] = piv[h] = 1;
-            rs_clear(unpiv, g);
-            rs_clear(unpiv, h);
             units.push_back({UNIT_PACKAGE2, q, g, h});
         } else {
             const int v = vg;
             const int w = (v == 1) ? 2 : 1;  // smallest nonzero value other than v
-            RowSet S = rs_or(with_proj(q, v), with_proj(q, v ^ w));
-            rs_clear(S, g);
-            add_row(S, g);
+            int ng = 0;
+            for (int i = 0; i < k; i++) {
+                const int c = proj(R[i], q);
+                lg[ng] = i;
+                ng += (i != g) & ((c == v) | (c == (v ^ w)));
+            }
+            for (int t = 0; t < ng; t++) add_row(lg[t], R[g], C[g]);
             piv[g] = 1;
-            rs_clear(unpiv, g);
             units.push_back({UNIT_PACKAGE1, q, g, -1});
         }
+        live.erase(std::find(live.begin(), live.end(), g));
+        if (h >= 0) live.erase(std::find(live.begin(), live.end(), h));
         used[q] = 1;
         G.pivots.push_back(q);
     }
@@ -388,6 +374,7 @@ static void diag_f4(const Plan& p, const std::vector<int>& qorder, std::vector<c
         setb(C[i].p[0], i);  // scalar 1 on basis row i
     }
     std::vector<char> piv(k, 0);
+    std::vector<int> lst(k);
     std::vector<std::pair<int, int>> order;  // (row, qubit)
     int npiv = 0;
     for (int t = 0; t < n && npiv < k; t++) {
@@ -400,13 +387,22 @@ static void diag_f4(const Plan& p, const std::vector<int>& qorder, std::vector<c
         int inv = f4_inv(proj(R[g], q));
         R[g] = vscale(R[g], inv);
         C[g] = cscale(C[g], inv);
-        for (int i = 0; i < k; i++) {
-            if (i == g) continue;
-            int c = proj(R[i], q);
-            if (c) {
-                vxor(R[i], vscale(R[g], c));
-                cxor(C[i], cscale(C[g], c));
-            }
+        // row i takes c R[g], c = its symbol at q (R[g] has symbol 1 there)
+        Vec sv[4];
+        Coef sc[4];
+        for (int c = 1; c < 4; c++) {
+            sv[c] = vscale(R[g], c);
+            sc[c] = cscale(C[g], c);
+        }
+        int nl = 0;
+        for (int i = 0; i < k; i++) {  // branch-free list of the rows to change
+            lst[nl] = i;
+            nl += (i != g) & (proj(R[i], q) != 0);
+        }
+        for (int t = 0; t < nl; t++) {
+            const int i = lst[t], c = proj(R[i], q);
+            vxor(R[i], sv[c]);
+            cxor(C[i], sc[c]);
         }
         piv[g] = 1;
         npiv++;
@@ -461,14 +457,48 @@ static void build_device_tables(const Plan& p, Gamma& G) {
     }
     G.dev_r0.assign(G.A.size() * 6, 0);
     G.dev_r1.assign(G.A.size() * 6, 0);
+    // The qubit permutation as nibble tables: entry (N, v) is the 128-bit
+    // image of value v in nibble N of a plane, so a plane maps with one lookup
+    // per nibble.
+    const int nnib = (p.n + 3) / 4;
+    std::vector<uint64_t> img((size_t)nnib * 32);
+    for (int N = 0; N < nnib; N++) {
+        uint64_t* T = &img[(size_t)N * 32];
+        T[0] = T[1] = 0;
+        for (int v = 1; v < 16; v++) {
+            const int q = N * 4 + __builtin_ctz((unsigned)v), prev = v & (v - 1);
+            uint64_t lo = 0, hi = 0;
+            if (q < p.n) {
+                const int d = pos_of[q];
+                if (d < 64) lo = 1ull << d;
+                else hi = 1ull << (d - 64);
+            }
+            T[2 * v] = T[2 * prev] | lo;
+            T[2 * v + 1] = T[2 * prev + 1] | hi;
+        }
+    }
+    auto permute = [&](const uint32_t* src, uint32_t* dst) {
+        uint64_t lo = 0, hi = 0;
+        for (int N = 0; N < nnib; N++) {
+            const unsigned v = (src[N >> 3] >> ((N & 7) * 4)) & 0xFu;
+            lo |= img[((size_t)N * 16 + v) * 2];
+            hi |= img[((size_t)N * 16 + v) * 2 + 1];
+        }
+        for (int w = 0; w < W; w++) dst[w] = (uint32_t)((w < 2 ? lo : hi) >> ((w & 1) * 32));
+    };
     for (int t = 0; t < u; t++) {
         const Unit& x = t < (int)G.A.size() ? G.A[t] : G.B[t - G.A.size()];
         for (int e = 0; e < x.nrep; e++) {
             uint32_t* dx = &G.dev_reps[(((size_t)t * 3 + e) * 2 + 0) * W];
             uint32_t* dz = &G.dev_reps[(((size_t)t * 3 + e) * 2 + 1) * W];
-            for (int w = 0; w < W; w++) {
-                for (uint32_t m = x.rep[e].x[w]; m; m &= m - 1) setb(dx, pos_of[w * 32 + __builtin_ctz(m)]);
-                for (uint32_t m = x.rep[e].z[w]; m; m &= m - 1) setb(dz, pos_of[w * 32 + __builtin_ctz(m)]);
+            if (e == 2) {  // rep 2 = rep 0 + rep 1, and the permutation is linear
+                for (int w = 0; w < W; w++) {
+                    dx[w] = dx[w - 4 * W] ^ dx[w - 2 * W];
+                    dz[w] = dz[w - 4 * W] ^ dz[w - 2 * W];
+                }
+            } else {
+                permute(x.rep[e].x, dx);
+                permute(x.rep[e].z, dz);
             }
             for (int c = 0; c < 2; c++)
                 for (int w = 0; w < CW; w++)
@@ -575,12 +605,37 @@ static double choose_J(Plan* p) {
                      [&](int a, int b) { return p->gammas[a].f < p->gammas[b].f; });
     double best = INFINITY;
     std::vector<int> bestJ;
+    // Every prefix sums the same round counts: each (matrix, round) is
+    // computed once, as plan_round_count does, from tables of its binomials
+    // and powers of 3 (the same values, summed in the same order).
+    std::vector<std::vector<double>> cnt(p->gammas.size()), ca(p->gammas.size()), cb(p->gammas.size());
+    std::vector<double> p3;
+    auto count = [&](int g, int r) {
+        std::vector<double>& v = cnt[g];
+        while ((int)v.size() <= r) v.push_back(-1.0);
+        if (v[r] >= 0) return v[r];
+        const Gamma& G = p->gammas[g];
+        const int a = (int)G.A.size(), b = (int)G.B.size();
+        if (ca[g].empty()) {
+            for (int i = 0; i <= a; i++) ca[g].push_back(dbinom(a, i));
+            for (int i = 0; i <= b; i++) cb[g].push_back(dbinom(b, i));
+        }
+        while ((int)p3.size() <= r) p3.push_back(pow(3.0, (double)p3.size()));
+        double s = 0;
+        if (p->field == 4) {
+            s = r >= 1 ? (r <= a ? ca[g][r] : 0.0) * p3[r - 1] : 0.0;
+        } else {
+            for (int i = std::max(0, r - b); i <= std::min(r, a); i++) s += ca[g][i] * p3[i] * cb[g][r - i];
+        }
+        v[r] = s;
+        return s;
+    };
     for (size_t m = 1; m <= cand.size(); m++) {
         std::vector<int> J(cand.begin(), cand.begin() + m);
         double work = 0;
         for (int r = 1; r <= DIST_MAXU; r++) {
             for (size_t t = 0; t < J.size(); t++) {
-                work += plan_round_count(*p, J[t], r);
+                work += count(J[t], r);
                 if (bound_for(*p, J, r, (int)t) >= p->d_est) goto done;
             }
         }
@@ -623,16 +678,37 @@ static void slot_codeword(const Plan& p, const WitnessSlot& s, Vec* v, Coef* k) 
     *k = x.coef[s.digit[0]];
 }
 
-// S2 with the unused qubits considered in qorder, then the seed U, d_est and
-// J (no device tables yet).  A known codeword lighter than every
+// S2 with the unused qubits considered in qorder, then the seed U, d_est
+// (d_random capped by the seed) and J (no device tables yet).  A known codeword lighter than every
 // representative of this diagonalization becomes the seed.  *work = the
 // estimated codewords to lift the bound to d_est.
-static int diagonalize(Plan* p, const std::vector<int>& qorder, double* work, int known_w = DIST_WINF,
-                       const Vec* known_v = nullptr, const Coef* known_k = nullptr) {
+// Expected number of nonzero codewords of weight <= w in a random code of
+// the same size: 2^(K2 - 2n) * sum_v C(n, v) 3^v.  The estimate of d is the
+// first w where it reaches 1 (n if none).
+static int random_code_d(const Plan& p) {
+    const int n = p.n, K2 = p.field == 2 ? p.k_eff : 2 * p.k_eff;
+    double acc = 0;
+    for (int w = 1; w <= n; w++) {
+        acc += dbinom(n, w) * pow(3.0, w);
+        if (log2(acc) + K2 - 2.0 * n >= 0) return w;
+    }
+    return n;
+}
+
+static int diagonalize(Plan* p, const std::vector<int>& qorder, int d_random, double* work,
+                       int known_w = DIST_WINF, const Vec* known_v = nullptr, const Coef* known_k = nullptr) {
     const int n = p->n, field = p->field;
     p->gammas.clear();
     std::vector<char> used(n, 0);
+    // qubits where some basis row is nonzero: a matrix needs an unused one
+    Vec support;
+    memset(&support, 0, sizeof support);
+    for (const Vec& b : p->basis)
+        for (int w = 0; w < p->W; w++) support.x[w] |= b.x[w] | b.z[w];
     for (int j = 0; j < DIST_MAXGAMMA; j++) {
+        bool open = false;
+        for (int q = 0; q < n && !open; q++) open = !used[q] && bit(support.x, q);
+        if (!open) break;
         Gamma G;
         std::vector<char> u2 = used;
         if (field == 2) diag_f2(*p, qorder, u2, G);
@@ -655,20 +731,7 @@ static int diagonalize(Plan* p, const std::vector<int>& qorder, double* work, in
         p->seed_vec = *known_v;
         p->seed_coef = *known_k;
     }
-    // Expected number of nonzero codewords of weight <= w in a random code of
-    // the same size: 2^(K2 - 2n) * sum_v C(n, v) 3^v.  d_est = first w where it
-    // reaches 1, capped by the lightest known codeword.
-    const int K2 = field == 2 ? p->k_eff : 2 * p->k_eff;
-    double acc = 0;
-    p->d_est = n;
-    for (int w = 1; w <= n; w++) {
-        acc += dbinom(n, w) * pow(3.0, w);
-        if (log2(acc) + K2 - 2.0 * n >= 0) {
-            p->d_est = w;
-            break;
-        }
-    }
-    p->d_est = std::max(1, std::min(p->d_est, p->u0));
+    p->d_est = std::max(1, std::min(d_random, p->u0));
     *work = choose_J(p);
     return P_OK;
 }
@@ -698,7 +761,8 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
     std::vector<int> qorder(n);
     for (int q = 0; q < n; q++) qorder[q] = q;
     double work = 0;
-    rc = diagonalize(p, qorder, &work);
+    const int d_random = random_code_d(*p);
+    rc = diagonalize(p, qorder, d_random, &work);
     if (rc) return rc;
     const int trials = plan_search_trials();
     if (trials > 0 && work > kSearchWork && free_rows_in_J(*p)) {
@@ -727,7 +791,7 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
             alt.kept = p->kept;
             alt.basis = p->basis;
             double w2 = 0;
-            if (diagonalize(&alt, qorder, &w2, kw, &kv, &kk) != P_OK) continue;
+            if (diagonalize(&alt, qorder, d_random, &w2, kw, &kv, &kk) != P_OK) continue;
             if (alt.u0 < kw) {  // a lighter representative: the new best seed
                 kw = alt.u0;
                 slot_codeword(alt, alt.u0_slot, &kv, &kk);

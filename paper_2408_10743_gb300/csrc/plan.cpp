@@ -236,8 +236,9 @@ static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<c
         memset(&C[i], 0, sizeof(Coef));
         setb(C[i].p[0], i);
     }
-    // R[i] += R[g] and C[i] += C[g] (F2 coefficients: plane 0 only)
-    auto add_row = [&](int i, const Vec& v, const Coef& c) {  // fixed widths: vectorized
+    // R[i] += v and C[i] += c (F2 coefficients: plane 0 only), at fixed
+    // widths, which the compiler vectorizes
+    auto add_row = [&](int i, const Vec& v, const Coef& c) {
         vxor(R[i], v);
         for (int w = 0; w < DIST_MAXCW; w++) C[i].p[0][w] ^= c.p[0][w];
     };

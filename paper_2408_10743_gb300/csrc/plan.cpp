@@ -213,6 +213,50 @@ static void reduce_rank(Plan* p) {
 // S2: package diagonalization.
 // ---------------------------------------------------------------------------
 
+// Set of rows (bit i = row i) in NW 64-bit words.
+template <int NW>
+struct RowSet {
+    uint64_t w[NW];
+};
+template <int NW>
+static inline void rs_set(RowSet<NW>& s, int i) { s.w[i >> 6] |= 1ull << (i & 63); }
+template <int NW>
+static inline void rs_clear(RowSet<NW>& s, int i) { s.w[i >> 6] &= ~(1ull << (i & 63)); }
+template <int NW>
+static inline int rs_first(const RowSet<NW>& s) {  // lowest row, -1 if empty
+    for (int t = 0; t < NW; t++)
+        if (s.w[t]) return t * 64 + __builtin_ctzll(s.w[t]);
+    return -1;
+}
+template <int NW>
+static inline RowSet<NW> rs_and(const RowSet<NW>& a, const RowSet<NW>& b) {
+    RowSet<NW> r;
+    for (int t = 0; t < NW; t++) r.w[t] = a.w[t] & b.w[t];
+    return r;
+}
+template <int NW>
+static inline RowSet<NW> rs_andnot(const RowSet<NW>& a, const RowSet<NW>& b) {
+    RowSet<NW> r;
+    for (int t = 0; t < NW; t++) r.w[t] = a.w[t] & ~b.w[t];
+    return r;
+}
+template <int NW>
+static inline RowSet<NW> rs_or(const RowSet<NW>& a, const RowSet<NW>& b) {
+    RowSet<NW> r;
+    for (int t = 0; t < NW; t++) r.w[t] = a.w[t] | b.w[t];
+    return r;
+}
+template <int NW>
+static inline void rs_xor_into(RowSet<NW>& a, const RowSet<NW>& b) {
+    for (int t = 0; t < NW; t++) a.w[t] ^= b.w[t];
+}
+template <int NW>
+static inline bool rs_any(const RowSet<NW>& a) {
+    uint64_t o = 0;
+    for (int t = 0; t < NW; t++) o |= a.w[t];
+    return o != 0;
+}
+
 // F2 (Sections 2.2-2.3 in F2 language).  Works on the qubits not used by an
 // earlier matrix.  At each step it takes the unused qubit whose projections,
 // over the rows not pivoted yet, span the most (rank 2 first, then rank 1,
@@ -228,7 +272,9 @@ static void reduce_rank(Plan* p) {
 // Rows left without a pivot are free.  A later pivot only adds rows whose
 // projection on earlier pivot qubits is already 0, so earlier packages keep
 // their property.
-static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<char>& used, Gamma& G) {
+// NW = words of a row set (k <= 64 NW).
+template <int NW>
+static void diag_f2_t(const Plan& p, const std::vector<int>& qorder, std::vector<char>& used, Gamma& G) {
     const int k = p.k_eff, n = p.n;
     std::vector<Vec> R = p.basis;
     std::vector<Coef> C(k);
@@ -236,36 +282,57 @@ static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<c
         memset(&C[i], 0, sizeof(Coef));
         setb(C[i].p[0], i);
     }
-    // R[i] += v and C[i] += c (F2 coefficients: plane 0 only), at fixed
-    // widths, which the compiler vectorizes
-    auto add_row = [&](int i, const Vec& v, const Coef& c) {
-        vxor(R[i], v);
-        for (int w = 0; w < DIST_MAXCW; w++) C[i].p[0][w] ^= c.p[0][w];
+    // Column view of R on the unused qubits: cx[q] (cz[q]) = rows with a 1 in
+    // the x (z) plane at qubit q.  The projection of row i onto q is
+    // (i in cx[q]) + 2 (i in cz[q]).  A qubit's column is not read once the
+    // qubit is used, so only the unused ones are kept in step with the rows.
+    uint32_t openq[DIST_MAXW] = {0};
+    for (int q = 0; q < n; q++)
+        if (!used[q]) setb(openq, q);
+    std::vector<RowSet<NW>> cx(n), cz(n);
+    memset(cx.data(), 0, n * sizeof(RowSet<NW>));
+    memset(cz.data(), 0, n * sizeof(RowSet<NW>));
+    for (int i = 0; i < k; i++)
+        for (int w = 0; w < p.W; w++) {
+            for (uint32_t m = R[i].x[w] & openq[w]; m; m &= m - 1) rs_set(cx[w * 32 + __builtin_ctz(m)], i);
+            for (uint32_t m = R[i].z[w] & openq[w]; m; m &= m - 1) rs_set(cz[w * 32 + __builtin_ctz(m)], i);
+        }
+    RowSet<NW> unpiv;
+    memset(&unpiv, 0, sizeof unpiv);
+    for (int i = 0; i < k; i++) rs_set(unpiv, i);
+    // rows with projection val (1, 2, 3) at q
+    auto with_proj = [&](int q, int val) {
+        return val == 1 ? rs_andnot(cx[q], cz[q]) : val == 2 ? rs_andnot(cz[q], cx[q]) : rs_and(cx[q], cz[q]);
     };
-    // unpivoted rows in increasing order
-    std::vector<int> live(k);
-    for (int i = 0; i < k; i++) live[i] = i;
+    // R[i] += v and C[i] += c (F2 coefficients: plane 0 only) for every row i
+    // in S, at fixed widths, which the compiler vectorizes
+    auto add_rows = [&](const RowSet<NW>& S, const Vec& v, const Coef& c) {
+        for (int t = 0; t < NW; t++)
+            for (uint64_t m = S.w[t]; m; m &= m - 1) {
+                const int i = t * 64 + __builtin_ctzll(m);
+                vxor(R[i], v);
+                for (int w = 0; w < DIST_MAXCW; w++) C[i].p[0][w] ^= c.p[0][w];
+            }
+    };
+    // the open columns after the rows of S took v
+    auto add_cols = [&](const RowSet<NW>& S, const Vec& v) {
+        for (int w = 0; w < p.W; w++) {
+            for (uint32_t m = v.x[w] & openq[w]; m; m &= m - 1) rs_xor_into(cx[w * 32 + __builtin_ctz(m)], S);
+            for (uint32_t m = v.z[w] & openq[w]; m; m &= m - 1) rs_xor_into(cz[w * 32 + __builtin_ctz(m)], S);
+        }
+    };
     std::vector<char> piv(k, 0);
-    std::vector<int> lg(k), lh(k), lgh(k);  // rows that take g, h, g+h at the current pivot
     struct U { int kind, q, g, h; };
     std::vector<U> units;
     units.reserve(k);
     for (;;) {
-        // rank of the unpivoted rows' projections at q: how many distinct
-        // nonzero values they take, 2 for two or three
         int best_q = -1, best_rank = 0;
         for (int t = 0; t < n; t++) {
             const int q = qorder[t];
             if (used[q]) continue;
-            unsigned seen = 0;
-            int rank = 0;
-            for (int i : live) {
-                const int v = proj(R[i], q);
-                if (v && !(seen & (1u << v))) {
-                    seen |= 1u << v;
-                    if (++rank == 2) break;
-                }
-            }
+            const RowSet<NW> a = rs_and(cx[q], unpiv), b = rs_and(cz[q], unpiv);
+            const int nz = (int)rs_any(rs_andnot(a, b)) + (int)rs_any(rs_andnot(b, a)) + (int)rs_any(rs_and(a, b));
+            const int rank = nz >= 2 ? 2 : nz;
             if (rank > best_rank) {
                 best_rank = rank;
                 best_q = q;
@@ -274,61 +341,44 @@ static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<c
         }
         if (best_rank == 0) break;
         const int q = best_q;
-        int g = -1, h = -1;
-        for (int i : live)
-            if (proj(R[i], q)) {
-                g = i;
-                break;
-            }
+        // q is used from here on: its column is no longer updated
+        used[q] = 1;
+        openq[q >> 5] &= ~(1u << (q & 31));
+        const RowSet<NW> live = rs_and(rs_or(cx[q], cz[q]), unpiv);  // unpivoted rows, nonzero at q
+        const int g = rs_first(live);
         const int vg = proj(R[g], q);
         if (best_rank == 2) {
-            for (int i : live) {
-                const int v = proj(R[i], q);
-                if (v && v != vg) {
-                    h = i;
-                    break;
-                }
-            }
+            const int h = rs_first(rs_andnot(live, with_proj(q, vg)));
             const int vh = proj(R[h], q);
-            // rows with projection vg take g, vh take h, vg+vh take g+h (R[g]
-            // and R[h] are not changed, so the order is free)
-            int ng = 0, nh = 0, ngh = 0;
-            for (int i = 0; i < k; i++) {  // branch-free lists
-                const int v = proj(R[i], q), other = (i != g) & (i != h);
-                lg[ng] = i;
-                ng += other & (v == vg);
-                lh[nh] = i;
-                nh += other & (v == vh);
-                lgh[ngh] = i;
-                ngh += other & (v == (vg ^ vh));
-            }
-            for (int t = 0; t < ng; t++) add_row(lg[t], R[g], C[g]);
-            for (int t = 0; t < nh; t++) add_row(lh[t], R[h], C[h]);
-            if (ngh) {
-                Vec sv = R[g];
-                vxor(sv, R[h]);
-                Coef sc = C[g];
-                for (int w = 0; w < DIST_MAXCW; w++) sc.p[0][w] ^= C[h].p[0][w];
-                for (int t = 0; t < ngh; t++) add_row(lgh[t], sv, sc);
-            }
+            // rows with projection vg take g, vh take h, vg+vh take g+h
+            RowSet<NW> Sg = with_proj(q, vg), Sh = with_proj(q, vh), Sgh = with_proj(q, vg ^ vh);
+            rs_clear(Sg, g); rs_clear(Sg, h);
+            rs_clear(Sh, g); rs_clear(Sh, h);
+            rs_clear(Sgh, g); rs_clear(Sgh, h);
+            add_cols(rs_or(Sg, Sgh), R[g]);
+            add_cols(rs_or(Sh, Sgh), R[h]);
+            Vec sv = R[g];
+            vxor(sv, R[h]);
+            Coef sc = C[g];
+            for (int w = 0; w < DIST_MAXCW; w++) sc.p[0][w] ^= C[h].p[0][w];
+            add_rows(Sg, R[g], C[g]);
+            add_rows(Sh, R[h], C[h]);
+            add_rows(Sgh, sv, sc);
             piv[g] = piv[h] = 1;
+            rs_clear(unpiv, g);
+            rs_clear(unpiv, h);
             units.push_back({UNIT_PACKAGE2, q, g, h});
         } else {
             const int v = vg;
             const int w = (v == 1) ? 2 : 1;  // smallest nonzero value other than v
-            int ng = 0;
-            for (int i = 0; i < k; i++) {
-                const int c = proj(R[i], q);
-                lg[ng] = i;
-                ng += (i != g) & ((c == v) | (c == (v ^ w)));
-            }
-            for (int t = 0; t < ng; t++) add_row(lg[t], R[g], C[g]);
+            RowSet<NW> S = rs_or(with_proj(q, v), with_proj(q, v ^ w));
+            rs_clear(S, g);
+            add_cols(S, R[g]);
+            add_rows(S, R[g], C[g]);
             piv[g] = 1;
+            rs_clear(unpiv, g);
             units.push_back({UNIT_PACKAGE1, q, g, -1});
         }
-        live.erase(std::find(live.begin(), live.end(), g));
-        if (h >= 0) live.erase(std::find(live.begin(), live.end(), h));
-        used[q] = 1;
         G.pivots.push_back(q);
     }
     for (int i = 0; i < k; i++)
@@ -360,6 +410,15 @@ static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<c
         if (u.kind == UNIT_FREE) G.f++;
         else G.npack++;
     }
+}
+
+// diag_f2_t with row sets just wide enough for the k_eff rows
+static void diag_f2(const Plan& p, const std::vector<int>& qorder, std::vector<char>& used, Gamma& G) {
+    const int nw = (p.k_eff + 63) / 64;
+    if (nw <= 1) diag_f2_t<1>(p, qorder, used, G);
+    else if (nw == 2) diag_f2_t<2>(p, qorder, used, G);
+    else if (nw == 3) diag_f2_t<3>(p, qorder, used, G);
+    else diag_f2_t<4>(p, qorder, used, G);
 }
 
 // F4-linear codes (Section 2.3): reduced echelon form over F4 on the unused

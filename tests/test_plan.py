@@ -47,9 +47,8 @@ def check_structure(g, field=2):
     used = set()
     for gm in gammas:
         reps_all = [r for u in gm["units"] for r in u["reps"]]
-        # every representative is a codeword
-        for r in reps_all:
-            assert f2_rank(np.vstack([G2, r])) == rank
+        # every representative is a codeword: together they add no rank
+        assert f2_rank(np.vstack([G2] + reps_all)) == rank
         # the units' independent representatives form a basis of the code
         basis = []
         for u in gm["units"]:
@@ -229,3 +228,25 @@ def test_launch_digest():
     assert prof["kernel_digest"] == bench.kernel_digest()
     with pytest.raises(dist.DistError):
         dist.dist_launch_digest(np.array([[2, 0]], dtype=np.uint8), target_warps=2432)
+
+
+@pytest.mark.parametrize("case", ["f2_full", "f2_iid", "f2_css", "f4"])
+def test_package_structure_max_sizes(case):
+    """The largest inputs the planner takes: n = 128 qubits (four words per
+    plane) and up to 256 rows (row sets of four words), dense, CSS-like and
+    F4-linear."""
+    rng = np.random.default_rng({"f2_full": 31, "f2_iid": 32, "f2_css": 33, "f4": 34}[case])
+    n = 128
+    if case == "f2_full":
+        g = rng.integers(0, 2, size=(256, 2 * n), dtype=np.uint8)
+    elif case == "f2_iid":
+        g = rng.integers(0, 2, size=(200, 2 * n), dtype=np.uint8)
+    elif case == "f2_css":
+        g = np.zeros((240, 2 * n), dtype=np.uint8)
+        for r in range(240):
+            off = 0 if r % 2 == 0 else n
+            g[r, off + rng.choice(n, size=6, replace=False)] = 1
+    else:
+        g = rng.integers(0, 4, size=(100, n), dtype=np.uint8)
+    info, _ = check_structure(g, field=4 if case == "f4" else 2)
+    assert info.k_eff == f2_rank(f2_image(g, 4 if case == "f4" else 2)) // (2 if case == "f4" else 1)

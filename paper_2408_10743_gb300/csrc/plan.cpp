@@ -666,8 +666,8 @@ static double choose_J(Plan* p) {
     double best = INFINITY;
     std::vector<int> bestJ;
     // Every prefix sums the same round counts: each (matrix, round) is
-    // computed once, as plan_round_count does, from tables of its binomials
-    // and powers of 3 (the same values, summed in the same order).
+    // computed once, as plan_round_count does, from binomials and powers of 3
+    // computed once each (the same values, summed in the same order).
     std::vector<std::vector<double>> cnt(p->gammas.size()), ca(p->gammas.size()), cb(p->gammas.size());
     std::vector<double> p3;
     auto count = [&](int g, int r) {
@@ -676,16 +676,18 @@ static double choose_J(Plan* p) {
         if (v[r] >= 0) return v[r];
         const Gamma& G = p->gammas[g];
         const int a = (int)G.A.size(), b = (int)G.B.size();
-        if (ca[g].empty()) {
-            for (int i = 0; i <= a; i++) ca[g].push_back(dbinom(a, i));
-            for (int i = 0; i <= b; i++) cb[g].push_back(dbinom(b, i));
-        }
+        auto binom = [](std::vector<double>& t, int m, int i) {  // C(m, i), i <= m
+            if (t.empty()) t.assign(m + 1, -1.0);
+            if (t[i] < 0) t[i] = dbinom(m, i);
+            return t[i];
+        };
         while ((int)p3.size() <= r) p3.push_back(pow(3.0, (double)p3.size()));
         double s = 0;
         if (p->field == 4) {
-            s = r >= 1 ? (r <= a ? ca[g][r] : 0.0) * p3[r - 1] : 0.0;
+            s = r >= 1 ? (r <= a ? binom(ca[g], a, r) : 0.0) * p3[r - 1] : 0.0;
         } else {
-            for (int i = std::max(0, r - b); i <= std::min(r, a); i++) s += ca[g][i] * p3[i] * cb[g][r - i];
+            for (int i = std::max(0, r - b); i <= std::min(r, a); i++)
+                s += binom(ca[g], a, i) * p3[i] * binom(cb[g], b, r - i);
         }
         v[r] = s;
         return s;

@@ -134,7 +134,8 @@ static unsigned long long upow3(int e) {
 // ---------------------------------------------------------------------------
 // Eight bytes, each 0 or 1, packed into eight bits (byte t -> bit t): the
 // multiplier moves byte t's low bit to bit 56 + t, and no two partial products
-// meet, so nothing carries.
+// meet, so nothing carries.  The bytes are loaded little-endian (byte t of
+// memory in bits 8t..8t+7), the order of both x86-64 and AArch64 Linux.
 static inline uint32_t pack8(uint64_t b) { return (uint32_t)(((b & 0x0101010101010101ull) * 0x0102040810204080ull) >> 56); }
 
 static int load_input(const uint8_t* gen, int n, int K, int field, Plan* p) {

@@ -106,10 +106,12 @@ struct NoAllocExec {
     Layout L;
     cudaStream_t st;
     unsigned long long nl = 0;
+    uint32_t U_host = DIST_WINF;  // the device's U as of the last copy or read-back
     Scratch* scr() const { return (Scratch*)(d->base + L.scr); }
     int reset() {
         if (cudaMemsetAsync(scr(), 0, sizeof(Scratch), st) != cudaSuccess) return DIST_ECUDA;
         if (cudaMemsetAsync(scr(), 0xFF, 2, st) != cudaSuccess) return DIST_ECUDA;  // U = 0xFFFF
+        U_host = DIST_WINF;
         return DIST_OK;
     }
     int seed(uint32_t U0, const WitnessSlot& s) {
@@ -117,6 +119,7 @@ struct NoAllocExec {
             cudaMemcpyAsync(&scr()->slot[U0], &s, sizeof s, cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return DIST_ECUDA;
+        U_host = U0;
         return DIST_OK;
     }
     int target_warps() const { return d->sms * d->blocks_per_sm * DIST_ENUM_WARPS; }
@@ -129,6 +132,9 @@ struct NoAllocExec {
         ep.segs = (const SegDesc*)(d->base + L.segs);
         ep.binom = (const unsigned long long*)(d->base + L.binom);
         ep.scr = scr();
+        // U already at the random-code estimate of d: certification work
+        // (the same first-wave rule as dist_solve)
+        ep.first_static = U_host <= (uint32_t)p.d_est ? 1 : 0;
         if (deadline_wall > 0) {
             double left = deadline_wall - wall_now();
             ep.budget_ns = left > 1e-3 ? (unsigned long long)(left * 1e9) : 1000000ull;
@@ -138,7 +144,7 @@ struct NoAllocExec {
         if (smem > d->smem_optin) return DIST_ERANGE;
         const int bps = enum_blocks_per_sm(smem);
         if (bps < 1) return DIST_ECUDA;
-        unsigned long long want = (lp.nchunks + 7) / 8;
+        unsigned long long want = (lp.nchunks + DIST_ENUM_WARPS - 1) / DIST_ENUM_WARPS;
         if (want < 1) want = 1;
         const unsigned long long cap = (unsigned long long)d->sms * (unsigned long long)bps;
         const int grid = (int)(want < cap ? want : cap);
@@ -155,6 +161,7 @@ struct NoAllocExec {
             cudaStreamSynchronize(st) != cudaSuccess)
             return DIST_ECUDA;
         out->U = (uint32_t)(hdr[0] & 0xFFFFFFFFu);
+        U_host = out->U;
         out->status = (uint32_t)(hdr[0] >> 32);
         out->codewords = hdr[2];
         return DIST_OK;

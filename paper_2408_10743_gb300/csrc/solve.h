@@ -18,6 +18,9 @@
 // steps before s are complete, every unseen codeword weighs at least
 // L_before(s) >= U, and d = U.  If no such s exists nothing was dropped and
 // the bound after the launch's last step holds; d = U once it reaches U.
+// A launch that ends on its time budget drops claimed chunks of any step, so
+// the argument does not apply to it: after such a launch only the bound
+// before its first step holds.
 #pragma once
 #include <string.h>
 #include <time.h>
@@ -124,6 +127,14 @@ int solve_loop(const Plan& p, Exec& ex, double time_limit_s, dist_result* out) {
         rc = ex.run(lp, deadline, &sr);
         if (rc) return rc;
         U = sr.U;
+        if (sr.status & 2u) {
+            // The kernel spent its time budget and dropped the chunks it had
+            // not run, in any step of the launch: only the bound that held
+            // before the launch is known to hold after it.
+            L = lp.step_L_before[0];
+            if (U == DIST_WINF || (int)U > L) status = DIST_EINCOMPLETE;
+            break;
+        }
         bool certified = false;
         for (size_t s = 0; s < lp.step_r.size(); s++) {
             if (U != DIST_WINF && (int)U <= lp.step_L_before[s]) {
@@ -134,11 +145,6 @@ int solve_loop(const Plan& p, Exec& ex, double time_limit_s, dist_result* out) {
             out->rounds = lp.step_r[s];  // last step known to be complete so far
         }
         if (certified) break;
-        if (sr.status & 2u) {  // the kernel spent its time budget
-            status = DIST_EINCOMPLETE;
-            L = lp.step_L_before[0];
-            break;
-        }
         L = plan_lower_bound(p, lp.step_r.back(), lp.step_jpos.back());
         if (L == (int)DIST_WINF) break;  // a matrix has been enumerated completely
         if (U != DIST_WINF && L >= (int)U) break;

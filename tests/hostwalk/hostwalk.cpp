@@ -45,6 +45,10 @@ struct HostExec {
     std::vector<unsigned long long> binom;
     int warps = 4;
     unsigned long long nlaunch = 0;
+    // > 0: a launch stops after this many chunks as if its time budget ran
+    // out (status bit 1, the rest of its chunks dropped), like the kernel's
+    // budget stop
+    long long stop_after = 0;
     HostExec(const Plan* pp) : p(pp), binom((DIST_MAXU + 1) * (DIST_MAXR + 1)) {
         binom_table(binom.data());
     }
@@ -87,6 +91,10 @@ struct HostExec {
         HostSink sink{&scr};
         nlaunch++;
         for (unsigned long long chunk = 0; chunk < lp.nchunks; chunk++) {
+            if (stop_after > 0 && chunk == (unsigned long long)stop_after) {
+                scr.status |= 2u;
+                break;
+            }
             int sgi = 0;
             while (sgi + 1 < (int)lp.segs.size() && lp.segs[sgi + 1].chunk_base <= chunk) ++sgi;
             const SegDesc& sg = lp.segs[sgi];
@@ -135,6 +143,19 @@ extern "C" int hw_solve(const uint8_t* gen, int n, int K, int field, int n_stab,
     }
     HostExec ex(&p);
     ex.warps = warps;
+    return solve_loop(p, ex, 0.0, out);
+}
+
+// solve_loop with launches that stop after stop_after chunks as the kernel
+// does when its time budget runs out.
+extern "C" int hw_solve_stop(const uint8_t* gen, int n, int K, int field, int warps, long long stop_after,
+                             dist_result* out) {
+    Plan p;
+    int rc = plan_build(gen, n, K, field, &p);
+    if (rc) return rc;
+    HostExec ex(&p);
+    ex.warps = warps;
+    ex.stop_after = stop_after;
     return solve_loop(p, ex, 0.0, out);
 }
 

@@ -209,12 +209,31 @@ def test_repeat_and_streams(stream):
 
 
 def test_bounded_solve(stream):
+    """Time-limited solves: a certified answer (status 0) is the unbounded
+    solve's d; an answer at the limit brackets it, lower <= d <= upper.  The
+    codes' first launches span several steps, and the short limits end them
+    part way, when the upper bound may already have fallen."""
     g = synth.random_f2_code(96, 60, synth.Xoshiro256ss(12))
     with dist.Code(g) as c:
         r = c.solve(stream=stream, time_limit_s=0.05)
     assert r["status"] in (0, dist.binding.DIST_EINCOMPLETE)
     assert 1 <= r["lower"] <= r["d"]
     check_witness(g, r)
+    early = 0
+    for t, (n, K) in enumerate(((64, 56), (72, 72), (60, 44))):
+        g = synth.random_f2_code(n, K, synth.Xoshiro256ss(7700 + t))
+        with dist.Code(g) as c:
+            d_ref = c.solve(stream=stream)["d"]
+            for limit in (1e-4, 1e-3, 2e-3, 4e-3, 8e-3, 2e-2):
+                r = c.solve(stream=stream, time_limit_s=limit)
+                assert r["status"] in (0, dist.binding.DIST_EINCOMPLETE), (n, K, limit)
+                if r["status"] == 0:
+                    assert r["d"] == d_ref, (n, K, limit, r["d"], d_ref)
+                else:
+                    early += 1
+                    assert r["lower"] <= d_ref <= r["d"], (n, K, limit)
+                check_witness(g, r)
+    assert early > 0
 
 
 def test_tuning_changes_speed_not_results(stream):

@@ -61,6 +61,9 @@ def hw():
     L.hw_seed_decode.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
                                  ctypes.POINTER(ctypes.c_uint8)]
+    L.hw_solve_stop.restype = ctypes.c_int
+    L.hw_solve_stop.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(DistResult)]
     L.hw_solve_sliced.restype = ctypes.c_int
     L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -513,3 +516,34 @@ def test_ten_thousand_tiny_codes(hw):
         d, _, _ = oracle.bruteforce(g, threads=1)
         assert r.d == d, (g.tolist(), r.d, d)
         done += 1
+
+
+def test_budget_stop_never_certifies_a_wrong_d(hw):
+    """A launch that stops on its time budget drops the chunks it had not yet
+    run, in any step.  The round loop may then certify d only from the bound
+    that held before the launch; otherwise it answers with bounds
+    lower <= d <= upper (DIST_EINCOMPLETE).  Swept over stopping points of
+    random codes, many of whose upper bound falls during the first launch
+    (a certification from a later step's bound would then be wrong)."""
+    from paper_2408_10743_gb300.binding import DIST_EINCOMPLETE
+    early = certified = 0
+    for t in range(40):
+        rng = synth.Xoshiro256ss(5000 + t)
+        n = 12 + rng.below(30)
+        K = (n + 1) // 2 + rng.below(n // 2 + 1)
+        g = synth.random_f2_code(n, K, rng)
+        d_true = oracle.bz(g)["d"]
+        ptr = g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        for warps in (1, 8):
+            for stop in list(range(1, 24)) + [40, 120, 400]:
+                r = DistResult()
+                rc = hw.hw_solve_stop(ptr, n, K, 2, warps, stop, ctypes.byref(r))
+                assert rc in (0, DIST_EINCOMPLETE), (n, K, warps, stop, rc)
+                if rc == 0:
+                    certified += 1
+                    assert r.d == d_true, (n, K, warps, stop, r.d, d_true)
+                    check_witness(g, r)
+                else:
+                    early += 1
+                    assert r.lower <= d_true <= r.d, (n, K, warps, stop, r.lower, r.d, d_true)
+    assert early > 0 and certified > 0

@@ -55,3 +55,48 @@ def test_noalloc_rejects_codes_beyond_the_array():
     with pytest.raises(dist.DistError) as e:
         dist.dist_solve_noalloc(full)
     assert e.value.code == DIST_ERANGE
+
+
+_PROBE = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import torch
+import paper_2408_10743_gb300 as dist
+from paper_2408_10743_gb300 import synth
+torch.cuda.set_device(0)
+gens = [synth.single_f2(0), synth.single_f2(1), synth.random_f2_code(48, 40, synth.Xoshiro256ss(31))]
+# first call of the process: the library's device set-up (module load, the
+# array's address), before any allocating entry point has run
+ds = [dist.dist_solve_noalloc(gens[0]).d]
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+for g in gens * 2:
+    ds.append(dist.dist_solve_noalloc(g).d)
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+# the allocating entry points, for contrast: their device blocks are visible
+with dist.Code(gens[0]) as c:
+    ds.append(c.solve()["d"])
+torch.cuda.synchronize()
+free2 = torch.cuda.mem_get_info()[0]
+print(json.dumps({"free0": free0, "free1": free1, "free2": free2, "d": ds}))
+"""
+
+
+def test_noalloc_allocates_no_device_memory():
+    """In a fresh process, repeated no-allocation solves leave the device's
+    free memory unchanged; a solve through dist_init + dist_solve afterwards
+    takes some, which shows that the measurement sees allocations."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _PROBE, root], capture_output=True, text=True,
+                         timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    assert rec["free1"] == rec["free0"], rec
+    assert rec["free2"] < rec["free1"], rec
+    d = rec["d"]
+    assert d[1:4] == d[4:7] and d[0] == d[1] == d[-1], d

@@ -225,6 +225,17 @@ int dist_autotune_codes(dist_code *const *codes, int count, double budget_s, dis
  */
 int dist_set_plan_search(int trials);
 int dist_get_plan_search(void);
+/*
+ * Matrix-inclusion limit of the planner (process-wide; Section 2.3, the
+ * second generator matrix and its bound term): dist_init enumerates at most
+ * `m` of the generator matrices it builds on disjoint qubit sets, the prefix
+ * (by free rows) with the least estimated work (0 = no limit, the default;
+ * 1 = the first matrix only, as a one-matrix Brouwer-Zimmermann does).
+ * Affects speed, never results.  DIST_EINVAL for m < 0; values above 16 act
+ * as 16.
+ */
+int dist_set_gamma_limit(int m);
+int dist_get_gamma_limit(void);
 
 /*
  * dist_plan_info -- host-only view of the plan step S2-S3 built for an input

@@ -112,6 +112,8 @@ SIGNATURES = {
     "dist_autotune": (ctypes.c_int, [ctypes.POINTER(Tuning), ctypes.c_double]),
     "dist_set_plan_search": (ctypes.c_int, [ctypes.c_int]),
     "dist_get_plan_search": (ctypes.c_int, []),
+    "dist_set_gamma_limit": (ctypes.c_int, [ctypes.c_int]),
+    "dist_get_gamma_limit": (ctypes.c_int, []),
     "dist_autotune_codes": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_double,
                                            ctypes.POINTER(Tuning)]),
     "dist_version": (ctypes.c_char_p, []),
@@ -341,6 +343,14 @@ def dist_set_plan_search(trials):
 
 def dist_get_plan_search() -> int:
     return lib().dist_get_plan_search()
+
+
+def dist_set_gamma_limit(m):
+    return _check(lib().dist_set_gamma_limit(int(m)), "dist_set_gamma_limit")
+
+
+def dist_get_gamma_limit() -> int:
+    return lib().dist_get_gamma_limit()
 
 
 def dist_get_tuning() -> dict:

@@ -481,6 +481,14 @@ int dist_set_plan_search(int trials) {
 
 int dist_get_plan_search(void) { return plan_search_trials(); }
 
+int dist_set_gamma_limit(int m) {
+    if (m < 0) return DIST_EINVAL;
+    plan_set_gamma_limit(m);
+    return DIST_OK;
+}
+
+int dist_get_gamma_limit(void) { return plan_gamma_limit(); }
+
 int dist_get_tuning(dist_tuning* t) {
     if (!t) return DIST_EINVAL;
     const Tuning cur = tuning_get();

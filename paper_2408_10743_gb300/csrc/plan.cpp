@@ -656,6 +656,10 @@ int plan_lower_bound(const Plan& p, int r, int jpos) { return bound_for(p, p.J, 
 
 int plan_initial_bound(const Plan& p) { return std::max(1, bound_for(p, p.J, 0, (int)p.J.size())); }
 
+static std::atomic<int> g_gamma_limit{0};
+int plan_gamma_limit() { return g_gamma_limit.load(); }
+void plan_set_gamma_limit(int m) { g_gamma_limit.store(std::max(0, std::min(m, DIST_MAXGAMMA))); }
+
 // Choice of J: among the matrices sorted by free rows, the prefix whose
 // estimated work to lift the bound to d_est is smallest.  Any nonempty J is
 // correct; this only decides speed.
@@ -693,7 +697,9 @@ static double choose_J(Plan* p) {
         v[r] = s;
         return s;
     };
-    for (size_t m = 1; m <= cand.size(); m++) {
+    const int limit = plan_gamma_limit();
+    const size_t mmax = limit > 0 ? std::min(cand.size(), (size_t)limit) : cand.size();
+    for (size_t m = 1; m <= mmax; m++) {
         std::vector<int> J(cand.begin(), cand.begin() + m);
         double work = 0;
         for (int r = 1; r <= DIST_MAXU; r++) {

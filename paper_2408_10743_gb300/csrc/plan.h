@@ -109,6 +109,10 @@ Tuning tuning_get();
 // only; default 8, range 0..256; process-wide).
 int plan_search_trials();
 void plan_set_search_trials(int t);
+// Largest number of generator matrices the choice of J may take (0: no
+// limit beyond the policy's own choice).
+int plan_gamma_limit();
+void plan_set_gamma_limit(int m);
 void tuning_set(const Tuning& t);
 
 // S1 + S2 + choice of J.  gen layout: field 2 -> K x 2n bytes {0,1} (x | z);

@@ -22,6 +22,8 @@ covering the K/N range of its random normalizer matrices, Section 3):
   random positions; resampled until rank 72.
 * ``batch_codes``      -- many random F2 codes, n ~ U[16,56], K ~ U[ceil(n/2), n].
 * ``request_stream``   -- Poisson arrivals of random F2 and quasi-cyclic requests.
+* ``small_k_code``     -- normalizer matrices of random stabilizer codes with
+  few logical qubits (n + k rows, stabilizers first), K/N about 0.54.
 
 Layouts match the library: F2 -> uint8 (K, 2n) bits x_0..x_{n-1} | z_0..z_{n-1};
 F4 -> uint8 (k, n) symbols v = a + 2b standing for a + alpha*b.
@@ -148,8 +150,12 @@ def f4_systematic(n: int, k: int, rng: Xoshiro256ss) -> np.ndarray:
 
 
 def circulant(first_row: np.ndarray) -> np.ndarray:
-    b = len(first_row)
-    return np.stack([np.roll(first_row, i) for i in range(b)]).astype(np.uint8)
+    """b x b circulant whose row i is the first row shifted right by i:
+    entry (i, j) is first_row[(j - i) mod b]."""
+    fr = np.asarray(first_row, dtype=np.uint8)
+    b = len(fr)
+    idx = (np.arange(b)[None, :] - np.arange(b)[:, None]) % b
+    return fr[idx]
 
 
 def _qc_plane(rng: Xoshiro256ss, block_rows: int, block_cols: int, b: int,
@@ -188,6 +194,42 @@ def quasi_cyclic(rng: Xoshiro256ss, n: int = 72, block_rows: int = 6, block_cols
 quasi_cyclic.last_tries = 0
 
 
+def random_symplectic_image(rows: np.ndarray, rng: Xoshiro256ss, steps: int) -> np.ndarray:
+    """Applies `steps` symplectic transvections T_v(x) = x + <x, v> v with
+    uniformly drawn nonzero v in F2^{2n} to each row (x | z) of `rows`; the
+    form is <(a|b), (c|d)> = a.d + b.c.  Transvections generate the
+    symplectic group, so the rows' commutation relations are kept."""
+    out = np.array(rows, dtype=np.uint8, copy=True)
+    n2 = out.shape[1]
+    n = n2 // 2
+    for _ in range(steps):
+        v = rng.bits(n2)
+        while not v.any():
+            v = rng.bits(n2)
+        sw = np.concatenate([v[n:], v[:n]])  # <x, v> = x . (v_z | v_x)
+        form = (out.astype(np.int64) @ sw.astype(np.int64)) & 1
+        out ^= (form[:, None] * v[None, :]).astype(np.uint8)
+    return out
+
+
+def small_k_normalizer(n: int, k: int, rng: Xoshiro256ss, steps: int | None = None):
+    """Normalizer matrix of a random stabilizer code with n qubits and k
+    logical qubits (small k): the standard code's stabilizers Z_1..Z_{n-k} and
+    logicals X_j, Z_j (j > n-k) moved by a random symplectic map (a product of
+    transvections).  Returns (N, n_stab): the n + k rows of N, stabilizers
+    first (n_stab = n - k), each row x | z of 2n bits."""
+    if not 0 <= k < n:
+        raise ValueError("need 0 <= k < n")
+    rows = np.zeros((n + k, 2 * n), dtype=np.uint8)
+    for i in range(n - k):
+        rows[i, n + i] = 1                     # Z_i
+    for j in range(k):
+        q = n - k + j
+        rows[n - k + 2 * j, q] = 1             # X_q
+        rows[n - k + 2 * j + 1, n + q] = 1     # Z_q
+    return random_symplectic_image(rows, rng, 4 * n if steps is None else steps), n - k
+
+
 # ---------------------------------------------------------------------------
 # The named workloads.
 # ---------------------------------------------------------------------------
@@ -207,45 +249,72 @@ def single_qc(index: int = 0) -> np.ndarray:
     return quasi_cyclic(Xoshiro256ss(seed_for(2, index)))
 
 
+def small_k_code(index: int = 0, n: int = 56, k: int | None = None):
+    """A random small-k stabilizer code of n qubits (the paper's second-matrix
+    dataset has K/N = (n+k)/2n of 0.538-0.545 and at most 9100 entries,
+    i.e. n up to about 64): k = round(0.08 n) unless given.  Returns
+    (N, n_stab)."""
+    if k is None:
+        k = max(1, int(round(0.08 * n)))
+    return small_k_normalizer(n, k, Xoshiro256ss(seed_for(6, (n << 16) | (k << 8) | index)))
+
+
+def batch_code(index: int, nmin: int = 16, nmax: int = 56, config_id: int = 3) -> np.ndarray:
+    """Item ``index`` of the batched workload (workload 3): a random F2 code
+    with n ~ U[nmin, nmax], K ~ U[ceil(n/2), n]."""
+    rng = Xoshiro256ss(seed_for(config_id, index))
+    n = nmin + rng.below(nmax - nmin + 1)
+    kmin = (n + 1) // 2
+    K = kmin + rng.below(n - kmin + 1)
+    return random_f2_code(n, K, rng)
+
+
 def batch_codes(count: int = 4096, nmin: int = 16, nmax: int = 56, config_id: int = 3):
     """Independent random F2 codes with n ~ U[nmin, nmax], K ~ U[ceil(n/2), n]
     (workload 3).  Returns a list of (K, 2n) uint8 arrays."""
+    return [batch_code(i, nmin, nmax, config_id) for i in range(count)]
+
+
+def stream_request(index: int, nmin: int = 20, nmax: int = 96, config_id: int = 4):
+    """The code of request ``index`` of the served stream (workload 4), as
+    (kind, generator): kind "f2" or "qc", drawn 50/50.  It depends only on the
+    index, not on the arrival rate.  Quasi-cyclic sizes: n is snapped down to
+    a multiple of 6 (>= 24), the x and z parts use 6 block-columns of b = n/6
+    circulants, round(6K/n) in {3..6} block-rows (K = block_rows * b),
+    circulant weights uniform in {2..min(5,b)}."""
+    rng = Xoshiro256ss(seed_for(config_id, index))
+    n = nmin + rng.below(nmax - nmin + 1)
+    kmin = (n + 1) // 2
+    K = kmin + rng.below(n - kmin + 1)
+    if rng.below(2) == 0:
+        return "f2", random_f2_code(n, K, rng)
+    nq = max(24, (n // 6) * 6)
+    br = min(6, max(3, int(round(6.0 * K / nq))))
+    return "qc", quasi_cyclic(rng, n=nq, block_rows=br, block_cols=6, wmin=2, wmax=5)
+
+
+def request_times(rate_hz: float = 2000.0, duration_s: float = 60.0, config_id: int = 4,
+                  max_requests: int | None = None) -> list[float]:
+    """Poisson arrival times (seconds) of the served stream: exponential gaps
+    of mean 1/rate_hz from one seeded stream, up to duration_s."""
+    master = Xoshiro256ss(seed_for(config_id, 0xFFFFFFFF))
+    t = 0.0
     out = []
-    for i in range(count):
-        rng = Xoshiro256ss(seed_for(config_id, i))
-        n = nmin + rng.below(nmax - nmin + 1)
-        kmin = (n + 1) // 2
-        K = kmin + rng.below(n - kmin + 1)
-        out.append(random_f2_code(n, K, rng))
-    return out
+    while True:
+        u = master.uniform()
+        t += -math.log(1.0 - u) / rate_hz
+        if t >= duration_s or (max_requests is not None and len(out) >= max_requests):
+            return out
+        out.append(t)
 
 
 def request_stream(rate_hz: float = 2000.0, duration_s: float = 60.0, nmin: int = 20,
                    nmax: int = 96, config_id: int = 4, max_requests: int | None = None):
     """Poisson arrival stream of distance queries (workload 4).
 
-    Yields (arrival_time_s, kind, generator) with kind "f2" or "qc" drawn 50/50.
-    Quasi-cyclic sizes: n is snapped down to a multiple of 6 (>= 24), the x and
-    z parts use 6 block-columns of b = n/6 circulants, round(6K/n) in {3..6}
-    block-rows (K = block_rows * b), circulant weights uniform in {2..min(5,b)}.
+    Yields (arrival_time_s, kind, generator); request i arrives at the i-th
+    time of request_times and carries the code stream_request(i).
     """
-    master = Xoshiro256ss(seed_for(config_id, 0xFFFFFFFF))
-    t = 0.0
-    i = 0
-    while True:
-        u = master.uniform()
-        t += -math.log(1.0 - u) / rate_hz
-        if t >= duration_s or (max_requests is not None and i >= max_requests):
-            return
-        rng = Xoshiro256ss(seed_for(config_id, i))
-        n = nmin + rng.below(nmax - nmin + 1)
-        kmin = (n + 1) // 2
-        K = kmin + rng.below(n - kmin + 1)
-        if rng.below(2) == 0:
-            yield t, "f2", random_f2_code(n, K, rng)
-        else:
-            nq = max(24, (n // 6) * 6)
-            b = nq // 6
-            br = min(6, max(3, int(round(6.0 * K / nq))))
-            yield t, "qc", quasi_cyclic(rng, n=nq, block_rows=br, block_cols=6, wmin=2, wmax=5)
-        i += 1
+    for i, t in enumerate(request_times(rate_hz, duration_s, config_id, max_requests)):
+        kind, g = stream_request(i, nmin, nmax, config_id)
+        yield t, kind, g

@@ -319,3 +319,35 @@ def tiny_random_code(rng: np.random.Generator, n: int, K: int, kind: str) -> np.
     if kind == "sparse":
         return (rng.random((K, 2 * n)) < 0.2).astype(np.uint8)
     raise ValueError(kind)
+
+
+def generator_digest(gens):
+    """The digest make_oracle_tables.py writes over generator matrices."""
+    import hashlib
+    h = hashlib.sha256()
+    for g in gens:
+        h.update(bytes([g.shape[0] & 255, g.shape[1] & 255]))
+        h.update(np.ascontiguousarray(g, dtype=np.uint8).tobytes())
+    return h.hexdigest()
+
+
+def load_oracle_table(name):
+    """Reads tests/golden/<name> (written by make_oracle_tables.py): returns
+    (header digests {"all": hex, "first1000": hex}, {index: (n, K, d, lower,
+    upper)}), d None where the oracle did not certify it (lower <= d <= upper)."""
+    digests, rows = {}, {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            if line.startswith("# generators sha256"):
+                digests["all"] = line.split()[-1]
+            elif line.startswith("# first 1000 generators sha256"):
+                digests["first1000"] = line.split()[-1]
+            elif line.strip() and not line.startswith("#"):
+                p = line.split()
+                i, n, K = int(p[0]), int(p[1]), int(p[2])
+                if p[3] == "-":
+                    rows[i] = (n, K, None, int(p[4]), int(p[5]))
+                else:
+                    d = int(p[3])
+                    rows[i] = (n, K, d, d, d)
+    return digests, rows

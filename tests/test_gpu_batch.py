@@ -9,7 +9,7 @@ import oracle
 import paper_2408_10743_gb300 as dist
 from paper_2408_10743_gb300 import synth
 from paper_2408_10743_gb300.binding import DIST_EBUSY
-from codes import sym_weight_bits, tiny_random_code, toric
+from codes import load_oracle_table, sym_weight_bits, tiny_random_code, toric
 
 pytestmark = pytest.mark.gpu
 
@@ -141,15 +141,25 @@ def test_admission_limits_and_ownership():
         c.close()
 
 
-def test_batch_workload3_sample():
-    """First codes of the 4096-code batched workload vs the single-code path."""
-    gens = synth.batch_codes(64)
+def test_batch_workload_vs_oracle_table():
+    """All 4096 codes of the batched workload (n ~ U[16,56], K ~ U[n/2,n]) in
+    one batch, and each one solved alone, against the CPU oracle's stored
+    distances (tests/golden/batch4096_oracle.txt): d equal element by element,
+    every witness valid."""
+    _, table = load_oracle_table("batch4096_oracle.txt")
+    gens = synth.batch_codes(4096)
     codes = [dist.Code(g) for g in gens]
     with dist.Batch() as b:
-        res = b.wait(b.submit(codes), timeout_s=120)
-    for g, c, r in zip(gens, codes, res):
-        assert r["d"] == c.solve()["d"]
+        res = b.wait(b.submit(codes), timeout_s=300)
+    bad = [(i, r["d"], table[i][2]) for i, r in enumerate(res) if r["d"] != table[i][2]]
+    assert not bad, bad[:10]
+    for g, r in zip(gens, res):
         valid(g, r)
+    alone = [dist.dist_solve(c._h) for c in codes]
+    bad = [(i, r.d, table[i][2]) for i, r in enumerate(alone) if r.d != table[i][2]]
+    assert not bad, bad[:10]
+    for c in codes:
+        c.close()
 
 
 def test_time_limit_bounds_and_wait_any():

@@ -250,3 +250,39 @@ def test_package_structure_max_sizes(case):
         g = rng.integers(0, 4, size=(100, n), dtype=np.uint8)
     info, _ = check_structure(g, field=4 if case == "f4" else 2)
     assert info.k_eff == f2_rank(f2_image(g, 4 if case == "f4" else 2)) // (2 if case == "f4" else 1)
+
+
+def test_small_k_normalizers_plan_a_second_matrix():
+    """Normalizer matrices with few logical qubits (Section 2.3: the second
+    matrix's bound term pays off when k is small): the planner builds a second
+    matrix on the unused qubits with about 2k free rows, the inclusion policy
+    enumerates it, and the inclusion limit of 1 keeps only the first."""
+    import paper_2408_10743_gb300 as dist
+    from paper_2408_10743_gb300 import synth
+    limit = dist.dist_get_gamma_limit()
+    try:
+        for n, k, idx in ((40, 2, 0), (44, 3, 1), (48, 3, 0), (56, 4, 0)):
+            N, n_stab = synth.small_k_code(idx, n, k)
+            assert N.shape == (n + k, 2 * n) and n_stab == n - k
+            dist.dist_set_gamma_limit(0)
+            info = dist.dist_plan_info_get(N, n_stab=n_stab)
+            assert info.n_gamma_built >= 2 and info.n_gamma_used == 2
+            assert info.f[0] == 0 and 2 * k <= info.f[1] <= 2 * k + 2
+            dist.dist_set_gamma_limit(1)
+            assert dist.dist_plan_info_get(N, n_stab=n_stab).n_gamma_used == 1
+        with pytest.raises(dist.DistError):
+            dist.dist_set_gamma_limit(-1)
+    finally:
+        dist.dist_set_gamma_limit(limit)
+
+
+def test_small_k_generator_is_a_normalizer():
+    """synth.small_k_normalizer: the stabilizer rows commute with every row,
+    the rows are independent, and a logical pair anticommutes."""
+    from paper_2408_10743_gb300 import synth
+    for n, k in ((12, 2), (30, 3), (56, 4)):
+        N, s = synth.small_k_code(0, n, k)
+        J = np.concatenate([N[:, n:], N[:, :n]], axis=1).astype(np.int64)
+        G = (N.astype(np.int64) @ J.T) & 1
+        assert not G[:s].any() and not G[:, :s].any()
+        assert G[s, s + 1] == 1 and f2_rank(N) == n + k

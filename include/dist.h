@@ -106,16 +106,35 @@ typedef struct {
 } dist_result;
 
 /*
- * dist_solve -- steps S3-S6: enumerate rounds until L >= U and return the
- * certified d with a witness.  Work is ordered on cuda_stream; the call
- * returns after the result is on the host.
+ * dist_solve -- steps S3-S6, the Brouwer-Zimmermann loop of Section 2.1 with
+ * the package bound of Section 2.3: for r = 1, 2, ... every r-subset of the
+ * units of each enumerated generator matrix, every representative choice
+ * (F4: the first unit's scalar fixed to 1), weighed by wt_s = popcount(x OR
+ * z); the upper bound U is the lightest codeword met (outside S with
+ * dist_set_exclude), the lower bound L = sum_j max(0, r + 1 - f_j) over the
+ * finished rounds (f_j: free rows of matrix j), and d = U once L >= U.
+ *   c:           from dist_init; used by one host thread at a time.
+ *   out:         caller-owned; filled completely (d, witness, coefficients,
+ *                counts, times).  witness is re-checked on the host against
+ *                the input rows before DIST_OK is returned.
+ *   cuda_stream: a cudaStream_t (NULL: the library's own stream); work is
+ *                ordered on it and the call returns after the result is on
+ *                the host.
+ * Errors: DIST_EINVAL (NULL arguments), DIST_EBUSY (c is in a batch),
+ * DIST_EZERO (no nonzero codeword outside S), DIST_ERANGE (certification
+ * needs combinations beyond the device walk), DIST_ECUDA, DIST_EINTERNAL (a
+ * witness failed the host re-check; no d is returned).
  */
 int dist_solve(dist_code *c, dist_result *out, void *cuda_stream);
 
 /*
- * dist_solve_bounded -- as dist_solve, but stops after about time_limit_s
- * seconds (checked between launches and by the kernels themselves) and then
- * returns DIST_EINCOMPLETE with lower <= d <= upper (out->d = upper).
+ * dist_solve_bounded -- as dist_solve (Section 2.1), but stops after about
+ * time_limit_s seconds and then returns DIST_EINCOMPLETE with certified
+ * bounds lower <= d <= upper (out->d = upper, out->witness of weight upper).
+ * The limit is checked between launches and by the kernel itself (a
+ * %globaltimer budget); a launch that ends on its budget certifies d only if
+ * U already met the bound that held before it.  time_limit_s <= 0 means no
+ * limit (dist_solve).
  */
 int dist_solve_bounded(dist_code *c, dist_result *out, void *cuda_stream, double time_limit_s);
 
@@ -200,8 +219,9 @@ int dist_batch_destroy(dist_batch *b);
  * chunk also holds at least eight subsets.  Values outside the ranges are
  * clamped; fields <= 0 keep the current value.  dist_autotune times calibration solves (random codes of
  * 64 x 56 and 72 x 72) on the current device over a grid of the three,
- * applies the setting with the best geometric-mean codewords/s, and returns
- * it (and that rate) -- about budget_s seconds (<= 0: about 10 s).
+ * applies the setting with the best geometric-mean codewords/s (the setting
+ * in force stays unless another is at least 2 % faster), and returns it (and
+ * that rate) -- about budget_s seconds (<= 0: about 10 s).
  */
 typedef struct {
     int32_t chunks_per_warp;
@@ -261,23 +281,6 @@ int dist_plan_info_get(const uint8_t *generator, int n, int K, int field, int n_
  */
 int dist_plan_unit(const uint8_t *generator, int n, int K, int field, int gamma, int unit,
                    int rep, uint8_t *vec_out, int *qubit, int *kind);
-
-/*
- * dist_launch_digest -- a 64-bit FNV-1a digest of what the first enumeration
- * launch of dist_solve reads for this input: the device tables, the seed
- * bound and its witness slot, the launch parameters (device pointers and the
- * time budget left out) and the segment table, under the current tuning.
- *   generator, n, K, field, n_stab: as dist_init and dist_set_exclude.
- *   target_warps: resident warps the launch is planned for (SMs x blocks per
- *                 SM x 8); > 0 needs no device, <= 0 takes the current
- *                 device's (a CUDA call, DIST_ECUDA without one).
- *   digest: written on success, 0 on failure.
- * Equal digests hand the kernel byte-identical work, so a hardware-counter
- * profile of that launch (its DRAM traffic) stays valid for as long as the
- * kernel sources are unchanged too.  Errors: as dist_init.
- */
-int dist_launch_digest(const uint8_t *generator, int n, int K, int field, int n_stab, int target_warps,
-                       uint64_t *digest);
 
 /*
  * Qubit stabilizer codes (Section 2).  The classical stabilizer code S of an

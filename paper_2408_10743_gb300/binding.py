@@ -90,8 +90,6 @@ SIGNATURES = {
     "dist_plan_unit": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
-    "dist_launch_digest": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                          ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     "dist_intpeak": (ctypes.c_int, [ctypes.POINTER(IntpeakResult), ctypes.c_int, _VP]),
     "dist_normalizer": (ctypes.c_int, [_U8P, ctypes.c_int, ctypes.c_int, _U8P, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int)]),
@@ -255,14 +253,6 @@ def dist_plan_unit(generator, gamma, unit, rep, field=DIST_F2):
     _check(lib().dist_plan_unit(_ptr(g), n, K, field, gamma, unit, rep, _ptr(out),
                                 ctypes.byref(q), ctypes.byref(kind)), "dist_plan_unit")
     return out, q.value, kind.value
-
-
-def dist_launch_digest(generator, field=DIST_F2, n_stab=0, target_warps=0) -> int:
-    g, n, K = _as_gen(generator, field)
-    d = ctypes.c_uint64(0)
-    _check(lib().dist_launch_digest(_ptr(g), n, K, field, n_stab, target_warps, ctypes.byref(d)),
-           "dist_launch_digest")
-    return d.value
 
 
 def dist_intpeak(iters=4096, stream=None) -> IntpeakResult:

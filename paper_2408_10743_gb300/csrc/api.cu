@@ -407,27 +407,6 @@ int dist_plan_info_get(const uint8_t* generator, int n, int K, int field, int n_
     return DIST_OK;
 }
 
-int dist_launch_digest(const uint8_t* generator, int n, int K, int field, int n_stab, int target_warps,
-                       uint64_t* digest) {
-    if (!digest) return DIST_EINVAL;
-    *digest = 0;
-    Plan p;
-    int rc = map_plan_rc(plan_build(generator, n, K, field, &p));
-    if (rc) return rc;
-    if (n_stab) {
-        rc = map_plan_rc(plan_set_exclude(&p, n_stab));
-        if (rc) return rc;
-    }
-    if (target_warps <= 0) {  // this device's, as a solve computes it
-        DeviceCtx* d = nullptr;
-        rc = device_ctx(&d);
-        if (rc) return rc;
-        target_warps = d->sms * d->blocks_per_sm * DIST_ENUM_WARPS;
-    }
-    *digest = first_launch_digest(p, target_warps);
-    return DIST_OK;
-}
-
 int dist_plan_unit(const uint8_t* generator, int n, int K, int field, int gamma, int unit, int rep,
                    uint8_t* vec_out, int* qubit, int* kind) {
     if (!vec_out) return DIST_EINVAL;
@@ -505,10 +484,14 @@ int dist_get_tuning(dist_tuning* t) {
 namespace {
 
 // Times two solves of every code per setting of the grid (the second one
-// counts) and applies the setting with the best geometric-mean codewords/s.
+// counts) and applies the setting with the best geometric-mean codewords/s,
+// the setting in force winning unless another is 2 % faster.
 int autotune_on(const std::vector<dist_code*>& codes, double budget_s, dist_tuning* best) {
     const Tuning saved = tuning_get();
-    std::vector<Tuning> grid;
+    // the setting in force is timed first and kept unless another one is
+    // at least 2 % faster: on codes whose launches the tuning does not
+    // reach, the choice would otherwise follow timing noise
+    std::vector<Tuning> grid{saved};
     for (int a : {2, 3, 6, 12})
         for (int b : {13, 14, 16})
             for (int f : {8, 10, 12}) {
@@ -539,7 +522,7 @@ int autotune_on(const std::vector<dist_code*>& codes, double budget_s, dist_tuni
             }
         }
         const double rate = std::exp(log_rate / (double)codes.size());
-        if (rate > best_rate) {
+        if (best_rate < 0 || rate > 1.02 * best_rate) {
             best_rate = rate;
             best_t = t;
         }

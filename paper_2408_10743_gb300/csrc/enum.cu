@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         }
         const LaneCtx& C = s_ctx[sg.g];
         unsigned long long lo, hi;
-        if (seg_lane_range(sg, chunk, lane, lo, hi)) done += walk_range(C, sink, thr, sg, lo, hi);
+        if (seg_lane_range(sg, chunk, lane, lo, hi)) done += walk_range(C, sink, thr, sg, lo, hi, u_now);
         if (P.budget_ns) {
             int stop = 0;
             if (lane == 0 && global_ns() - t_start > P.budget_ns) {
@@ -239,6 +239,7 @@ __device__ __forceinline__ void slice_params(const unsigned char* arena, const u
 __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB)
     enum_batch_kernel(const unsigned char* __restrict__ arena, const unsigned long long* binom) {
     __shared__ BatchParams sP;
+    __shared__ LaneCtx s_wctx[DIST_ENUM_WARPS];
     if (threadIdx.x == 0) slice_params(arena, binom, &sP);
     __syncthreads();
     const BatchParams& P = sP;
@@ -297,26 +298,33 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB)
             continue;
         }
         const GammaDesc& g = P.gammas[bc.g0 + sg.g];
-        LaneCtx C;
-        C.reps = bc.tables + g.rep_off;
-        C.r0 = reinterpret_cast<const U2*>(bc.tables + g.r0_off);
-        C.r1 = reinterpret_cast<const U2*>(bc.tables + g.r1_off);
-        C.flags = bc.tables + g.flag_off;
-        C.t1 = g.t1;
-        C.coefs = bc.tables + g.coef_off;
-        C.binom = P.binom;
-        C.bstride = DIST_MAXR + 1;
-        C.outside = bc.outside;
-        C.a = g.a;
-        C.b = g.b;
-        C.W = bc.W;
-        C.CW = bc.CW;
-        C.gamma = g.gamma;
-        C.proj = bc.proj;
-        C.exclude = bc.exclude;
+        // The warp's lane context lives in shared memory: a local copy whose
+        // address reaches the walk's cold functions would be read from local
+        // memory in the hot loop.
+        __syncwarp();
+        LaneCtx& C = s_wctx[threadIdx.x >> 5];
+        if (lane == 0) {
+            C.reps = bc.tables + g.rep_off;
+            C.r0 = reinterpret_cast<const U2*>(bc.tables + g.r0_off);
+            C.r1 = reinterpret_cast<const U2*>(bc.tables + g.r1_off);
+            C.flags = bc.tables + g.flag_off;
+            C.t1 = g.t1;
+            C.coefs = bc.tables + g.coef_off;
+            C.binom = P.binom;
+            C.bstride = DIST_MAXR + 1;
+            C.outside = bc.outside;
+            C.a = g.a;
+            C.b = g.b;
+            C.W = bc.W;
+            C.CW = bc.CW;
+            C.gamma = g.gamma;
+            C.proj = bc.proj;
+            C.exclude = bc.exclude;
+        }
+        __syncwarp();
         DevSink sink{bc.scr};
         unsigned long long lo, hi, done = 0;
-        if (seg_lane_range(sg, chunk, lane, lo, hi)) done = walk_range(C, sink, thr, sg, lo, hi);
+        if (seg_lane_range(sg, chunk, lane, lo, hi)) done = walk_range(C, sink, thr, sg, lo, hi, sink.peek());
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
         int stop = 0;

@@ -5,8 +5,11 @@
 //
 // One launch per step (round r of matrix j).  Each block stages the matrix's
 // rows, restricted to the columns outside its information set (a pivot row
-// adds exactly 1 on the set, a free row 0), in shared memory; lanes walk
-// rank ranges of r-subsets in revolving-door order.
+// adds exactly 1 on the set, a free row 0), in shared memory.  Rounds r >= 2
+// walk the subsets in colexicographic order over a shared-memory table of
+// all row pairs (iso_pair_kernel, below); round 1 and matrices whose pair
+// table does not fit have each lane walk its own rank range in
+// revolving-door order (iso_rd_kernel).
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -17,6 +20,7 @@
 #include "code.h"
 #include "iso.h"
 #include "solve.h"
+#include "packed.cuh"
 #include "rdorder.cuh"
 #include "walk.cuh"
 
@@ -211,6 +215,230 @@ __global__ void __launch_bounds__(256) iso_rd_kernel(const __grid_constant__ Iso
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pair-table walk (rounds r >= 2).  In colexicographic order the r-subsets
+// s_1 < s_2 < ... < s_r of the rows have rank
+//     sum_t C(s_t, t) = (s_1 + C(s_2, 2)) + sum_{t >= 3} C(s_t, t),
+// so for a fixed "top" (s_3, ..., s_r) the subsets are consecutive and run
+// through the pairs (s_1, s_2) below s_3 in the order of their pair index
+// s_1 + C(s_2, 2): a prefix of length C(s_3, 2) of all C(K, 2) pairs.  Each
+// block stages a table of every pair's sum on filter words 0-1 and pivot
+// count, in pair-index order.  A warp takes a range of consecutive ranks;
+// its lanes share the current top and take that top's pairs 32 apart, so a
+// codeword is one table load, two XORs and two popcounts against the top's
+// sum, and the step to the next top is the same on every lane.  Lanes idle
+// only in the last pass over a top whose pair count is not a multiple of 32.
+// Only a codeword whose words-0-1 bound falls below U is weighed in full.
+// ---------------------------------------------------------------------------
+
+// Largest c in [lo, hi] with C(c, t) <= R, by bisection on the binomial table.
+__device__ __forceinline__ int colex_top(const unsigned long long* B, int t, unsigned long long R, int lo, int hi) {
+    int a = lo, b = hi + 1;  // C(a, t) <= R < C(b, t) (C(hi + 1, t) taken as infinite)
+    while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (B[mid * (DIST_MAXR + 1) + t] <= R) a = mid;
+        else b = mid;
+    }
+    return a;
+}
+
+// Full weight of the subset (the pair from pair index p, the top (s_3..s_r)
+// packed in T with its lowest element m2) and, when it beats thr, its record;
+// returns the new threshold.  Inlined: as a called function it made the
+// compiler keep part of the walk's state on the stack across the call site,
+// one local load per top step.
+template <int WORDS>
+__device__ __forceinline__ uint32_t iso_pair_slow(const IsoParams& P, const uint32_t* srow, const uint8_t* spiv,
+                                               uint64_t T, int m2, uint32_t p, uint32_t thr) {
+    uint8_t s[DIST_MAXR];
+    int c1 = 1;
+    while ((unsigned)((c1 + 1) * c1 / 2) <= p) ++c1;  // C(c1 + 1, 2) > p >= C(c1, 2)
+    s[0] = (uint8_t)(p - (unsigned)(c1 * (c1 - 1) / 2));
+    s[1] = (uint8_t)c1;
+    for (int t = 2; t < P.r; t++) s[t] = (uint8_t)pk_get(T, t - 2);
+    if (P.r >= 3) s[2] = (uint8_t)m2;
+    const uint32_t w = iso_full<WORDS>(srow, spiv, s, P.r);
+    if (w < thr) iso_record(P, w, s, thr);
+    return thr;
+}
+
+// Largest top size the pair walk keeps in one packed register.
+constexpr int kIsoPairMaxTop = 8;
+
+template <int WORDS>
+__global__ void __launch_bounds__(256) iso_pair_kernel(const __grid_constant__ IsoParams P) {
+    extern __shared__ __align__(16) uint32_t iso_smem[];
+    const int K = P.K, r = P.r, nt = P.r - 2;  // nt: elements of the top
+    const int npairs = K * (K - 1) / 2;
+    uint4* spt = reinterpret_cast<uint4*>(iso_smem);         // [C(K,2)]: words 0-1 of the pair's sum, pivots
+    uint4* srt = spt + npairs;                               // [K]: words 0-1 of the row, pivot
+    uint4* sdt = srt + K;                                    // [K]: rows c and c + 1 XORed, pivot change
+    uint32_t* srow = reinterpret_cast<uint32_t*>(sdt + K);   // [K][WORDS]
+    uint8_t* spiv = reinterpret_cast<uint8_t*>(srow + K * WORDS);
+    for (int t = threadIdx.x; t < K * WORDS; t += blockDim.x) {
+        const int row = t / WORDS, w = t - row * WORDS;
+        srow[t] = w < P.words ? P.rows[(size_t)row * P.words + w] : 0u;
+    }
+    for (int t = threadIdx.x; t < K; t += blockDim.x) spiv[t] = P.piv[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < K; t += blockDim.x)
+        srt[t] = make_uint4(srow[t * WORDS], WORDS > 1 ? srow[t * WORDS + 1] : 0u, spiv[t], 0u);
+    __syncthreads();
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+        const uint4 a = srt[t], b = t + 1 < K ? srt[t + 1] : make_uint4(0u, 0u, 0u, 0u);
+        sdt[t] = make_uint4(a.x ^ b.x, a.y ^ b.y, b.z - a.z, 0u);
+    }
+    for (int c1 = 1 + (int)(threadIdx.x >> 5); c1 < K; c1 += (int)(blockDim.x >> 5)) {
+        const int base = c1 * (c1 - 1) / 2;
+        for (int c0 = (int)(threadIdx.x & 31); c0 < c1; c0 += 32) {
+            const uint4 a = srt[c0], b = srt[c1];
+            spt[base + c0] = make_uint4(a.x ^ b.x, a.y ^ b.y, a.z + b.z, 0u);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    volatile uint32_t* Up = &P.scr->U;
+    uint32_t thr = DIST_WINF;
+    for (;;) {
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(&P.scr->next_chunk, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        if (chunk >= P.nchunks) break;
+        // The warp's ranks [R0, R1): every lane holds the same top; the lanes
+        // take its pairs p0, p0 + 1, ... 32 apart.
+        const unsigned long long R0 = chunk * 32ull * P.spl;
+        const unsigned long long R1 = min(R0 + 32ull * P.spl, P.nsub);
+        // the top (s_3, ..., s_r) packed, element t - 3 in bits 8(t-3)..;
+        // m2 = s_3 is kept apart (the packed copy of it is refreshed only
+        // where it is read), s4 = s_4 (K if there is none)
+        uint64_t T = 0;
+        uint32_t bx = 0, by = 0, npb = 0;
+        unsigned long long R = R0;
+        {
+            int hi = K - 1;
+            for (int t = r; t >= 3; --t) {
+                const int c = colex_top(P.binom, t, R, t - 1, hi);
+                T |= (uint64_t)c << (8 * (t - 3));
+                R -= P.binom[c * (DIST_MAXR + 1) + t];
+                const uint4 q = srt[c];
+                bx ^= q.x;
+                by ^= q.y;
+                npb += q.z;
+                hi = c - 1;
+            }
+        }
+        uint32_t p0 = (uint32_t)R;  // pair index of rank R0 in its top
+        int m2 = nt >= 1 ? pk_get(T, 0) : K;
+        int s4 = nt >= 2 ? pk_get(T, 1) : K;
+        uint32_t cm = (uint32_t)(m2 * (m2 - 1) / 2);
+        uint32_t left = (uint32_t)(R1 - R0);  // at most 32 x 2^14
+        // the running bound, prefetched and taken once at least 32 passes
+        // have run since, so that the load's latency is covered (a stale,
+        // larger U is still a valid threshold)
+        uint32_t u_next = *Up, passes = 0;
+        thr = min(thr, u_next);
+        for (;;) {
+            if (passes >= 32u) {
+                thr = min(thr, u_next);
+                u_next = *Up;
+                passes = 0;
+            }
+            const uint32_t nh = min(cm - p0, left);
+            passes += (nh + 31u) >> 5;
+            uint32_t q = (uint32_t)lane;
+            for (; q + 32u < nh; q += 64u) {  // two pairs per pass: two table loads in flight
+                const uint32_t p = p0 + q;
+                const uint4 e0 = spt[p], e1 = spt[p + 32u];
+                const uint32_t w0 = npb + e0.z + (uint32_t)__popc(bx ^ e0.x) + (uint32_t)__popc(by ^ e0.y);
+                const uint32_t w1 = npb + e1.z + (uint32_t)__popc(bx ^ e1.x) + (uint32_t)__popc(by ^ e1.y);
+                if (w0 < thr) thr = iso_pair_slow<WORDS>(P, srow, spiv, T, m2, p, thr);
+                if (w1 < thr) thr = iso_pair_slow<WORDS>(P, srow, spiv, T, m2, p + 32u, thr);
+            }
+            if (q < nh) {
+                const uint32_t p = p0 + q;
+                const uint4 e = spt[p];
+                const uint32_t w = npb + e.z + (uint32_t)__popc(bx ^ e.x) + (uint32_t)__popc(by ^ e.y);
+                if (w < thr) thr = iso_pair_slow<WORDS>(P, srow, spiv, T, m2, p, thr);
+            }
+            left -= nh;
+            if (left == 0) break;
+            p0 = 0;
+            // the next top in colex order (the same step on every lane)
+            if (m2 + 1 < s4) {  // s_3 moves up by one: C(m2 + 1, 2) = C(m2, 2) + m2
+                const uint4 d = sdt[m2];
+                bx ^= d.x;
+                by ^= d.y;
+                npb += d.z;
+                cm += (uint32_t)m2;
+                ++m2;
+            } else {  // carry: the first s_t that can move up does, the ones below it reset
+                T = pk_put(T, 0, m2);
+                int t = 0;
+                while (t + 1 < nt && pk_get(T, t) + 1 == pk_get(T, t + 1)) ++t;
+                for (int u = 0; u < t; ++u) {
+                    const uint4 qo = srt[pk_get(T, u)], qn = srt[u + 2];
+                    bx ^= qo.x ^ qn.x;
+                    by ^= qo.y ^ qn.y;
+                    npb += qn.z - qo.z;
+                    T = pk_put(T, u, u + 2);
+                }
+                const int c = pk_get(T, t);
+                const uint4 d = sdt[c];
+                bx ^= d.x;
+                by ^= d.y;
+                npb += d.z;
+                T = pk_put(T, t, c + 1);
+                m2 = pk_get(T, 0);
+                s4 = nt >= 2 ? pk_get(T, 1) : K;
+                cm = (uint32_t)(m2 * (m2 - 1) / 2);
+            }
+        }
+        if (lane == 0) atomicAdd(&P.scr->codewords, R1 - R0);
+    }
+}
+
+template <int WORDS>
+size_t iso_pair_smem(int K) {
+    return (size_t)K * (K - 1) / 2 * 16 + (size_t)K * 32 + (size_t)K * WORDS * 4 + (size_t)K + 16;
+}
+
+template <int WORDS>
+cudaError_t iso_pair_launch_w(const IsoParams& P, int sms, size_t optin, cudaStream_t st, bool* used) {
+    *used = false;
+    const size_t smem = iso_pair_smem<WORDS>(P.K);
+    if (smem > optin || P.r - 2 > kIsoPairMaxTop) return cudaSuccess;  // the caller takes the plain walk
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(iso_pair_kernel<WORDS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return cudaErrorUnknown;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, iso_pair_kernel<WORDS>, 256, smem) != cudaSuccess)
+        return cudaErrorUnknown;
+    bps = std::max(1, bps);
+    const unsigned long long want = (P.nchunks + 7) / 8;
+    const int grid = (int)std::min<unsigned long long>(want, (unsigned long long)sms * bps);
+    iso_pair_kernel<WORDS><<<std::max(1, grid), 256, smem, st>>>(P);
+    *used = true;
+    return cudaGetLastError();
+}
+
+cudaError_t iso_pair_launch(const IsoParams& P, int words, int sms, size_t optin, cudaStream_t st, bool* used) {
+    switch (words) {
+        case 1: return iso_pair_launch_w<1>(P, sms, optin, st, used);
+        case 2: return iso_pair_launch_w<2>(P, sms, optin, st, used);
+        case 3: return iso_pair_launch_w<3>(P, sms, optin, st, used);
+        case 4: return iso_pair_launch_w<4>(P, sms, optin, st, used);
+        case 5: return iso_pair_launch_w<5>(P, sms, optin, st, used);
+        case 6: return iso_pair_launch_w<6>(P, sms, optin, st, used);
+        case 7: return iso_pair_launch_w<7>(P, sms, optin, st, used);
+        case 8: return iso_pair_launch_w<8>(P, sms, optin, st, used);
+        case 9: return iso_pair_launch_w<9>(P, sms, optin, st, used);
+        case 10: return iso_pair_launch_w<10>(P, sms, optin, st, used);
+        case 11: return iso_pair_launch_w<11>(P, sms, optin, st, used);
+        default: return iso_pair_launch_w<12>(P, sms, optin, st, used);
+    }
+}
+
 template <int WORDS>
 cudaError_t iso_rd_launch_w(const IsoParams& P, int sms, cudaStream_t st) {
     const size_t smem = (size_t)P.K * 40 + (size_t)P.K * WORDS * 4 + (size_t)P.K + 16;
@@ -332,7 +560,17 @@ extern "C" int dist_solve_isometry(dist_code* c, dist_result* out, void* cuda_st
     double gpu_s = 0;
     int L = iso_lower_bound(ip, 0, m - 1), rounds = 0;
     if (cudaMemcpyAsync(db, img.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) status = DIST_ECUDA;
-    const unsigned long long tw = (unsigned long long)c->dev->sms * 16ull;  // resident warps (2 x 8 per SM)
+    const unsigned long long tw = (unsigned long long)c->dev->sms * 32ull;  // resident warps (4 x 8 per SM)
+    // rounds r >= 2 take the pair-table walk where its table fits in shared
+    // memory, round 1 and larger matrices the revolving-door walk
+    auto launch_step = [&](const IsoParams& P) -> cudaError_t {
+        if (P.r >= 2) {
+            bool used = false;
+            const cudaError_t e = iso_pair_launch(P, ip.words, c->dev->sms, c->dev->smem_optin, st, &used);
+            if (e != cudaSuccess || used) return e;
+        }
+        return iso_rd_launch(P, ip.words, c->dev->sms, st);
+    };
     for (int r = 1; status == DIST_OK && r <= std::min(K, DIST_MAXR); r++) {
         for (int j = 0; j < m; j++) {
             if (U != DIST_WINF && L >= (int)U) goto certified;
@@ -349,9 +587,11 @@ extern "C" int dist_solve_isometry(dist_code* c, dist_result* out, void* cuda_st
             P.binom = c->dev->d_binom;
             P.scr = dscr;
             P.nsub = nsub;
-            // about 8 warp-chunks per resident warp, at most 2^14 subsets per lane
-            unsigned long long spl = nsub / (32ull * tw * 8ull);
-            spl = std::max(1ull, std::min(spl, 1ull << 14));
+            // about 32 warp-chunks per resident warp, at most 2^11 subsets per
+            // lane (about half a millisecond of a warp), so that the last
+            // chunks leave little of the GPU idle
+            unsigned long long spl = nsub / (32ull * tw * 32ull);
+            spl = std::max(1ull, std::min(spl, 1ull << 11));
             P.spl = (uint32_t)spl;
             P.nchunks = (nsub + 32 * spl - 1) / (32 * spl);
             P.K = K;
@@ -363,7 +603,7 @@ extern "C" int dist_solve_isometry(dist_code* c, dist_result* out, void* cuda_st
             for (int w = 0; w < DIST_MAXCW; w++) P.outside[w] = p.outside[w];
             if (cudaMemsetAsync(&dscr->next_chunk, 0, sizeof(unsigned long long), st) != cudaSuccess ||
                 cudaEventRecord(kit->e0, st) != cudaSuccess ||
-                iso_rd_launch(P, ip.words, c->dev->sms, st) != cudaSuccess ||
+                launch_step(P) != cudaSuccess ||
                 cudaEventRecord(kit->e1, st) != cudaSuccess ||
                 cudaMemcpyAsync(hs, dscr, 32, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                 cudaStreamSynchronize(st) != cudaSuccess) {

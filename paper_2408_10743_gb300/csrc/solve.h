@@ -52,40 +52,6 @@ static const double kLaunchCodewords = 2e13;
 static inline int seed_bound(const Plan& p) { return p.n_stab > 0 ? p.u0_excl : p.u0; }
 static inline const WitnessSlot& seed_slot(const Plan& p) { return p.n_stab > 0 ? p.u0_excl_slot : p.u0_slot; }
 
-// 64-bit FNV-1a digest of what the first enumeration launch of a solve of p
-// reads on a device with target_warps resident warps, under the current
-// tuning: the device tables, the seed bound and its witness slot, the launch
-// parameters (device pointers and time budget excluded) and the segment
-// table.  Equal digests hand the kernel byte-identical work, so a profile of
-// that launch stays valid while the kernel's own sources are unchanged.
-static inline unsigned long long first_launch_digest(const Plan& p, int target_warps) {
-    unsigned long long h = 1469598103934665603ull;
-    auto put = [&h](const void* d, size_t n) {
-        const unsigned char* c = static_cast<const unsigned char*>(d);
-        for (size_t i = 0; i < n; i++) {
-            h ^= c[i];
-            h *= 1099511628211ull;
-        }
-    };
-    const int ub = seed_bound(p);
-    put(&target_warps, sizeof target_warps);
-    put(p.tables.data(), p.tables.size() * sizeof(uint32_t));
-    put(&ub, sizeof ub);
-    if (ub < (int)DIST_WINF) put(&seed_slot(p), sizeof(WitnessSlot));
-    // solve_loop's first step: round 1 of J[0], from the initial bound
-    LaunchPlan lp;
-    const int rc = plan_launch(p, 1, 0, plan_initial_bound(p), ub, target_warps, kLaunchCodewords, &lp);
-    put(&rc, sizeof rc);
-    if (rc == P_OK) {
-        EnumParams ep;
-        plan_params(p, lp, &ep);  // zeroes the pointers and the budget
-        ep.first_static = (uint32_t)ub <= (uint32_t)p.d_est ? 1 : 0;
-        put(&ep, sizeof ep);
-        put(lp.segs.data(), lp.segs.size() * sizeof(SegDesc));
-    }
-    return h;
-}
-
 // Exec must provide:
 //   int reset();                                   // U = DIST_WINF, counters and slots cleared
 //   int seed(uint32_t U0, const WitnessSlot& s);   // U = U0 with s in slot[U0]

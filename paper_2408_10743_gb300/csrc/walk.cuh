@@ -27,6 +27,8 @@
 // current upper bound is it re-walked with full weights (the slow path), so
 // the result is exact.
 #pragma once
+#include <math.h>
+
 #include "dist_types.h"
 
 namespace dist {
@@ -69,20 +71,38 @@ DIST_HD unsigned long long binom_at(const unsigned long long* B, int stride, int
     return B[n * stride + k];
 }
 
+// Largest c in [lo, hi] with C(c, t) <= R (C(lo, t) <= R holds).  The start
+// is the closed-form estimate C(c, t) ~ (c - (t-1)/2)^t / t!, i.e.
+// c ~ (R t!)^(1/t) + (t-1)/2; exact binomial lookups then move it to the
+// answer (one or two steps in practice), so the result does not depend on
+// the floating-point rounding of the estimate.  A lane starting a chunk pays
+// about two dependent table loads per element instead of a bisection's six.
+DIST_HD int cns_top(const unsigned long long* B, int stride, int t, unsigned long long R, int lo, int hi) {
+    int c;
+    if (t == 1) {
+        c = (int)(R < (unsigned long long)hi ? R : (unsigned long long)hi);
+    } else {
+        float fact = 1.0f;
+        for (int k = 2; k <= t; k++) fact *= (float)k;
+        const float x = exp2f((log2f((float)R + 0.5f) + log2f(fact)) / (float)t) + 0.5f * (float)(t - 1);
+        c = x < (float)lo ? lo : (x > (float)hi ? hi : (int)x);
+    }
+    while (c > lo && binom_at(B, stride, c, t) > R) --c;
+    while (c < hi && binom_at(B, stride, c + 1, t) <= R) ++c;
+    return c;
+}
+
 // Subset of revolving-door rank R (0 <= R < C(n, t)), t elements of
-// {0..n-1}, written ascending into s.
+// {0..n-1}, written ascending into s: the largest element c_t is the largest
+// c with C(c, t) <= R, and the rest is the subset of rank C(c_t + 1, t) - 1 - R
+// of {0..c_t - 1}.
 DIST_HD void rd_unrank(const unsigned long long* B, int stride, int n, unsigned long long R, int t,
                        uint8_t* s) {
     for (int tt = t; tt >= 1; --tt) {
-        int lo = tt - 1, hi = n;  // C(lo, tt) <= R < C(hi, tt)
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (binom_at(B, stride, mid, tt) <= R) lo = mid;
-            else hi = mid;
-        }
-        s[tt - 1] = (uint8_t)lo;
-        R = binom_at(B, stride, lo + 1, tt) - 1 - R;
-        n = lo;
+        const int c = cns_top(B, stride, tt, R, tt - 1, n - 1);
+        s[tt - 1] = (uint8_t)c;
+        R = binom_at(B, stride, c + 1, tt) - 1 - R;
+        n = c;
     }
 }
 
@@ -147,9 +167,15 @@ DIST_HD const uint32_t* rep_ptr(const LaneCtx& C, int unit, int e, int plane) {
 
 // Exact weight of the combination (A-units sA with digits eA, B-units sB);
 // records it when it beats thr and, in exclusion mode, lies outside S.
+// Returns the new threshold.  consider() and block_slow() are inlined: as
+// called functions they made the compiler keep more of the fast loop's state
+// on the stack around their call sites.  The functions that stay calls take
+// the sink and the threshold by value: an address passed to a function that
+// is not inlined would keep the caller's copy in local memory through its
+// hot loop.
 template <class Sink>
-DIST_HD_COLD void consider(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                           const uint8_t* eA, int nb, const uint8_t* sB) {
+DIST_HD_FAST uint32_t consider(const LaneCtx& C, Sink sink, uint32_t thr, int i, const uint8_t* sA,
+                               const uint8_t* eA, int nb, const uint8_t* sB) {
     uint32_t x[DIST_MAXW], z[DIST_MAXW];
     for (int w = 0; w < DIST_MAXW; w++) x[w] = z[w] = 0;
     for (int p = 0; p < i; p++) {
@@ -170,7 +196,7 @@ DIST_HD_COLD void consider(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, c
     }
     uint32_t wt = 0;
     for (int w = 0; w < C.W; w++) wt += popc32(x[w] | z[w]);
-    if (wt >= thr) return;
+    if (wt >= thr) return thr;
     if (C.exclude) {
         uint32_t acc = 0;
         for (int w = 0; w < C.CW; w++) {
@@ -187,9 +213,8 @@ DIST_HD_COLD void consider(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, c
             }
             acc |= (c0 | c1) & C.outside[w];
         }
-        if (!acc) return;  // inside S = span(first n_stab rows)
+        if (!acc) return thr;  // inside S = span(first n_stab rows)
     }
-    thr = wt;
     uint8_t units[DIST_MAXR], digits[DIST_MAXR];
     for (int p = 0; p < i; p++) {
         units[p] = sA[p];
@@ -200,6 +225,7 @@ DIST_HD_COLD void consider(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, c
         digits[i + q] = 0;
     }
     sink.record(wt, C.gamma, i + nb, units, digits);
+    return wt;
 }
 
 // Every representative choice of one subset, each weighed on all W words
@@ -239,7 +265,7 @@ DIST_HD void eval_generic_w(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, 
         uint32_t wt = 0;
 #pragma unroll
         for (int w = 0; w < W; w++) wt += (uint32_t)popc32(x[w] | z[w]);
-        if (wt < thr) consider(C, sink, thr, i, sA, e, nb, sB);
+        if (wt < thr) thr = consider(C, sink, thr, i, sA, e, nb, sB);
         int q = 0;
         while (q < nd && cnt[q] == 2) {
             cnt[q] = 0;
@@ -260,14 +286,15 @@ DIST_HD void eval_generic_w(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, 
 }
 
 template <class Sink>
-DIST_HD_COLD void eval_generic(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                               int nb, const uint8_t* sB) {
+DIST_HD_COLD uint32_t eval_generic(const LaneCtx& C, Sink sink, uint32_t thr, int i, const uint8_t* sA,
+                                   int nb, const uint8_t* sB) {
     switch (C.W) {
         case 1: eval_generic_w<1>(C, sink, thr, i, sA, nb, sB); break;
         case 2: eval_generic_w<2>(C, sink, thr, i, sA, nb, sB); break;
         case 3: eval_generic_w<3>(C, sink, thr, i, sA, nb, sB); break;
         default: eval_generic_w<4>(C, sink, thr, i, sA, nb, sB); break;
     }
+    return thr;
 }
 
 // Slow path of one 81-codeword block: each codeword whose lower bound
@@ -277,9 +304,10 @@ DIST_HD_COLD void eval_generic(const LaneCtx& C, Sink& sink, uint32_t& thr, int 
 // subset's packages whose pivot lies beyond the first F words, each worth one
 // more unit of weight.
 template <int F, class Sink>
-DIST_HD_COLD void block_slow(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, const uint8_t* sA,
-                             const uint8_t* dig, int nb, const uint8_t* sB, const uint32_t* vbx,
-                             const uint32_t* vbz, int eB0, uint32_t P) {
+DIST_HD_FAST uint32_t block_slow(const LaneCtx& C, Sink sink, uint32_t thr, int i, const uint8_t* sA,
+                                 const uint8_t* dig, int nb, const uint8_t* sB, uint32_t vbx0, uint32_t vbx1,
+                                 uint32_t vbz0, uint32_t vbz1, int eB0, uint32_t P) {
+    const uint32_t vbx[2] = {vbx0, vbx1}, vbz[2] = {vbz0, vbz1};
     uint8_t e[DIST_MAXR];
     const U2* tab[2] = {C.r0, C.r1};
     uint32_t bx[F], bz[F];
@@ -315,9 +343,10 @@ DIST_HD_COLD void block_slow(const LaneCtx& C, Sink& sink, uint32_t& thr, int i,
             e[i - 3] = (uint8_t)eB;
             e[i - 2] = (uint8_t)e0;
             e[i - 1] = (uint8_t)e1;
-            consider(C, sink, thr, i, sA, e, nb, sB);
+            thr = consider(C, sink, thr, i, sA, e, nb, sB);
         }
     }
+    return thr;
 }
 
 // Popcount of codeword j of the current base (first F words).
@@ -430,7 +459,7 @@ DIST_HD_FAST void eval_fast(const LaneCtx& C, Sink& sink, uint32_t& thr, int i, 
 #undef DIST_SWEEP9
 #undef DIST_STEP
         // weight >= popcount(first F words) + P: only then can a codeword beat thr
-        if (m + P < thr) block_slow<F>(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, eB, P);
+        if (m + P < thr) thr = block_slow<F>(C, sink, thr, i, sA, dig, nb, sB, vbx[0], vbx[1], vbz[0], vbz[1], eB, P);
 #pragma unroll
         for (int f = 0; f < F; f++) {  // B moved twice: rotate its delta triple by two
             const U2 t = Db2[f];
@@ -481,14 +510,17 @@ DIST_HD bool seg_lane_range(const SegDesc& sg, unsigned long long chunk, int lan
 // Walks the combination ranks [lo, hi) of segment sg; returns the number of
 // codewords evaluated.  Sink provides peek() (current upper bound),
 // record(...) and vote_any(p) (true if p holds on any lane running in step
-// with this one).
+// with this one).  u_first is a recent value of U the caller already holds,
+// taken as the bound of the first subset, so that the lane does not wait for
+// a fresh read before its first subset.
 template <class Sink>
 DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& thr, const SegDesc& sg,
-                                      unsigned long long lo, unsigned long long hi) {
+                                      unsigned long long lo, unsigned long long hi, uint32_t u_first) {
     const int i = (int)sg.i, nb = (int)sg.r - i;
     uint8_t sA[DIST_MAXR], sB[DIST_MAXR], dig[DIST_MAXR];
     for (int p = 0; p < DIST_MAXR; p++) dig[p] = 0;
-    unsigned long long tB = lo / sg.NA, tA = lo - tB * sg.NA;
+    // (no B-units in the subset: every rank is an A-rank, no 64-bit division)
+    unsigned long long tB = sg.NB == 1 ? 0ull : lo / sg.NA, tA = lo - tB * sg.NA;
     rd_unrank(C.binom, C.bstride, C.b, tB, nb, sB);
     rd_unrank(C.binom, C.bstride, C.a, tA, i, sA);
     uint32_t vbx[2], vbz[2], PB1, PB2;
@@ -497,7 +529,7 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
     unsigned long long done = 0;
     // The running bound is read one subset ahead: a stale (larger) value is
     // still a valid threshold, and the load's latency overlaps the work.
-    uint32_t u_next = sink.peek();
+    uint32_t u_next = u_first;
     for (unsigned long long idx = lo; idx < hi; ++idx) {
         const uint32_t u = u_next;
         u_next = sink.peek();
@@ -520,7 +552,7 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
                 if (P1 < thr) eval_fast<1>(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, P1);
             }
         } else {
-            eval_generic(C, sink, thr, i, sA, nb, sB);
+            thr = eval_generic(C, sink, thr, i, sA, nb, sB);
         }
         done += sg.codes;
         if (idx + 1 < hi) {

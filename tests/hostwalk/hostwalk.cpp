@@ -116,7 +116,7 @@ struct HostExec {
                 unsigned long long lo, hi;
                 if (!seg_lane_range(sg, chunk, lane, lo, hi)) continue;
                 uint32_t thr = DIST_WINF;
-                scr.codewords += walk_range(C, sink, thr, sg, lo, hi);
+                scr.codewords += walk_range(C, sink, thr, sg, lo, hi, sink.peek());
             }
         }
         out->U = scr.U;
@@ -131,6 +131,68 @@ struct HostExec {
 };
 
 }  // namespace
+
+
+// 64-bit FNV-1a digest of what the first enumeration launch of a solve
+// reads: ties a committed ncu capture of that launch to the planner's
+// current output (tests compare it with the digest recorded beside the
+// capture).
+namespace {
+// reads on a device with target_warps resident warps, under the current
+// tuning: the device tables, the seed bound and its witness slot, the launch
+// parameters (device pointers and time budget excluded) and the segment
+// table.  Equal digests hand the kernel byte-identical work, so a profile of
+// that launch stays valid while the kernel's own sources are unchanged.
+unsigned long long first_launch_digest(const Plan& p, int target_warps) {
+    unsigned long long h = 1469598103934665603ull;
+    auto put = [&h](const void* d, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(d);
+        for (size_t i = 0; i < n; i++) {
+            h ^= c[i];
+            h *= 1099511628211ull;
+        }
+    };
+    const int ub = seed_bound(p);
+    put(&target_warps, sizeof target_warps);
+    put(p.tables.data(), p.tables.size() * sizeof(uint32_t));
+    put(&ub, sizeof ub);
+    if (ub < (int)DIST_WINF) put(&seed_slot(p), sizeof(WitnessSlot));
+    // solve_loop's first step: round 1 of J[0], from the initial bound
+    LaunchPlan lp;
+    const int rc = plan_launch(p, 1, 0, plan_initial_bound(p), ub, target_warps, kLaunchCodewords, &lp);
+    put(&rc, sizeof rc);
+    if (rc == P_OK) {
+        EnumParams ep;
+        plan_params(p, lp, &ep);  // zeroes the pointers and the budget
+        ep.first_static = (uint32_t)ub <= (uint32_t)p.d_est ? 1 : 0;
+        put(&ep, sizeof ep);
+        put(lp.segs.data(), lp.segs.size() * sizeof(SegDesc));
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" int hw_launch_digest(const uint8_t* gen, int n, int K, int field, int n_stab, int target_warps,
+                                unsigned long long* digest) {
+    Plan p;
+    int rc = plan_build(gen, n, K, field, &p);
+    if (rc) return rc;
+    if (n_stab) {
+        rc = plan_set_exclude(&p, n_stab);
+        if (rc) return rc;
+    }
+    *digest = first_launch_digest(p, target_warps);
+    return 0;
+}
+
+extern "C" void hw_set_tuning(int chunks_per_warp, int lane_cap_log2, int lane_floor_log2) {
+    Tuning t = tuning_get();
+    t.chunks_per_warp = chunks_per_warp;
+    t.lane_cap_log2 = lane_cap_log2;
+    t.lane_floor_log2 = lane_floor_log2;
+    tuning_set(t);
+}
 
 extern "C" int hw_solve(const uint8_t* gen, int n, int K, int field, int n_stab, int warps,
                         dist_result* out) {
@@ -245,7 +307,7 @@ extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int 
                     unsigned long long lo, hi;
                     if (!seg_lane_range(sg, chunk, lane, lo, hi)) continue;
                     uint32_t thr = DIST_WINF;
-                    ex.scr.codewords += walk_range(C, sink, thr, sg, lo, hi);
+                    ex.scr.codewords += walk_range(C, sink, thr, sg, lo, hi, sink.peek());
                 }
             }
             (void)part;

@@ -268,14 +268,3 @@ def test_wide_codes_four_words(stream):
         r = gpu(g, stream=stream)
         assert r["d"] == oracle.bruteforce(g)[0], (n, K)
         check_witness(g, r)
-
-
-def test_launch_digest_on_device(stream):
-    """The digest for this device's resident warps (no warp count given) is
-    the host-only digest for SMs x blocks per SM x 8 warps at one of the
-    occupancies the kernel can have."""
-    import torch
-    g = synth.single_qc(0)
-    d = dist.dist_launch_digest(g)
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert d in {dist.dist_launch_digest(g, target_warps=sms * b * 8) for b in (1, 2, 3, 4)}

@@ -64,6 +64,10 @@ def hw():
     L.hw_solve_stop.restype = ctypes.c_int
     L.hw_solve_stop.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(DistResult)]
+    L.hw_launch_digest.restype = ctypes.c_int
+    L.hw_launch_digest.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.hw_set_tuning.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.hw_solve_sliced.restype = ctypes.c_int
     L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -547,3 +551,44 @@ def test_budget_stop_never_certifies_a_wrong_d(hw):
                     early += 1
                     assert r.lower <= d_true <= r.d, (n, K, warps, stop, r.lower, r.d, d_true)
     assert early > 0 and certified > 0
+
+
+def launch_digest(L, g, n_stab=0, warps=2432):
+    g = np.ascontiguousarray(g, dtype=np.uint8)
+    d = ctypes.c_ulonglong(0)
+    rc = L.hw_launch_digest(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), g.shape[1] // 2, g.shape[0], 2,
+                            n_stab, warps, ctypes.byref(d))
+    assert rc == 0
+    return d.value
+
+
+def test_launch_digest(hw):
+    """The digest of what the first enumeration launch of a solve reads
+    (tables, seed, launch parameters, segment table) depends on the warps it
+    is planned for, the code, exclusion and the tuning.  The committed ncu
+    summary of the QC n = 72 launch records the digest of the launch it
+    captured (default tuning, 152 SMs x 2 blocks x 8 warps) and of the kernel
+    sources; the current planner and sources reproduce both, so its DRAM
+    traffic still describes the launch bench.py times."""
+    import json
+    import bench
+    g = synth.single_qc(0)
+    try:
+        hw.hw_set_tuning(6, 14, 12)
+        a = launch_digest(hw, g)
+        assert a == launch_digest(hw, g)
+        assert a != launch_digest(hw, g, warps=2280)
+        assert a != launch_digest(hw, synth.single_qc(1))
+        assert a != launch_digest(hw, g, n_stab=36)
+        # the lane cap shapes the chunks of a random 64 x 60 code (the QC
+        # launch's chunks are set by rules the tuning does not reach)
+        r = synth.random_f2_code(64, 60, synth.Xoshiro256ss(5))
+        b = launch_digest(hw, r)
+        hw.hw_set_tuning(3, 16, 10)
+        assert b != launch_digest(hw, r)
+    finally:
+        hw.hw_set_tuning(6, 14, 12)
+    with open(bench.PROFILE_JSON) as fh:
+        prof = json.load(fh)
+    assert prof["launch_digest"] == "%016x" % a
+    assert prof["kernel_digest"] == bench.kernel_digest()

@@ -252,6 +252,39 @@ def test_witness_is_a_codeword_of_weight_d():
         assert f2_rank(np.vstack([g, w])) == f2_rank(g)
 
 
+def test_bruteforce_witness_is_a_codeword_of_weight_d():
+    """The brute force's witness (decoded from the Gray-code index of the
+    lightest codeword it met) is nonzero, lies in the span, weighs d, and in
+    exclusion mode lies outside the span of the excluded rows; for an F4
+    input it lies in the F4 span (the F2 span of v and alpha v)."""
+    from codes import f4_linear_f2_view
+    rng = np.random.default_rng(18)
+    for trial in range(40):
+        n = int(rng.integers(3, 11))
+        K = int(rng.integers(1, min(2 * n, 14) + 1))
+        g = tiny_random_code(rng, n, K, ["iid", "css", "yheavy", "sparse"][trial % 4])
+        if f2_rank(g) == 0:
+            continue
+        d, w, _ = oracle.bruteforce(g)
+        assert w.any() and sym_weight_bits(w, n) == d
+        assert f2_rank(np.vstack([g, w])) == f2_rank(g)
+        s = int(rng.integers(0, K))
+        if s and f2_rank(g[:s]) < f2_rank(g):
+            d2, w2, _ = oracle.bruteforce(g, n_stab=s)
+            assert sym_weight_bits(w2, n) == d2 >= d
+            assert f2_rank(np.vstack([g, w2])) == f2_rank(g)
+            assert f2_rank(np.vstack([g[:s], w2])) == f2_rank(g[:s]) + 1
+    for _ in range(10):
+        n, k = int(rng.integers(3, 9)), int(rng.integers(1, 4))
+        g4 = rng.integers(0, 4, size=(k, n), dtype=np.uint8)
+        if not g4.any():
+            continue
+        d, w, _ = oracle.bruteforce(g4, field=4)
+        view = f4_linear_f2_view(g4)
+        assert sym_weight_bits(w, n) == d
+        assert f2_rank(np.vstack([view, w])) == f2_rank(view)
+
+
 def test_time_budget_returns_bounds():
     rng = np.random.default_rng(9)
     n, K = 60, 60

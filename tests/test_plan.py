@@ -195,41 +195,6 @@ def test_information_set_search():
     assert list(x.f[:x.n_gamma_built]) == list(y.f[:y.n_gamma_built])
 
 
-def test_launch_digest():
-    """dist_launch_digest (host only with an explicit warp count): the same
-    input gives the same digest, and what the first launch reads changes it
-    -- the warps it is planned for, the code, exclusion, the tuning.  The
-    committed ncu summary of the QC n = 72 launch records the digest of the
-    launch it captured (default tuning, 152 SMs x 2 blocks x 8 warps) and of
-    the kernel sources; the current planner and sources reproduce both, so
-    its DRAM traffic still describes the launch the bench times."""
-    import json
-    import bench
-    g = synth.single_qc(0)
-    prev = dist.dist_get_tuning()
-    try:
-        dist.dist_set_tuning(6, 14, 12)
-        a = dist.dist_launch_digest(g, target_warps=2432)
-        assert a == dist.dist_launch_digest(g, target_warps=2432)
-        assert a != dist.dist_launch_digest(g, target_warps=2280)
-        assert a != dist.dist_launch_digest(synth.single_qc(1), target_warps=2432)
-        assert a != dist.dist_launch_digest(g, n_stab=36, target_warps=2432)
-        # the lane cap shapes the chunks of a random 64 x 60 code (the QC
-        # launch's chunks are set by rules the tuning does not reach)
-        r = synth.random_f2_code(64, 60, synth.Xoshiro256ss(5))
-        b = dist.dist_launch_digest(r, target_warps=2432)
-        dist.dist_set_tuning(3, 16, 10)
-        assert b != dist.dist_launch_digest(r, target_warps=2432)
-    finally:
-        dist.dist_set_tuning(prev["chunks_per_warp"], prev["lane_cap_log2"], prev["lane_floor_log2"])
-    with open(bench.PROFILE_JSON) as fh:
-        prof = json.load(fh)
-    assert prof["launch_digest"] == "%016x" % a
-    assert prof["kernel_digest"] == bench.kernel_digest()
-    with pytest.raises(dist.DistError):
-        dist.dist_launch_digest(np.array([[2, 0]], dtype=np.uint8), target_warps=2432)
-
-
 @pytest.mark.parametrize("case", ["f2_full", "f2_iid", "f2_css", "f4"])
 def test_package_structure_max_sizes(case):
     """The largest inputs the planner takes: n = 128 qubits (four words per

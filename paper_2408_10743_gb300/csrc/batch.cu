@@ -50,8 +50,26 @@ namespace {
 
 // A code with at most this many chunks is served entirely from the order list.
 const unsigned long long kSmallChunks = 64;
-// Host threads that plan a large admission.
+// Host threads that plan, re-chunk and post-process a large slice.
 const size_t kPlanThreads = 8;
+
+// fn(a, b) over [0, n) cut into ranges of at least `grain` items, on up to
+// kPlanThreads host threads (this one included); every item is touched by
+// exactly one thread.
+template <class F>
+void par_ranges(size_t n, size_t grain, const F& fn) {
+    const size_t nthreads = std::max<size_t>(1, std::min(kPlanThreads, n / std::max<size_t>(1, grain)));
+    if (nthreads <= 1) {
+        fn((size_t)0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    const size_t per = (n + nthreads - 1) / nthreads;
+    for (size_t t = 1; t < nthreads; t++)
+        pool.emplace_back([&fn, t, per, n] { fn(std::min(n, t * per), std::min(n, (t + 1) * per)); });
+    fn(0, std::min(n, per));
+    for (std::thread& th : pool) th.join();
+}
 
 struct Item {
     dist_code* c = nullptr;
@@ -186,25 +204,14 @@ int dist_batch::slice() {
     // plans are independent: large admissions are planned on several host
     // threads (each writes only its own items)
     std::vector<int> prc(todo.size(), P_OK);
-    auto plan_range = [&](size_t a, size_t b) {
+    par_ranges(todo.size(), 128, [&](size_t a, size_t b) {
         for (size_t k = a; k < b; k++) {
             Item* it = todo[k];
             const Plan& p = it->c->plan;
             const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
             prc[k] = plan_launch(p, it->r_next, it->j_next, it->L, u0, tw, 1e300, &it->lp);
         }
-    };
-    const size_t nthreads = todo.size() >= 256 ? std::min<size_t>(kPlanThreads, todo.size() / 128) : 1;
-    if (nthreads > 1) {
-        std::vector<std::thread> pool;
-        const size_t per = (todo.size() + nthreads - 1) / nthreads;
-        for (size_t t = 1; t < nthreads; t++)
-            pool.emplace_back(plan_range, std::min(todo.size(), t * per), std::min(todo.size(), (t + 1) * per));
-        plan_range(0, std::min(todo.size(), per));
-        for (std::thread& th : pool) th.join();
-    } else {
-        plan_range(0, todo.size());
-    }
+    });
     for (size_t k = 0; k < todo.size(); k++) {
         Item* it = todo[k];
         if (prc[k]) {
@@ -220,12 +227,14 @@ int dist_batch::slice() {
         double all = 0;
         for (Item* it : active)
             if (!it->done) all += estimated_work(it);
-        for (Item* it : fresh) {
-            const double share = estimated_work(it) / std::max(all, 1.0);
-            const int twi = (int)std::min<double>(tw, std::max(32.0, std::ceil(4.0 * share * tw)));
-            if (twi >= tw) continue;
-            plan_rechunk(&it->lp, twi);
-        }
+        par_ranges(fresh.size(), 128, [&](size_t a, size_t b) {
+            for (size_t k = a; k < b; k++) {
+                Item* it = fresh[k];
+                const double share = estimated_work(it) / std::max(all, 1.0);
+                const int twi = (int)std::min<double>(tw, std::max(32.0, std::ceil(4.0 * share * tw)));
+                if (twi < tw) plan_rechunk(&it->lp, twi);
+            }
+        });
     }
     std::vector<Item*> run;
     for (Item* it : active)
@@ -362,8 +371,11 @@ int dist_batch::slice() {
     gpu_seconds += ms * 1e-3;
     launches++;
     slices++;
-    // per code: certify, resume, or plan the next steps
-    for (int i = 0; i < n; i++) {
+    // per code: certify, resume, or plan the next steps (each item is
+    // touched by one host thread only)
+    const double t_now = wall_now();
+    par_ranges((size_t)n, 128, [&](size_t a, size_t b) {
+    for (size_t i = a; i < b; i++) {
         Item* it = run[i];
         it->slices++;
         const BatchOut& o = outs[i];
@@ -374,8 +386,7 @@ int dist_batch::slice() {
         it->res.codewords = o.codewords;
         const SliceVerdict v = plan_after_slice(p, lp, U, next);
         it->last_round = std::max(it->last_round, v.last_round);
-        if (v.kind != SLICE_CERTIFIED && opts.time_limit_s > 0 &&
-            wall_now() - it->t_admit > opts.time_limit_s) {
+        if (v.kind != SLICE_CERTIFIED && opts.time_limit_s > 0 && t_now - it->t_admit > opts.time_limit_s) {
             // out of time: report the bounds reached, lower <= d <= U
             dist_result& r = it->res;
             r.k_eff = p.k_eff;
@@ -419,6 +430,7 @@ int dist_batch::slice() {
         }
         finish(it, DIST_OK);
     }
+    });
     post_seconds += wall_now() - t_launch - ms * 1e-3;
     return DIST_OK;
 }

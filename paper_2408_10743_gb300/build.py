@@ -20,7 +20,10 @@ LIB = os.path.join(HERE, "libdist.so")
 CU_SOURCES = ["api.cu", "batch.cu", "enum.cu", "intpeak.cu", "iso.cu", "noalloc.cu"]
 CPP_SOURCES = ["plan.cpp", "stab.cpp", "iso.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
+# Warnings are errors: a host-only function called from a host-device
+# function, for one, is only a warning, and the device code then calls
+# nothing sensible.
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v", "-Werror", "all-warnings",
               "-I", CSRC, "-I", INCLUDE]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-I", CSRC, "-I", INCLUDE]
 

@@ -109,7 +109,10 @@ static double dbinom(int n, int k) {
     return exp(lgamma(n + 1.0) - lgamma(k + 1.0) - lgamma(n - k + 1.0));
 }
 
-static unsigned long long ubinom(int n, int k) {
+// C(n, k) exactly, or ~0 if it exceeds 2^63.  n <= DIST_MAXU and
+// k <= DIST_MAXR (every launch's sizes) come from a table built once by the
+// recurrence C(n, k) = C(n-1, k-1) + C(n-1, k), which saturates the same way.
+static unsigned long long ubinom_loop(int n, int k) {
     if (k < 0 || k > n) return 0;
     if (k > n - k) k = n - k;
     unsigned __int128 v = 1;
@@ -118,6 +121,28 @@ static unsigned long long ubinom(int n, int k) {
         if (v > ((unsigned __int128)1 << 63)) return ~0ull;
     }
     return (unsigned long long)v;
+}
+
+static unsigned long long ubinom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    if (n > DIST_MAXU || k > DIST_MAXR) return ubinom_loop(n, k);
+    static const std::vector<unsigned long long> tab = [] {
+        const unsigned long long SAT = ~0ull, LIM = 1ull << 63;
+        std::vector<unsigned long long> t((size_t)(DIST_MAXU + 1) * (DIST_MAXR + 1), 0);
+        for (int m = 0; m <= DIST_MAXU; m++)
+            for (int j = 0; j <= DIST_MAXR && j <= m; j++) {
+                unsigned long long v = 1;
+                if (j > 0 && j < m) {
+                    const unsigned long long a = t[(size_t)(m - 1) * (DIST_MAXR + 1) + j - 1];
+                    const unsigned long long b = t[(size_t)(m - 1) * (DIST_MAXR + 1) + j];
+                    const unsigned __int128 sum = (unsigned __int128)a + b;
+                    v = (a == SAT || b == SAT || sum > LIM) ? SAT : (unsigned long long)sum;
+                }
+                t[(size_t)m * (DIST_MAXR + 1) + j] = v;
+            }
+        return t;
+    }();
+    return tab[(size_t)n * (DIST_MAXR + 1) + k];
 }
 
 static unsigned long long upow3(int e) {

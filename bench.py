@@ -596,21 +596,27 @@ def run_ours(args):
         all_cw = float(total_cw)
     value = all_cw / total_s
 
-    # end to end through the public API with host buffers: init (host generator
-    # -> planner -> table upload) + solve + result read-back, every step
+    # end to end through the C-ABI calls with host buffers: dist_init (host
+    # generator -> planner; the tables travel with the first solve's upload) +
+    # dist_solve (uploads, launches, result read-back) + dist_free, every step
     e2e_s, e2e_cw, e2e_init, e2e_solve = [], [], [], []
+    d_dev = ds[0]
+    g_host = np.ascontiguousarray(g, dtype=np.uint8)
+    n_e2e, K_e2e = (g_host.shape[1] // 2 if field == dist.DIST_F2 else g_host.shape[1]), g_host.shape[0]
     for _ in range(max(3, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c2 = dist.Code(g, field)
+        h2 = dist.dist_init(g_host, n_e2e, K_e2e, field)
         t1 = time.perf_counter()
-        r2 = c2.solve(stream=stream)
+        r2 = dist.dist_solve(h2, stream=stream)
         t2 = time.perf_counter()
-        c2.close()
+        dist.dist_free(h2)
         e2e_s.append(time.perf_counter() - t0)
         e2e_init.append(t1 - t0)
         e2e_solve.append(t2 - t1)
-        e2e_cw.append(r2["codewords"])
+        e2e_cw.append(r2.codewords)
+        if r2.d != d_dev:
+            raise RuntimeError(f"end-to-end solve gave d = {r2.d}, the device-resident one {d_dev}")
     e2e_value = sum(e2e_cw) / sum(e2e_s)
     # the same certified distance by the isometry method (Algorithm 3) on the
     # GPU: the work per certified d of the two algorithms, outside the timed

@@ -36,6 +36,19 @@ std::mutex g_dev_mu;
 DeviceCtx g_dev[64];
 }  // namespace
 
+// Copies a code's tables to the device if they are not there yet (a copy
+// from pageable memory may return before its DMA lands, and the solves run
+// on non-blocking streams, so it waits for the copy).
+int upload_tables(dist_code* c) {
+    if (c->tables_on_device) return DIST_OK;
+    if (cudaMemcpy(c->d_tables, c->plan.tables.data(), c->plan.tables.size() * 4, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess)
+        return DIST_ECUDA;
+    c->tables_on_device = true;
+    return DIST_OK;
+}
+
 int map_plan_rc(int rc) {
     switch (rc) {
         case P_OK: return DIST_OK;
@@ -108,7 +121,7 @@ int kit_acquire(DeviceCtx* d, SolveKit** out) {
         kit_destroy(k);
         return DIST_ECUDA;
     }
-    if (cudaMallocHost(&k->h_state, state_bytes()) != cudaSuccess) {
+    if (cudaMallocHost(&k->h_state, state_bytes() + kKitTableBytes) != cudaSuccess) {
         k->h_state = nullptr;
         kit_destroy(k);
         return DIST_ENOMEM;
@@ -227,6 +240,13 @@ struct GpuExec {
         const int grid = (int)(want < cap ? want : cap);
         const size_t seg_bytes = lp.segs.size() * sizeof(SegDesc);
         memcpy(hsegs(), lp.segs.data(), seg_bytes);
+        if (!c->tables_on_device) {  // the code's first solve: its tables, staged in the kit
+            const size_t tb = c->plan.tables.size() * 4;
+            unsigned char* h_tab = kit->h_state + state_bytes();
+            memcpy(h_tab, c->plan.tables.data(), tb);
+            if (cudaMemcpyAsync(c->d_tables, h_tab, tb, cudaMemcpyHostToDevice, st) != cudaSuccess) return DIST_ECUDA;
+            c->tables_on_device = true;
+        }
         if (first) {  // scratch image (next_chunk = 0) and segment table in one copy
             if (cudaMemcpyAsync(c->d_scr, kit->h_state, align256(sizeof(Scratch)) + seg_bytes,
                                 cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -256,18 +276,6 @@ struct GpuExec {
         if (w > DIST_MAXN) return DIST_EINTERNAL;
         *s = hs()->slot[w];  // read back with the last launch (or the seed itself)
         return DIST_OK;
-    }
-};
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
 
@@ -303,12 +311,14 @@ int dist_init(dist_code** out, const uint8_t* generator, int n, int K, int field
     c->d_tables = static_cast<uint32_t*>(c->d_block);
     c->d_scr = reinterpret_cast<Scratch*>(static_cast<unsigned char*>(c->d_block) + tbytes);
     c->d_segs = reinterpret_cast<SegDesc*>(reinterpret_cast<unsigned char*>(c->d_scr) + align256(sizeof(Scratch)));
-    // A copy from pageable memory may return before its DMA lands; the
-    // solves run on non-blocking streams, so wait for it here.
-    if (cudaMemcpy(c->d_tables, c->plan.tables.data(), words * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
-        release(c);
-        return DIST_ECUDA;
+    // Small tables go to the device with the first solve (one copy fewer
+    // here); larger ones now.
+    if (words * 4 > kKitTableBytes) {
+        const int urc = upload_tables(c);
+        if (urc) {
+            release(c);
+            return urc;
+        }
     }
     *out = c;
     return DIST_OK;

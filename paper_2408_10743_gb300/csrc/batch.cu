@@ -502,6 +502,13 @@ int dist_batch_create(dist_batch** out, const dist_batch_opts* opts) {
 
 int dist_batch_submit(dist_batch* b, dist_code* const* codes, int count, uint64_t* ticket) {
     if (!b || !codes || count < 1 || !ticket) return DIST_EINVAL;
+    // the multi-code kernel reads every code's tables from the device
+    for (int i = 0; i < count; i++)
+        if (codes[i] && !codes[i]->in_batch && codes[i]->dev == b->dev) {
+            DeviceGuard g(b->dev->device);
+            const int rc = upload_tables(codes[i]);
+            if (rc) return rc;
+        }
     std::lock_guard<std::mutex> lk(b->mu);
     if (b->fatal) return b->fatal;
     for (int i = 0; i < count; i++) {

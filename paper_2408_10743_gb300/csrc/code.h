@@ -53,8 +53,27 @@ void block_release(DeviceCtx* d, void* p, size_t cap);
 // segment table of the current single-code launch.
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 inline size_t state_bytes() { return align256(sizeof(Scratch)) + DIST_MAXSEG * sizeof(SegDesc); }
+// Tables of at most this many bytes go to the device with a code's first
+// solve, staged in the solve kit behind its scratch image, instead of by a
+// separate synchronous copy in dist_init.
+constexpr size_t kKitTableBytes = 64 * 1024;
 
 int map_plan_rc(int rc);
+// Copies c's tables to the device unless they are there already (synchronous).
+int upload_tables(dist_code* c);
+
+// Makes a device current for a scope and restores the previous one.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace dist
 
@@ -68,5 +87,6 @@ struct dist_code {
     uint32_t* d_tables = nullptr;             // Plan::tables on the device
     Scratch* d_scr = nullptr;                 // bound, counters, witness slots
     SegDesc* d_segs = nullptr;                // segment table of the current launch (after d_scr)
+    bool tables_on_device = false;            // Plan::tables copied to d_tables
     int in_batch = 0;                         // owned by a batch ticket until it completes
 };

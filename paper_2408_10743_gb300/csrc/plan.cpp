@@ -7,6 +7,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <thread>
 
 namespace dist {
 
@@ -789,8 +793,9 @@ static int random_code_d(const Plan& p) {
     return n;
 }
 
-static int diagonalize(Plan* p, const std::vector<int>& qorder, int d_random, double* work,
-                       int known_w = DIST_WINF, const Vec* known_v = nullptr, const Coef* known_k = nullptr) {
+// S2 proper: the generator matrices of p's basis on disjoint qubit sets,
+// visiting the qubits in qorder.
+static int build_matrices(Plan* p, const std::vector<int>& qorder) {
     const int n = p->n, field = p->field;
     p->gammas.clear();
     std::vector<char> used(n, 0);
@@ -813,6 +818,14 @@ static int diagonalize(Plan* p, const std::vector<int>& qorder, int d_random, do
         p->gammas.push_back(std::move(G));
     }
     if (p->gammas.empty()) return P_EZERO;
+    return P_OK;
+}
+
+// The rest of a plan once its matrices are built: the seed of the upper
+// bound (the lightest representative, or a lighter codeword known from
+// another plan), the estimate of d and the choice of J.
+static int finish_plan(Plan* p, int d_random, double* work, int known_w = DIST_WINF, const Vec* known_v = nullptr,
+                       const Coef* known_k = nullptr) {
     // The lightest representative is a codeword: it seeds the upper bound.
     p->u0 = DIST_WINF;
     lightest_rep(*p, false, &p->u0, &p->u0_slot);
@@ -829,6 +842,93 @@ static int diagonalize(Plan* p, const std::vector<int>& qorder, int d_random, do
     *work = choose_J(p);
     return P_OK;
 }
+
+static int diagonalize(Plan* p, const std::vector<int>& qorder, int d_random, double* work) {
+    const int rc = build_matrices(p, qorder);
+    return rc ? rc : finish_plan(p, d_random, work);
+}
+
+namespace {
+
+// One persistent helper thread, so that plan_build can build the first
+// search trial's matrices while the index-order plan is built (a thread
+// started per call would cost about as much as the overlap saves).  A caller
+// that finds it busy does the work itself.
+class Helper {
+   public:
+    bool try_run(std::function<void()> job) {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (busy_) return false;
+        job_ = std::move(job);
+        busy_ = true;
+        cv_.notify_one();
+        return true;
+    }
+    void wait() {
+        std::unique_lock<std::mutex> lk(mu_);
+        done_.wait(lk, [this] { return !busy_; });
+    }
+    static Helper& get() {
+        static Helper* h = new Helper();  // never destroyed: its thread runs until exit
+        return *h;
+    }
+
+   private:
+    Helper() { std::thread([this] { loop(); }).detach(); }
+    void loop() {
+        for (;;) {
+            std::function<void()> job;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [this] { return busy_ && job_; });
+                job = std::move(job_);
+                job_ = nullptr;
+            }
+            job();
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                busy_ = false;
+            }
+            done_.notify_all();
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    std::function<void()> job_;
+    bool busy_ = false;
+};
+
+// Fisher-Yates with xorshift64* on qorder, advancing the generator x.
+void shuffle_order(std::vector<int>& qorder, uint64_t& x) {
+    for (int q = (int)qorder.size() - 1; q > 0; q--) {
+        x ^= x >> 12;
+        x ^= x << 25;
+        x ^= x >> 27;
+        const int j = (int)(((x * 0x2545F4914F6CDD1Dull) >> 33) % (uint64_t)(q + 1));
+        std::swap(qorder[q], qorder[j]);
+    }
+}
+
+// A plan on p's basis with no matrices yet.
+Plan empty_like(const Plan& p) {
+    Plan alt;
+    alt.n = p.n;
+    alt.field = p.field;
+    alt.K_in = p.K_in;
+    alt.W = p.W;
+    alt.CW = p.CW;
+    alt.k_eff = p.k_eff;
+    alt.input = p.input;
+    alt.kept = p.kept;
+    alt.basis = p.basis;
+    return alt;
+}
+
+// Codes from this size on (qubits) build the first search trial's matrices
+// beside the index-order plan: large codes are where the search runs.
+constexpr int kSpeculateN = 48;
+
+}  // namespace
 
 int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
     if (!gen || n < 1 || n > DIST_MAXN || K < 1) return P_EINVAL;
@@ -856,36 +956,51 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
     for (int q = 0; q < n; q++) qorder[q] = q;
     double work = 0;
     const int d_random = random_code_d(*p);
-    rc = diagonalize(p, qorder, d_random, &work);
-    if (rc) return rc;
     const int trials = plan_search_trials();
+    // The first trial's qubit order, and its matrices built on the helper
+    // thread while this one plans the index order (its matrices do not
+    // depend on that plan; what does is done below, in the same order as
+    // without the helper, so the result is the same).
+    uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)n * 0x100000001B3ull ^ (uint64_t)K;
+    std::vector<int> qorder1 = qorder;
+    uint64_t x1 = x;
+    shuffle_order(qorder1, x1);
+    Plan alt1;
+    int rc1 = P_EINVAL;
+    bool spec = false;
+    if (trials > 0 && n >= kSpeculateN) {
+        alt1 = empty_like(*p);
+        spec = Helper::get().try_run([&alt1, &qorder1, &rc1] { rc1 = build_matrices(&alt1, qorder1); });
+    }
+    rc = diagonalize(p, qorder, d_random, &work);
+    if (spec) Helper::get().wait();
+    if (rc) return rc;
     if (trials > 0 && work > kSearchWork && free_rows_in_J(*p)) {
         // the lightest codeword seen so far is an upper bound for every plan
         int kw = p->u0;
         Vec kv;
         Coef kk;
         slot_codeword(*p, p->u0_slot, &kv, &kk);
-        uint64_t x = 0x9E3779B97F4A7C15ull ^ (uint64_t)n * 0x100000001B3ull ^ (uint64_t)K;
         for (int t = 0; t < trials && free_rows_in_J(*p); t++) {
-            for (int q = n - 1; q > 0; q--) {  // Fisher-Yates with xorshift64*
-                x ^= x >> 12;
-                x ^= x << 25;
-                x ^= x >> 27;
-                const int j = (int)(((x * 0x2545F4914F6CDD1Dull) >> 33) % (uint64_t)(q + 1));
-                std::swap(qorder[q], qorder[j]);
-            }
             Plan alt;
-            alt.n = p->n;
-            alt.field = p->field;
-            alt.K_in = p->K_in;
-            alt.W = p->W;
-            alt.CW = p->CW;
-            alt.k_eff = p->k_eff;
-            alt.input = p->input;
-            alt.kept = p->kept;
-            alt.basis = p->basis;
+            int rcm;
+            if (t == 0) {
+                qorder = qorder1;
+                x = x1;
+                if (spec) {
+                    alt = std::move(alt1);
+                    rcm = rc1;
+                } else {
+                    alt = empty_like(*p);
+                    rcm = build_matrices(&alt, qorder);
+                }
+            } else {
+                shuffle_order(qorder, x);
+                alt = empty_like(*p);
+                rcm = build_matrices(&alt, qorder);
+            }
             double w2 = 0;
-            if (diagonalize(&alt, qorder, d_random, &w2, kw, &kv, &kk) != P_OK) continue;
+            if (rcm != P_OK || finish_plan(&alt, d_random, &w2, kw, &kv, &kk) != P_OK) continue;
             if (alt.u0 < kw) {  // a lighter representative: the new best seed
                 kw = alt.u0;
                 slot_codeword(alt, alt.u0_slot, &kv, &kk);

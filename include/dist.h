@@ -101,7 +101,7 @@ typedef struct {
     double seconds;       /* host wall time of the call */
     uint8_t witness[256]; /* a codeword of weight d: F2 2n bytes (x | z), F4 n symbols */
     uint8_t coeffs[256];  /* its coefficients over the input rows: F2 bits, F4 symbols */
-    double gpu_seconds;   /* summed CUDA-event time of the enumeration kernels */
+    double gpu_seconds;   /* summed run time of the enumeration kernels (dist_set_event_timing) */
     uint64_t launches;    /* enumeration kernels launched */
 } dist_result;
 
@@ -220,8 +220,10 @@ int dist_batch_destroy(dist_batch *b);
  * clamped; fields <= 0 keep the current value.  dist_autotune times calibration solves (random codes of
  * 64 x 56 and 72 x 72) on the current device over a grid of the three,
  * applies the setting with the best geometric-mean codewords/s (the setting
- * in force stays unless another is at least 2 % faster), and returns it (and
- * that rate) -- about budget_s seconds (<= 0: about 10 s).
+ * in force stays unless another is at least 2 % faster; a setting that cuts
+ * every launch of the codes exactly as one already timed is not timed
+ * again), and returns it (and that rate) -- about budget_s seconds (<= 0:
+ * about 10 s).
  */
 typedef struct {
     int32_t chunks_per_warp;
@@ -256,6 +258,17 @@ int dist_get_plan_search(void);
  */
 int dist_set_gamma_limit(int m);
 int dist_get_gamma_limit(void);
+/*
+ * How gpu_seconds of dist_solve, dist_solve_bounded and dist_solve_noalloc
+ * is measured (process-wide).  0 (the default): by the enumeration kernel
+ * itself, from the earliest block start to the latest warp end of each
+ * launch (%globaltimer, 32 ns steps), at no cost.  1: by CUDA events
+ * recorded on the solve's stream around each launch (not for
+ * dist_solve_noalloc, which creates no events); a timed event pair adds
+ * about 11 us to each launch on a GB300.  Never affects results.
+ */
+int dist_set_event_timing(int on);
+int dist_get_event_timing(void);
 
 /*
  * dist_plan_info -- host-only view of the plan step S2-S3 built for an input
@@ -339,7 +352,7 @@ int dist_intpeak(dist_intpeak_result *out, int iters, void *cuda_stream);
  * planning uses ordinary heap memory.  All calls share the array and each
  * clears what must start at zero, so calls whose GPU work overlaps (other
  * streams, other host threads) race: serialize them.  gpu_seconds in the
- * result is 0 (no events are created).
+ * result is the kernels' own run time (no events are created).
  */
 #define DIST_NOALLOC_MAX_BYTES 65536
 int dist_solve_noalloc(const uint8_t *generator, int n, int K, int field, int n_stab,

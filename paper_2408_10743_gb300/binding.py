@@ -112,6 +112,8 @@ SIGNATURES = {
     "dist_get_plan_search": (ctypes.c_int, []),
     "dist_set_gamma_limit": (ctypes.c_int, [ctypes.c_int]),
     "dist_get_gamma_limit": (ctypes.c_int, []),
+    "dist_set_event_timing": (ctypes.c_int, [ctypes.c_int]),
+    "dist_get_event_timing": (ctypes.c_int, []),
     "dist_autotune_codes": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_double,
                                            ctypes.POINTER(Tuning)]),
     "dist_version": (ctypes.c_char_p, []),
@@ -341,6 +343,14 @@ def dist_set_gamma_limit(m):
 
 def dist_get_gamma_limit() -> int:
     return lib().dist_get_gamma_limit()
+
+
+def dist_set_event_timing(on):
+    return _check(lib().dist_set_event_timing(1 if on else 0), "dist_set_event_timing")
+
+
+def dist_get_event_timing() -> int:
+    return lib().dist_get_event_timing()
 
 
 def dist_get_tuning() -> dict:

@@ -2,6 +2,8 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <cmath>
@@ -39,6 +41,8 @@ DeviceCtx g_dev[64];
 // Copies a code's tables to the device if they are not there yet (a copy
 // from pageable memory may return before its DMA lands, and the solves run
 // on non-blocking streams, so it waits for the copy).
+std::atomic<int> g_event_timing{0};
+
 int upload_tables(dist_code* c) {
     if (c->tables_on_device) return DIST_OK;
     if (cudaMemcpy(c->d_tables, c->plan.tables.data(), c->plan.tables.size() * 4, cudaMemcpyHostToDevice) !=
@@ -200,8 +204,11 @@ struct GpuExec {
     double gpu_s = 0.0;
     unsigned long long nl = 0;
     bool first = true;  // the next launch uploads the scratch image too
-    Scratch* hs() const { return reinterpret_cast<Scratch*>(kit->h_state); }
-    SegDesc* hsegs() const { return reinterpret_cast<SegDesc*>(kit->h_state + align256(sizeof(Scratch))); }
+    // kit staging: [table staging (kKitTableBytes) | scratch image | segment table]
+    Scratch* hs() const { return reinterpret_cast<Scratch*>(kit->h_state + kKitTableBytes); }
+    SegDesc* hsegs() const {
+        return reinterpret_cast<SegDesc*>(kit->h_state + kKitTableBytes + align256(sizeof(Scratch)));
+    }
     int reset() {
         memset(hs(), 0, sizeof(Scratch));
         hs()->U = DIST_WINF;
@@ -221,6 +228,7 @@ struct GpuExec {
         plan_params(c->plan, lp, &ep);
         // U already at the random-code estimate of d: certification work
         ep.first_static = hs()->U <= (uint32_t)c->plan.d_est ? 1 : 0;
+        ep.two_word = enum_two_word(ep, hs()->U);
         ep.tables = c->d_tables;
         ep.segs = c->d_segs;
         ep.binom = c->dev->d_binom;
@@ -240,33 +248,47 @@ struct GpuExec {
         const int grid = (int)(want < cap ? want : cap);
         const size_t seg_bytes = lp.segs.size() * sizeof(SegDesc);
         memcpy(hsegs(), lp.segs.data(), seg_bytes);
-        if (!c->tables_on_device) {  // the code's first solve: its tables, staged in the kit
-            const size_t tb = c->plan.tables.size() * 4;
-            unsigned char* h_tab = kit->h_state + state_bytes();
-            memcpy(h_tab, c->plan.tables.data(), tb);
-            if (cudaMemcpyAsync(c->d_tables, h_tab, tb, cudaMemcpyHostToDevice, st) != cudaSuccess) return DIST_ECUDA;
+        if (first) {
+            // scratch image (next_chunk = 0) and segment table in one copy;
+            // on the code's first solve its tables ride ahead of them, staged
+            // so that the staging holds tables | scratch | segments at the
+            // offsets the device block has them
+            unsigned char* src = reinterpret_cast<unsigned char*>(hs());
+            unsigned char* dst = reinterpret_cast<unsigned char*>(c->d_scr);
+            size_t bytes = align256(sizeof(Scratch)) + seg_bytes;
+            if (!c->tables_on_device) {  // at most kKitTableBytes (dist_init uploads larger ones)
+                const size_t tb = align256(c->plan.tables.size() * 4);  // offset of d_scr in the block
+                src -= tb;
+                memcpy(src, c->plan.tables.data(), c->plan.tables.size() * 4);
+                dst = static_cast<unsigned char*>(c->d_block);
+                bytes += tb;
+            }
+            if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return DIST_ECUDA;
             c->tables_on_device = true;
-        }
-        if (first) {  // scratch image (next_chunk = 0) and segment table in one copy
-            if (cudaMemcpyAsync(c->d_scr, kit->h_state, align256(sizeof(Scratch)) + seg_bytes,
-                                cudaMemcpyHostToDevice, st) != cudaSuccess)
-                return DIST_ECUDA;
             first = false;
         } else {
             if (cudaMemcpyAsync(c->d_segs, hsegs(), seg_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-                cudaMemsetAsync(&c->d_scr->next_chunk, 0, sizeof(unsigned long long), st) != cudaSuccess)
+                cudaMemsetAsync(&c->d_scr->next_chunk, 0, DIST_SCR_LAUNCH_RESET, st) != cudaSuccess)
                 return DIST_ECUDA;
         }
-        cudaEventRecord(kit->e0, st);
+        // CUDA events around the launch only when asked for: each timed
+        // event adds about 11 us to a launch; the kernel stamps its own run
+        // time either way
+        const bool events = g_event_timing.load(std::memory_order_relaxed) != 0;
+        if (events) cudaEventRecord(kit->e0, st);
         if (enum_launch(ep, grid, st) != cudaSuccess) return DIST_ECUDA;
-        cudaEventRecord(kit->e1, st);
+        if (events) cudaEventRecord(kit->e1, st);
         nl++;
         if (cudaMemcpyAsync(hs(), c->d_scr, sizeof(Scratch), cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return DIST_ECUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return DIST_ECUDA;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, kit->e0, kit->e1);
-        gpu_s += ms * 1e-3;
+        if (events) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, kit->e0, kit->e1);
+            gpu_s += ms * 1e-3;
+        } else {
+            gpu_s += scratch_kernel_seconds(*hs());
+        }
         out->U = hs()->U;
         out->status = hs()->status;
         out->codewords = hs()->codewords;
@@ -478,6 +500,13 @@ int dist_set_gamma_limit(int m) {
 
 int dist_get_gamma_limit(void) { return plan_gamma_limit(); }
 
+int dist_set_event_timing(int on) {
+    g_event_timing.store(on ? 1 : 0);
+    return DIST_OK;
+}
+
+int dist_get_event_timing(void) { return g_event_timing.load(); }
+
 int dist_get_tuning(dist_tuning* t) {
     if (!t) return DIST_EINVAL;
     const Tuning cur = tuning_get();
@@ -493,9 +522,40 @@ int dist_get_tuning(dist_tuning* t) {
 // kernels' CUDA events for each setting of the grid; best median rate wins.
 namespace {
 
+// Digest of the launches a solve of c would make under the tuning in force
+// if U stayed at its seed: the round loop's plan_launch sequence, segment
+// tables and chunk counts.  Two settings with the same digest cut every
+// launch the same way (U only decides where a solve stops), so only one of
+// them needs timing.
+unsigned long long launch_sequence_digest(const dist_code* c) {
+    const Plan& p = c->plan;
+    unsigned long long h = 1469598103934665603ull;
+    auto put = [&h](const void* d, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(d);
+        for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    const int ub = seed_bound(p);
+    const int warps = c->dev->sms * c->dev->blocks_per_sm * DIST_ENUM_WARPS;
+    int r = 1, jpos = 0, L = plan_initial_bound(p);
+    for (int launch = 0; launch < 64; launch++) {
+        LaunchPlan lp;
+        const int rc = plan_launch(p, r, jpos, L, ub, warps, kLaunchCodewords, &lp);
+        put(&rc, sizeof rc);
+        if (rc) break;
+        put(&lp.nchunks, sizeof lp.nchunks);
+        for (const SegDesc& sg : lp.segs) put(&sg, sizeof sg);
+        L = plan_lower_bound(p, lp.step_r.back(), lp.step_jpos.back());
+        if (L == (int)DIST_WINF || (ub < (int)DIST_WINF && L >= ub)) break;
+        r = lp.next_r;
+        jpos = lp.next_jpos;
+    }
+    return h;
+}
+
 // Times two solves of every code per setting of the grid (the second one
 // counts) and applies the setting with the best geometric-mean codewords/s,
-// the setting in force winning unless another is 2 % faster.
+// the setting in force winning unless another is 2 % faster.  A setting
+// whose launches are those of a setting already timed is not timed again.
 int autotune_on(const std::vector<dist_code*>& codes, double budget_s, dist_tuning* best) {
     const Tuning saved = tuning_get();
     // the setting in force is timed first and kept unless another one is
@@ -514,9 +574,14 @@ int autotune_on(const std::vector<dist_code*>& codes, double budget_s, dist_tuni
     double best_rate = -1;
     Tuning best_t = saved;
     const double t0 = wall_now();
+    std::vector<std::vector<unsigned long long>> seen;
     for (const Tuning& t : grid) {
         if (wall_now() - t0 > budget_s) break;
         tuning_set(t);
+        std::vector<unsigned long long> sig;
+        for (dist_code* c : codes) sig.push_back(launch_sequence_digest(c));
+        if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+        seen.push_back(sig);
         // geometric mean of the per-code rates: a short solve weighs as much
         // as a long one
         double log_rate = 0;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -59,6 +60,8 @@ inline size_t state_bytes() { return align256(sizeof(Scratch)) + DIST_MAXSEG * s
 constexpr size_t kKitTableBytes = 64 * 1024;
 
 int map_plan_rc(int rc);
+// Per-launch CUDA-event timing of single-code solves (dist_set_event_timing).
+extern std::atomic<int> g_event_timing;
 // Copies c's tables to the device unless they are there already (synchronous).
 int upload_tables(dist_code* c);
 

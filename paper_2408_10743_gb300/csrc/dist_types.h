@@ -52,15 +52,29 @@ struct WitnessSlot {
 };
 
 // Device-side state of one solve.  U is the running upper bound (atomicMin),
-// next_chunk the work counter of the current launch.
+// next_chunk the work counter of the current launch.  The single-code kernel
+// also stamps its own run time (%globaltimer, ns): the complement of its
+// earliest block start (kept by atomicMax, so that zero is the reset value)
+// and its latest warp end.  next_chunk and the two stamps are reset together
+// before every launch after the first.
 struct Scratch {
     uint32_t U;
     uint32_t status;              // bit 1: time budget spent
     unsigned long long next_chunk;
+    unsigned long long t_first_inv;
+    unsigned long long t_last;
     unsigned long long codewords; // (subset, representative) combinations evaluated
     unsigned long long pad;
     WitnessSlot slot[DIST_MAXN + 1];
 };
+// Bytes from next_chunk to the end of the stamps (zeroed before a launch).
+#define DIST_SCR_LAUNCH_RESET (3 * sizeof(unsigned long long))
+// Kernel run time of the last launch from its stamps, seconds (0 if unset).
+inline double scratch_kernel_seconds(const Scratch& s) {
+    if (s.t_last == 0 || s.t_first_inv == 0) return 0.0;
+    const unsigned long long t0 = ~s.t_first_inv;
+    return s.t_last > t0 ? 1e-9 * (double)(s.t_last - t0) : 0.0;
+}
 
 // A generator matrix as one launch sees it.
 struct GammaDesc {
@@ -76,6 +90,8 @@ struct GammaDesc {
     uint16_t a, b;        // A-units (three representatives), B-units (one)
     int32_t gamma;        // index in the plan (witness decoding)
     int32_t t1;           // use the two-word filter when thr - P exceeds this
+    uint32_t a_all;       // AND of the A-units' pivot flags
+    uint32_t pad;
 };
 
 // A segment: within one step (round r of one generator matrix), the
@@ -110,8 +126,19 @@ struct EnumParams {
     unsigned long long nchunks;
     unsigned long long budget_ns;       // stop after this long (per block, %globaltimer); 0 = none
     int first_static;                   // 1: the first wave of chunks goes by warp index
+    int two_word;                       // 0: the bound at the launch cannot reach the two-word filter
     GammaDesc g[DIST_MAXGAMMA];
 };
+
+// Whether a launch that starts with upper bound U can take the two-word
+// filter: a lane takes it when thr - P > t1 for its matrix, with thr <= U
+// and P >= 0 throughout the launch.
+inline int enum_two_word(const EnumParams& P, uint32_t U) {
+    if (P.W < 2) return 0;
+    for (int g = 0; g < P.ng; g++)
+        if ((long long)U > (long long)P.g[g].t1) return 1;
+    return 0;
+}
 
 // One code in a multi-code launch.
 struct BatchCode {

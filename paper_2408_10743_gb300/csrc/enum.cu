@@ -66,8 +66,10 @@ __device__ __forceinline__ void cp_async8(void* s, const void* g) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+template <bool kTwo>
 __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel(const __grid_constant__ EnumParams P) {
     uint32_t* sm = g_enum_smem;
+    if (threadIdx.x == 0) atomicMax(&P.scr->t_first_inv, ~global_ns());
     // Per-matrix lane context, read by reference from shared memory so that
     // none of it stays in registers across the inner loop.
     __shared__ LaneCtx s_ctx[DIST_MAXGAMMA];
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         C.r1 = reinterpret_cast<const U2*>(sm + g.s_r1);
         C.flags = sm + g.s_flag;
         C.t1 = g.t1;
+        C.a_all = g.a_all;
         C.coefs = P.tables + g.coef_off;
         C.binom = sbin;
         C.bstride = P.bcols;
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         }
         const LaneCtx& C = s_ctx[sg.g];
         unsigned long long lo, hi;
-        if (seg_lane_range(sg, chunk, lane, lo, hi)) done += walk_range(C, sink, thr, sg, lo, hi, u_now);
+        if (seg_lane_range(sg, chunk, lane, lo, hi)) done += walk_range<DevSink, kTwo>(C, sink, thr, sg, lo, hi, u_now);
         if (P.budget_ns) {
             int stop = 0;
             if (lane == 0 && global_ns() - t_start > P.budget_ns) {
@@ -186,7 +189,10 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
-    if (lane == 0 && done) atomicAdd(&P.scr->codewords, done);
+    if (lane == 0) {
+        if (done) atomicAdd(&P.scr->codewords, done);
+        atomicMax(&P.scr->t_last, global_ns());
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -309,6 +315,7 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB)
             C.r1 = reinterpret_cast<const U2*>(bc.tables + g.r1_off);
             C.flags = bc.tables + g.flag_off;
             C.t1 = g.t1;
+            C.a_all = g.a_all;
             C.coefs = bc.tables + g.coef_off;
             C.binom = P.binom;
             C.bstride = DIST_MAXR + 1;
@@ -441,27 +448,39 @@ int batch_blocks_per_sm() {
 
 size_t enum_smem_bytes(const EnumParams& P) { return (size_t)P.s_words * 4; }
 
+// Both instances of the kernel: the occupancy and shared-memory limits are
+// those of the more demanding one.
 int enum_blocks_per_sm(size_t smem) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, enum_kernel, DIST_ENUM_THREADS, smem) != cudaSuccess)
+    int n1 = 0, n2 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, enum_kernel<false>, DIST_ENUM_THREADS, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, enum_kernel<true>, DIST_ENUM_THREADS, smem) != cudaSuccess)
         return 0;
-    return nb;
+    return n1 < n2 ? n1 : n2;
 }
 
 // Largest dynamic shared memory a launch may ask for: the per-block opt-in
 // limit less the kernel's static shared memory (the lane contexts).
 size_t enum_max_dynamic_smem(size_t optin) {
-    cudaFuncAttributes a;
-    if (cudaFuncGetAttributes(&a, enum_kernel) != cudaSuccess || a.sharedSizeBytes >= optin) return 0;
-    return optin - a.sharedSizeBytes;
+    cudaFuncAttributes a1, a2;
+    if (cudaFuncGetAttributes(&a1, enum_kernel<false>) != cudaSuccess ||
+        cudaFuncGetAttributes(&a2, enum_kernel<true>) != cudaSuccess)
+        return 0;
+    const size_t st = a1.sharedSizeBytes > a2.sharedSizeBytes ? a1.sharedSizeBytes : a2.sharedSizeBytes;
+    return st >= optin ? 0 : optin - st;
 }
 
 cudaError_t enum_set_max_smem(size_t bytes) {
-    return cudaFuncSetAttribute(enum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const cudaError_t e = cudaFuncSetAttribute(enum_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(enum_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 cudaError_t enum_launch(const EnumParams& P, int grid, cudaStream_t st) {
-    enum_kernel<<<grid, DIST_ENUM_THREADS, enum_smem_bytes(P), st>>>(P);
+    if (P.two_word)
+        enum_kernel<true><<<grid, DIST_ENUM_THREADS, enum_smem_bytes(P), st>>>(P);
+    else
+        enum_kernel<false><<<grid, DIST_ENUM_THREADS, enum_smem_bytes(P), st>>>(P);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 // that must start at zero, and two calls whose work overlaps on the GPU
 // (different streams, or different host threads) race on it.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <mutex>
@@ -123,7 +124,8 @@ struct NoAllocExec {
         return DIST_OK;
     }
     int target_warps() const { return d->sms * d->blocks_per_sm * DIST_ENUM_WARPS; }
-    double gpu_seconds() const { return 0.0; }
+    double gpu_s = 0.0;
+    double gpu_seconds() const { return gpu_s; }
     unsigned long long launches() const { return nl; }
     int run(const LaunchPlan& lp, double deadline_wall, StepResult* out) {
         EnumParams ep;
@@ -135,6 +137,7 @@ struct NoAllocExec {
         // U already at the random-code estimate of d: certification work
         // (the same first-wave rule as dist_solve)
         ep.first_static = U_host <= (uint32_t)p.d_est ? 1 : 0;
+        ep.two_word = enum_two_word(ep, U_host);
         if (deadline_wall > 0) {
             double left = deadline_wall - wall_now();
             ep.budget_ns = left > 1e-3 ? (unsigned long long)(left * 1e9) : 1000000ull;
@@ -148,22 +151,22 @@ struct NoAllocExec {
         if (want < 1) want = 1;
         const unsigned long long cap = (unsigned long long)d->sms * (unsigned long long)bps;
         const int grid = (int)(want < cap ? want : cap);
-        unsigned long long zero = 0;
         if (cudaMemcpyAsync(d->base + L.segs, lp.segs.data(), lp.segs.size() * sizeof(SegDesc),
                             cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(&scr()->next_chunk, &zero, sizeof zero, cudaMemcpyHostToDevice, st) !=
-                cudaSuccess)
+            cudaMemsetAsync(&scr()->next_chunk, 0, DIST_SCR_LAUNCH_RESET, st) != cudaSuccess)
             return DIST_ECUDA;
         if (enum_launch(ep, grid, st) != cudaSuccess) return DIST_ECUDA;
         nl++;
-        unsigned long long hdr[4];
-        if (cudaMemcpyAsync(hdr, scr(), sizeof hdr, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        // the fields before the witness slots: bound, status, stamps, count
+        Scratch head;
+        if (cudaMemcpyAsync(&head, scr(), offsetof(Scratch, slot), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             return DIST_ECUDA;
-        out->U = (uint32_t)(hdr[0] & 0xFFFFFFFFu);
+        out->U = head.U;
         U_host = out->U;
-        out->status = (uint32_t)(hdr[0] >> 32);
-        out->codewords = hdr[2];
+        out->status = head.status;
+        out->codewords = head.codewords;
+        gpu_s += scratch_kernel_seconds(head);
         return DIST_OK;
     }
     int read_slot(uint32_t w, WitnessSlot* s) {

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <functional>
 #include <mutex>
@@ -526,6 +527,7 @@ static void diag_f4(const Plan& p, const std::vector<int>& qorder, std::vector<c
 // NOT pivots of this matrix come first (they fill word 0 of each plane, the
 // word the enumeration filters on), pivots after them.
 static void build_device_tables(const Plan& p, Gamma& G) {
+    G.tables_built = true;
     std::vector<char> isp(p.n, 0);
     for (int q : G.pivots) isp[q] = 1;
     G.perm.clear();
@@ -545,6 +547,8 @@ static void build_device_tables(const Plan& p, Gamma& G) {
         if (x.qubit >= 0 && pos_of[x.qubit] >= 32) G.dev_flags[t] |= 1u;
         if (x.qubit >= 0 && pos_of[x.qubit] >= 64) G.dev_flags[t] |= 2u;
     }
+    G.a_all = 3u;
+    for (size_t t = 0; t < G.A.size(); t++) G.a_all &= G.dev_flags[t];
     G.dev_r0.assign(G.A.size() * 6, 0);
     G.dev_r1.assign(G.A.size() * 6, 0);
     // The qubit permutation as nibble tables: entry (N, v) is the 128-bit
@@ -853,20 +857,26 @@ namespace {
 // One persistent helper thread, so that plan_build can build the first
 // search trial's matrices while the index-order plan is built (a thread
 // started per call would cost about as much as the overlap saves).  A caller
-// that finds it busy does the work itself.
+// that finds it busy does the work itself.  Waking a sleeping thread takes
+// from a few to tens of microseconds, as long as the job itself, so both
+// sides spin for a short while before they sleep: the helper for kIdleSpin
+// after each job (the next plan_build of a stream of codes then finds it
+// awake), the caller for kWaitSpin in wait().
 class Helper {
    public:
     bool try_run(std::function<void()> job) {
         std::lock_guard<std::mutex> lk(mu_);
-        if (busy_) return false;
+        if (busy_.load(std::memory_order_relaxed)) return false;
         job_ = std::move(job);
-        busy_ = true;
+        busy_.store(true, std::memory_order_release);
+        pending_.store(true, std::memory_order_release);
         cv_.notify_one();
         return true;
     }
     void wait() {
+        if (spin_until([this] { return !busy_.load(std::memory_order_acquire); }, kWaitSpin)) return;
         std::unique_lock<std::mutex> lk(mu_);
-        done_.wait(lk, [this] { return !busy_; });
+        done_.wait(lk, [this] { return !busy_.load(std::memory_order_acquire); });
     }
     static Helper& get() {
         static Helper* h = new Helper();  // never destroyed: its thread runs until exit
@@ -874,20 +884,34 @@ class Helper {
     }
 
    private:
+    static constexpr double kIdleSpin = 2e-3, kWaitSpin = 2e-3;  // seconds
+    // Polls pred for up to `seconds`; true if it held.
+    template <class Pred>
+    static bool spin_until(Pred pred, double seconds) {
+        const auto t0 = std::chrono::steady_clock::now();
+        for (unsigned it = 0;; it++) {
+            if (pred()) return true;
+            if ((it & 255u) == 255u &&
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > seconds)
+                return false;
+        }
+    }
     Helper() { std::thread([this] { loop(); }).detach(); }
     void loop() {
         for (;;) {
+            spin_until([this] { return pending_.load(std::memory_order_acquire); }, kIdleSpin);
             std::function<void()> job;
             {
                 std::unique_lock<std::mutex> lk(mu_);
-                cv_.wait(lk, [this] { return busy_ && job_; });
+                cv_.wait(lk, [this] { return pending_.load(std::memory_order_relaxed); });
+                pending_.store(false, std::memory_order_relaxed);
                 job = std::move(job_);
                 job_ = nullptr;
             }
             job();
             {
                 std::lock_guard<std::mutex> lk(mu_);
-                busy_ = false;
+                busy_.store(false, std::memory_order_release);
             }
             done_.notify_all();
         }
@@ -895,7 +919,7 @@ class Helper {
     std::mutex mu_;
     std::condition_variable cv_, done_;
     std::function<void()> job_;
-    bool busy_ = false;
+    std::atomic<bool> busy_{false}, pending_{false};
 };
 
 // Fisher-Yates with xorshift64* on qorder, advancing the generator x.
@@ -930,6 +954,32 @@ constexpr int kSpeculateN = 48;
 
 }  // namespace
 
+// Independence of a few rows over F2 (elimination on the lowest set bit).
+static bool rows_independent(std::vector<Vec> rows) {
+    std::vector<int> piv;
+    for (size_t i = 0; i < rows.size(); i++) {
+        Vec& t = rows[i];
+        for (size_t e = 0; e < i; e++) {
+            const int q = piv[e];
+            const int b = q < DIST_MAXN ? bit(t.x, q) : bit(t.z, q - DIST_MAXN);
+            if (b) vxor(t, rows[e]);
+        }
+        int q = -1;
+        for (int w = 0; w < DIST_MAXW && q < 0; w++)
+            if (t.x[w]) q = w * 32 + __builtin_ctz(t.x[w]);
+        for (int w = 0; w < DIST_MAXW && q < 0; w++)
+            if (t.z[w]) q = DIST_MAXN + w * 32 + __builtin_ctz(t.z[w]);
+        if (q < 0) return false;
+        piv.push_back(q);
+    }
+    return true;
+}
+
+// Returned by plan_from_basis when rows it took as independent are not.
+static constexpr int kDependent = 1;
+
+static int plan_from_basis(Plan* p, bool assume_independent);
+
 int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
     if (!gen || n < 1 || n > DIST_MAXN || K < 1) return P_EINVAL;
     if (field != 2 && field != 4) return P_EINVAL;
@@ -942,7 +992,37 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
     p->W = (n + 31) / 32;
     int rc = load_input(gen, n, K, field, p);
     if (rc) return rc;
-    reduce_rank(p);
+    // Over F2 the rows are first taken as they are: the diagonalization shows
+    // whether they are independent (below), and only if they are not does
+    // the plan start again from the rows the elimination keeps.  Both ways
+    // give the same plan for independent rows.
+    if (field == 2 && K <= 2 * n) {
+        rc = plan_from_basis(p, true);
+        if (rc != kDependent) return rc;
+        Plan q;
+        q.n = n;
+        q.field = field;
+        q.K_in = K;
+        q.W = p->W;
+        q.input = std::move(p->input);
+        *p = std::move(q);
+    }
+    return plan_from_basis(p, false);
+}
+
+// plan_build from the loaded input rows on: the basis (all rows, or the
+// independent ones in input order), S2 with the qubit-order search, tables.
+static int plan_from_basis(Plan* p, bool assume_independent) {
+    const int n = p->n, K = p->K_in;
+    int rc;
+    if (assume_independent) {
+        p->kept.resize(K);
+        for (int r = 0; r < K; r++) p->kept[r] = r;
+        p->basis = p->input;
+        p->k_eff = K;
+    } else {
+        reduce_rank(p);
+    }
     if (p->k_eff == 0) return P_EZERO;
     p->CW = (p->k_eff + 31) / 32;
 
@@ -970,10 +1050,25 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
     bool spec = false;
     if (trials > 0 && n >= kSpeculateN) {
         alt1 = empty_like(*p);
-        spec = Helper::get().try_run([&alt1, &qorder1, &rc1] { rc1 = build_matrices(&alt1, qorder1); });
+        // with its device tables: when the trial is needed it is usually kept
+        spec = Helper::get().try_run([&alt1, &qorder1, &rc1] {
+            rc1 = build_matrices(&alt1, qorder1);
+            if (rc1 == P_OK)
+                for (Gamma& G : alt1.gammas) build_device_tables(alt1, G);
+        });
     }
     rc = diagonalize(p, qorder, d_random, &work);
     if (spec) Helper::get().wait();
+    if (assume_independent) {
+        // A combination that uses a package member is nonzero at that
+        // package's pivot (Section 2.2), so the rows are independent exactly
+        // when the first matrix's free rows are.
+        if (rc != P_OK) return kDependent;
+        std::vector<Vec> free_rows;
+        for (const Unit& x : p->gammas[0].B)
+            if (x.kind == UNIT_FREE) free_rows.push_back(x.rep[0]);
+        if (!rows_independent(free_rows)) return kDependent;
+    }
     if (rc) return rc;
     if (trials > 0 && work > kSearchWork && free_rows_in_J(*p)) {
         // the lightest codeword seen so far is an upper bound for every plan
@@ -1011,7 +1106,8 @@ int plan_build(const uint8_t* gen, int n, int K, int field, Plan* p) {
             }
         }
     }
-    for (Gamma& G : p->gammas) build_device_tables(*p, G);
+    for (Gamma& G : p->gammas)
+        if (!G.tables_built) build_device_tables(*p, G);
 
     size_t off = 0;
     for (Gamma& G : p->gammas) {
@@ -1072,6 +1168,14 @@ int plan_set_exclude(Plan* p, int n_stab) {
 // fast-path codewords, for sizing chunks.
 static constexpr double kGenericCost = 32.0;
 
+// Fewest chunks per resident warp that the lane floor may leave a fast-path
+// segment: with about one chunk per warp the warps that drew a chunk late
+// leave the others idle for most of a chunk.  Measured on a launch whose last
+// step is 1.2 chunks per warp at the floor: 1.6 chunks per warp (three
+// subsets of 243 codewords per lane instead of four) ran 5 % faster, 2.4
+// chunks per warp 3 %.
+static constexpr double kSpreadChunks = 1.6;
+
 static void chunk_launch(LaunchPlan* lp, int target_warps) {
     // Chunks: each segment is cut into about chunks_per_warp (default 6)
     // warp-chunks per resident warp, so that every segment spreads over the
@@ -1081,9 +1185,10 @@ static void chunk_launch(LaunchPlan* lp, int target_warps) {
     // A segment on the
     // fast path gets at least 2^lane_floor_log2 codewords per lane, so that it
     // is not cut finer than the per-lane set-up (unranking the start subset,
-    // fetching the chunk) is worth -- but never fewer chunks than resident
-    // warps: the early, small steps are where the lighter codewords that
-    // lower U come from, and they must still spread over the whole GPU.
+    // fetching the chunk) is worth -- but never fewer chunks than
+    // kSpreadChunks per resident warp: the early, small steps are where the
+    // lighter codewords that lower U come from, and they must still spread
+    // over the whole GPU.
     // Generic-path segments cost tens of times more per codeword and keep
     // the plain split, so that they never become the critical path.
     // Outside the launch's last step a fast-path lane chunk holds at least
@@ -1108,7 +1213,7 @@ static void chunk_launch(LaunchPlan* lp, int target_warps) {
         const double seg_cw = (double)sd.NA * (double)sd.NB * (double)sd.codes;
         double per_lane = seg_cw / (32.0 * (double)tw * (double)tun.chunks_per_warp);
         if (DIST_FAST_PATH((int)sd.i, lp->proj)) {
-            const double spread = seg_cw / (32.0 * (double)tw);
+            const double spread = seg_cw / (32.0 * (double)tw * kSpreadChunks);
             per_lane = std::max(per_lane, std::min((double)(1u << tun.lane_floor_log2), spread));
             per_lane = std::min(per_lane, (double)(1u << tun.lane_cap_log2));
         } else {
@@ -1191,6 +1296,7 @@ int plan_launch(const Plan& p, int r, int jpos, int L_prev, int U_bound, int tar
             d.r0_off = G.r0_off;
             d.r1_off = G.r1_off;
             d.t1 = G.t1;
+            d.a_all = G.a_all;
             d.a = (uint16_t)a;
             d.b = (uint16_t)b;
             d.gamma = g;

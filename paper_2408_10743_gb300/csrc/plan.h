@@ -46,11 +46,13 @@ struct Gamma {
     std::vector<int> perm;        // device position p -> original qubit
     std::vector<uint32_t> dev_reps;   // [u][3][2][W], device qubit order
     std::vector<uint32_t> dev_coefs;  // [u][3][2][CW]
+    uint32_t a_all = 0;                 // AND of the A-units' flags
     std::vector<uint32_t> dev_flags;  // [u]: bit 0 package with pivot outside word 0, bit 1 outside words 0-1
     std::vector<uint32_t> dev_r0;     // [a][3][2]: word 0 of the A-units' representatives
     std::vector<uint32_t> dev_r1;     // [a][3][2]: word 1 (zeros if W = 1)
     int t1 = 0;                       // filter switch level (see walk.cuh)
     uint32_t rep_off = 0, coef_off = 0, flag_off = 0, r0_off = 0, r1_off = 0;  // offsets in Plan::tables
+    bool tables_built = false;        // dev_* and perm filled
     int units() const { return (int)(A.size() + B.size()); }
 };
 

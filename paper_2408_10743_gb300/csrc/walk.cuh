@@ -71,24 +71,45 @@ DIST_HD unsigned long long binom_at(const unsigned long long* B, int stride, int
     return B[n * stride + k];
 }
 
-// Largest c in [lo, hi] with C(c, t) <= R (C(lo, t) <= R holds).  The start
-// is the closed-form estimate C(c, t) ~ (c - (t-1)/2)^t / t!, i.e.
-// c ~ (R t!)^(1/t) + (t-1)/2; exact binomial lookups then move it to the
-// answer (one or two steps in practice), so the result does not depend on
-// the floating-point rounding of the estimate.  A lane starting a chunk pays
-// about two dependent table loads per element instead of a bisection's six.
-DIST_HD int cns_top(const unsigned long long* B, int stride, int t, unsigned long long R, int lo, int hi) {
-    int c;
-    if (t == 1) {
-        c = (int)(R < (unsigned long long)hi ? R : (unsigned long long)hi);
-    } else {
-        float fact = 1.0f;
-        for (int k = 2; k <= t; k++) fact *= (float)k;
-        const float x = exp2f((log2f((float)R + 0.5f) + log2f(fact)) / (float)t) + 0.5f * (float)(t - 1);
-        c = x < (float)lo ? lo : (x > (float)hi ? hi : (int)x);
+// The unranking estimate below needs only a few correct bits: the device
+// takes the hardware log2 and reciprocal approximations for it.
+#if defined(__CUDA_ARCH__)
+#define DIST_EST_LOG2(x) __log2f(x)
+#define DIST_EST_RCP(x) __fdividef(1.0f, (x))
+#else
+#define DIST_EST_LOG2(x) log2f(x)
+#define DIST_EST_RCP(x) (1.0f / (x))
+#endif
+
+// Largest c in [lo, hi] with C(c, t) <= R (C(lo, t) <= R holds); C(c + 1, t)
+// goes to *next.  The start is the closed-form estimate C(c, t) ~
+// (c - (t-1)/2)^t / t!, i.e. c ~ (R t!)^(1/t) + (t-1)/2, with lgf = log2(t!);
+// exact binomial lookups then move it to the answer, so the result does not
+// depend on the rounding of the estimate.  C(c, t) and C(c + 1, t) are read
+// together, so an estimate that is already right costs one round trip to the
+// table, and C(c + 1, t) is the value the caller needs next.
+DIST_HD int cns_top(const unsigned long long* B, int stride, int t, unsigned long long R, int lo, int hi,
+                    float lgf, unsigned long long* next) {
+    if (t == 1) {  // C(c, 1) = c
+        const int c = (int)(R < (unsigned long long)hi ? R : (unsigned long long)hi);
+        *next = (unsigned long long)c + 1ull;
+        return c;
     }
-    while (c > lo && binom_at(B, stride, c, t) > R) --c;
-    while (c < hi && binom_at(B, stride, c + 1, t) <= R) ++c;
+    const float x =
+        exp2f((DIST_EST_LOG2((float)R + 0.5f) + lgf) * DIST_EST_RCP((float)t)) + 0.5f * (float)(t - 1);
+    int c = x < (float)lo ? lo : (x > (float)hi ? hi : (int)x);
+    unsigned long long b0 = binom_at(B, stride, c, t), b1 = binom_at(B, stride, c + 1, t);
+    while (c > lo && b0 > R) {
+        --c;
+        b1 = b0;
+        b0 = binom_at(B, stride, c, t);
+    }
+    while (c < hi && b1 <= R) {
+        ++c;
+        b0 = b1;
+        b1 = binom_at(B, stride, c + 1, t);
+    }
+    *next = b1;
     return c;
 }
 
@@ -98,11 +119,15 @@ DIST_HD int cns_top(const unsigned long long* B, int stride, int t, unsigned lon
 // of {0..c_t - 1}.
 DIST_HD void rd_unrank(const unsigned long long* B, int stride, int n, unsigned long long R, int t,
                        uint8_t* s) {
+    float lgf = 0.0f;  // log2(tt!) for the estimate
+    for (int k = 2; k <= t; k++) lgf += DIST_EST_LOG2((float)k);
     for (int tt = t; tt >= 1; --tt) {
-        const int c = cns_top(B, stride, tt, R, tt - 1, n - 1);
+        unsigned long long nx;
+        const int c = cns_top(B, stride, tt, R, tt - 1, n - 1, lgf, &nx);
         s[tt - 1] = (uint8_t)c;
-        R = binom_at(B, stride, c + 1, tt) - 1 - R;
+        R = nx - 1 - R;
         n = c;
+        lgf -= DIST_EST_LOG2((float)tt);
     }
 }
 
@@ -159,6 +184,7 @@ struct LaneCtx {
     int bstride;
     int a, b, W, CW, gamma, proj, exclude;
     int t1;                            // two-word filter when thr - P exceeds this
+    uint32_t a_all;                    // AND of the A-units' flags: bit set = every A-unit has it
 };
 
 DIST_HD const uint32_t* rep_ptr(const LaneCtx& C, int unit, int e, int plane) {
@@ -512,8 +538,11 @@ DIST_HD bool seg_lane_range(const SegDesc& sg, unsigned long long chunk, int lan
 // record(...) and vote_any(p) (true if p holds on any lane running in step
 // with this one).  u_first is a recent value of U the caller already holds,
 // taken as the bound of the first subset, so that the lane does not wait for
-// a fresh read before its first subset.
-template <class Sink>
+// a fresh read before its first subset.  kTwo = false leaves out the two-word
+// filter; a launch whose bound can never reach it (U - P <= t1 from the
+// start) runs that instance, which needs fewer registers.  Either filter is
+// a lower bound on the weight, so the instance changes no result.
+template <class Sink, bool kTwo = true>
 DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& thr, const SegDesc& sg,
                                       unsigned long long lo, unsigned long long hi, uint32_t u_first) {
     const int i = (int)sg.i, nb = (int)sg.r - i;
@@ -537,15 +566,22 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
         if ((int)u <= sg.L_before) break;
         if (fast) {
             // packages with a pivot outside the filtered words each add one
+            // (P2 is read by the two-word filter only)
             uint32_t P1 = PB1, P2 = PB2;
-            for (int p = 0; p < i; p++) {
-                const uint32_t fl = C.flags[sA[p]];
-                P1 += fl & 1u;
-                P2 += (fl >> 1) & 1u;
+            if ((C.a_all & 1u) && (!kTwo || (C.a_all & 2u))) {
+                // every A-unit's pivot lies beyond the filtered words
+                P1 += (uint32_t)i;
+                P2 += (uint32_t)i;
+            } else {
+                for (int p = 0; p < i; p++) {
+                    const uint32_t fl = C.flags[sA[p]];
+                    P1 += fl & 1u;
+                    P2 += (fl >> 1) & 1u;
+                }
             }
             // two filter words while the bound is far above what word 0 can
             // rule out (decided together by the lanes running in step)
-            const bool two = sink.vote_any(C.W >= 2 && (int)thr - (int)P1 > C.t1);
+            const bool two = kTwo && sink.vote_any(C.W >= 2 && (int)thr - (int)P1 > C.t1);
             if (two) {
                 if (P2 < thr) eval_fast<2>(C, sink, thr, i, sA, dig, nb, sB, vbx, vbz, P2);
             } else {

@@ -106,6 +106,7 @@ struct HostExec {
             C.r1 = reinterpret_cast<const U2*>(sm.data() + g.s_r1);
             C.flags = sm.data() + g.s_flag;
             C.t1 = g.t1;
+            C.a_all = g.a_all;
             C.coefs = p->tables.data() + g.coef_off;
             C.binom = sbin;
             C.bstride = lp.bcols;
@@ -165,6 +166,7 @@ unsigned long long first_launch_digest(const Plan& p, int target_warps) {
         EnumParams ep;
         plan_params(p, lp, &ep);  // zeroes the pointers and the budget
         ep.first_static = (uint32_t)ub <= (uint32_t)p.d_est ? 1 : 0;
+        ep.two_word = enum_two_word(ep, (uint32_t)ub);
         put(&ep, sizeof ep);
         put(lp.segs.data(), lp.segs.size() * sizeof(SegDesc));
     }
@@ -297,6 +299,7 @@ extern "C" int hw_solve_sliced(const uint8_t* gen, int n, int K, int field, int 
                 C.r1 = reinterpret_cast<const U2*>(sm.data() + g.s_r1);
                 C.flags = sm.data() + g.s_flag;
                 C.t1 = g.t1;
+                C.a_all = g.a_all;
                 C.coefs = p.tables.data() + g.coef_off;
                 C.binom = sbin;
                 C.bstride = lp.bcols;

@@ -268,3 +268,27 @@ def test_wide_codes_four_words(stream):
         r = gpu(g, stream=stream)
         assert r["d"] == oracle.bruteforce(g)[0], (n, K)
         check_witness(g, r)
+
+
+def test_event_timing_changes_timing_not_results(stream):
+    """gpu_seconds from the kernel's own %globaltimer stamps (default) and
+    from CUDA events around each launch (dist_set_event_timing(1)) describe
+    the same launches: the same d, codewords and launches, both nonzero and
+    close to each other."""
+    g = synth.single_qc(0)
+    assert dist.dist_get_event_timing() == 0
+    with dist.Code(g, dist.DIST_F2) as c:
+        for _ in range(3):
+            c.solve(stream=stream)
+        a = c.solve(stream=stream)
+        dist.dist_set_event_timing(1)
+        try:
+            assert dist.dist_get_event_timing() == 1
+            c.solve(stream=stream)
+            b = c.solve(stream=stream)
+        finally:
+            dist.dist_set_event_timing(0)
+    assert a["d"] == b["d"] == 12
+    assert a["codewords"] == b["codewords"] and a["launches"] == b["launches"]
+    assert a["gpu_seconds"] > 0 and b["gpu_seconds"] > 0
+    assert abs(a["gpu_seconds"] - b["gpu_seconds"]) < 0.5 * max(a["gpu_seconds"], b["gpu_seconds"])

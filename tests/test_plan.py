@@ -251,3 +251,34 @@ def test_small_k_generator_is_a_normalizer():
         G = (N.astype(np.int64) @ J.T) & 1
         assert not G[:s].any() and not G[:, :s].any()
         assert G[s, s + 1] == 1 and f2_rank(N) == n + k
+
+
+def test_dependent_rows_fall_back_to_the_kept_basis():
+    """Over F2 the planner first takes the input rows as independent and
+    checks that on the first matrix's free rows; dependent inputs (a repeated
+    row, a zero row, a sum of rows, anywhere in the input) end up with the
+    rank and the package structure of the independent rows kept in input
+    order."""
+    rng = np.random.default_rng(41)
+    for trial in range(30):
+        n = int(rng.integers(6, 40))
+        K = int(rng.integers(2, n + 1))
+        g = rng.integers(0, 2, size=(K, 2 * n), dtype=np.uint8)
+        where = int(rng.integers(0, K + 1))
+        kind = trial % 3
+        if kind == 0:
+            extra = g[int(rng.integers(0, K))].copy()
+        elif kind == 1:
+            extra = np.zeros(2 * n, dtype=np.uint8)
+        else:
+            extra = g[0] ^ g[K - 1]
+        gd = np.insert(g, where, extra, axis=0)
+        info, _ = check_structure(gd)
+        assert info.k_eff == f2_rank(gd)
+        if f2_rank(g) == K:
+            # the same code: the same rank and matrices as without the extra row
+            # when the extra row comes last (earlier rows are kept first)
+            if where == K:
+                a = dist.dist_plan_info_get(g)
+                assert list(a.a[:a.n_gamma_built]) == list(info.a[:info.n_gamma_built])
+                assert list(a.f[:a.n_gamma_built]) == list(info.f[:info.n_gamma_built])

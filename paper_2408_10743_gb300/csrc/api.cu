@@ -105,6 +105,7 @@ void kit_destroy(SolveKit* k) {
     if (k->e1) cudaEventDestroy(k->e1);
     if (k->stream) cudaStreamDestroy(k->stream);
     if (k->h_state) cudaFreeHost(k->h_state);
+    if (k->h_out) cudaFreeHost(k->h_out);
     delete k;
 }
 }  // namespace
@@ -129,6 +130,16 @@ int kit_acquire(DeviceCtx* d, SolveKit** out) {
         k->h_state = nullptr;
         kit_destroy(k);
         return DIST_ENOMEM;
+    }
+    if (cudaHostAlloc(&k->h_out, sizeof(LaunchOut), cudaHostAllocMapped) != cudaSuccess) {
+        k->h_out = nullptr;
+        kit_destroy(k);
+        return DIST_ENOMEM;
+    }
+    memset(k->h_out, 0, sizeof(LaunchOut));
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&k->d_out), k->h_out, 0) != cudaSuccess) {
+        kit_destroy(k);
+        return DIST_ECUDA;
     }
     *out = k;
     return DIST_OK;
@@ -195,8 +206,9 @@ void release(dist_code* c) {
 // Runs one enumeration launch per call on the GPU (the executor of
 // solve_loop).  The scratch (bound, counters, witness slots) is prepared on
 // the host and goes to the device with the first launch's segment table in
-// one copy; after every launch the whole scratch comes back in one copy, so
-// the witness slot needs no further round trip.
+// one copy; after every launch the kernel's last warp writes the bound, the
+// counters and the witness slot of the bound to the kit's host-mapped
+// LaunchOut, so nothing is copied back.
 struct GpuExec {
     dist_code* c;
     SolveKit* kit;
@@ -204,6 +216,9 @@ struct GpuExec {
     double gpu_s = 0.0;
     unsigned long long nl = 0;
     bool first = true;  // the next launch uploads the scratch image too
+    bool have_last = false;  // last_slot holds slot[last_U] after the last launch
+    uint32_t last_U = DIST_WINF;
+    WitnessSlot last_slot{};
     // kit staging: [table staging (kKitTableBytes) | scratch image | segment table]
     Scratch* hs() const { return reinterpret_cast<Scratch*>(kit->h_state + kKitTableBytes); }
     SegDesc* hsegs() const {
@@ -213,6 +228,7 @@ struct GpuExec {
         memset(hs(), 0, sizeof(Scratch));
         hs()->U = DIST_WINF;
         first = true;
+        have_last = false;
         return DIST_OK;
     }
     int seed(uint32_t U0, const WitnessSlot& s) {
@@ -233,6 +249,8 @@ struct GpuExec {
         ep.segs = c->d_segs;
         ep.binom = c->dev->d_binom;
         ep.scr = c->d_scr;
+        ep.out = kit->d_out;
+        ep.seq = ++kit->seq;
         ep.budget_ns = 0;
         if (deadline_wall > 0) {
             double left = deadline_wall - wall_now();
@@ -279,15 +297,21 @@ struct GpuExec {
         if (enum_launch(ep, grid, st) != cudaSuccess) return DIST_ECUDA;
         if (events) cudaEventRecord(kit->e1, st);
         nl++;
-        if (cudaMemcpyAsync(hs(), c->d_scr, sizeof(Scratch), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-            return DIST_ECUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return DIST_ECUDA;
+        const volatile LaunchOut* o = kit->h_out;
+        if (o->seq != ep.seq) return DIST_EINTERNAL;  // the kernel always publishes
+        hs()->U = o->U;
+        hs()->status = o->status;
+        hs()->codewords = o->codewords;
+        last_U = o->U;
+        memcpy(&last_slot, const_cast<const WitnessSlot*>(&o->slot), sizeof last_slot);
+        have_last = true;
         if (events) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, kit->e0, kit->e1);
             gpu_s += ms * 1e-3;
         } else {
-            gpu_s += scratch_kernel_seconds(*hs());
+            gpu_s += stamps_seconds(o->t_first_inv, o->t_last);
         }
         out->U = hs()->U;
         out->status = hs()->status;
@@ -296,7 +320,17 @@ struct GpuExec {
     }
     int read_slot(uint32_t w, WitnessSlot* s) {
         if (w > DIST_MAXN) return DIST_EINTERNAL;
-        *s = hs()->slot[w];  // read back with the last launch (or the seed itself)
+        if (first) {  // no launch yet: the host image is the scratch
+            *s = hs()->slot[w];
+            return DIST_OK;
+        }
+        if (have_last && w == last_U) {  // published with the last launch
+            *s = last_slot;
+            return DIST_OK;
+        }
+        if (cudaMemcpyAsync(s, &c->d_scr->slot[w], sizeof *s, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return DIST_ECUDA;
         return DIST_OK;
     }
 };

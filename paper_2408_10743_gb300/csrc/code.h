@@ -19,6 +19,9 @@ struct SolveKit {
     cudaStream_t stream = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     unsigned char* h_state = nullptr;
+    LaunchOut* h_out = nullptr;     // host-mapped launch result (LaunchOut)
+    LaunchOut* d_out = nullptr;     // its device address
+    unsigned long long seq = 0;     // launches made with this kit
 };
 
 // Per-device constants (the binomial table the kernels unrank with, SM count,

@@ -55,26 +55,45 @@ struct WitnessSlot {
 // next_chunk the work counter of the current launch.  The single-code kernel
 // also stamps its own run time (%globaltimer, ns): the complement of its
 // earliest block start (kept by atomicMax, so that zero is the reset value)
-// and its latest warp end.  next_chunk and the two stamps are reset together
-// before every launch after the first.
+// and its latest warp end; warps_done counts its finished blocks.
+// next_chunk, the stamps and warps_done are reset together before every
+// launch after the first.
 struct Scratch {
     uint32_t U;
     uint32_t status;              // bit 1: time budget spent
     unsigned long long next_chunk;
     unsigned long long t_first_inv;
     unsigned long long t_last;
+    uint32_t warps_done;
+    uint32_t pad32;
     unsigned long long codewords; // (subset, representative) combinations evaluated
-    unsigned long long pad;
     WitnessSlot slot[DIST_MAXN + 1];
 };
-// Bytes from next_chunk to the end of the stamps (zeroed before a launch).
-#define DIST_SCR_LAUNCH_RESET (3 * sizeof(unsigned long long))
-// Kernel run time of the last launch from its stamps, seconds (0 if unset).
-inline double scratch_kernel_seconds(const Scratch& s) {
-    if (s.t_last == 0 || s.t_first_inv == 0) return 0.0;
-    const unsigned long long t0 = ~s.t_first_inv;
-    return s.t_last > t0 ? 1e-9 * (double)(s.t_last - t0) : 0.0;
+// Bytes from next_chunk to the end of warps_done (zeroed before a launch).
+#define DIST_SCR_LAUNCH_RESET (4 * sizeof(unsigned long long))
+
+// What the last block of a single-code launch writes to host-mapped memory
+// when the launch asks for it, so that the host needs no copy back: the
+// bound, status and codeword count after the launch, its stamps, and the
+// witness slot of that bound, and the launch's sequence number (read once
+// the launch has completed).
+struct alignas(16) LaunchOut {
+    uint32_t U;
+    uint32_t status;
+    unsigned long long codewords;
+    unsigned long long t_first_inv;
+    unsigned long long t_last;
+    WitnessSlot slot;             // slot[U] (zero if U > DIST_MAXN)
+    unsigned long long seq;       // the launch's EnumParams::seq
+};
+
+// Kernel run time of a launch from its stamps, seconds (0 if unset).
+inline double stamps_seconds(unsigned long long t_first_inv, unsigned long long t_last) {
+    if (t_last == 0 || t_first_inv == 0) return 0.0;
+    const unsigned long long t0 = ~t_first_inv;
+    return t_last > t0 ? 1e-9 * (double)(t_last - t0) : 0.0;
 }
+inline double scratch_kernel_seconds(const Scratch& s) { return stamps_seconds(s.t_first_inv, s.t_last); }
 
 // A generator matrix as one launch sees it.
 struct GammaDesc {
@@ -127,6 +146,8 @@ struct EnumParams {
     unsigned long long budget_ns;       // stop after this long (per block, %globaltimer); 0 = none
     int first_static;                   // 1: the first wave of chunks goes by warp index
     int two_word;                       // 0: the bound at the launch cannot reach the two-word filter
+    LaunchOut* out;                     // host-mapped result of the launch, or null
+    unsigned long long seq;             // written to out->seq when the result is complete
     GammaDesc g[DIST_MAXGAMMA];
 };
 

@@ -193,6 +193,39 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         if (done) atomicAdd(&P.scr->codewords, done);
         atomicMax(&P.scr->t_last, global_ns());
     }
+    if (P.out) {
+        // the last block to finish publishes the launch's result; its loads
+        // bypass L1 (the other blocks' updates are in L2 after their fences)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(&P.scr->warps_done, 1u) == gridDim.x - 1u) {
+                __threadfence();
+                const Scratch* s = P.scr;
+                const unsigned long long us = __ldcg(reinterpret_cast<const unsigned long long*>(s));
+                const unsigned long long cw = __ldcg(&s->codewords);
+                const unsigned long long t0 = __ldcg(&s->t_first_inv), t1 = __ldcg(&s->t_last);
+                const uint32_t U = (uint32_t)us;
+                const uint4* src = reinterpret_cast<const uint4*>(&s->slot[U <= DIST_MAXN ? U : 0]);
+                uint4 sl[sizeof(WitnessSlot) / 16];
+#pragma unroll
+                for (int w = 0; w < (int)(sizeof(WitnessSlot) / 16); w++)
+                    sl[w] = U <= DIST_MAXN ? __ldcg(src + w) : make_uint4(0u, 0u, 0u, 0u);
+                LaunchOut* o = P.out;
+                o->U = U;
+                o->status = (uint32_t)(us >> 32);
+                o->codewords = cw;
+                o->t_first_inv = t0;
+                o->t_last = t1;
+                uint4* dst = reinterpret_cast<uint4*>(&o->slot);
+#pragma unroll
+                for (int w = 0; w < (int)(sizeof(WitnessSlot) / 16); w++) dst[w] = sl[w];
+                // the host reads it after the launch has completed, when all
+                // of it is visible: no system-scope fence is needed
+                o->seq = P.seq;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -86,3 +86,21 @@ def test_qc72_and_work_comparison():
     assert ri["d"] == rp["d"] == int(want["d"])
     valid(g, ri)
     assert ri["codewords"] > 5 * rp["codewords"]
+
+
+def test_batch_codes_vs_oracle_table():
+    """The isometry method on 256 of the batch workload's random codes
+    (n 16-56, so rounds up to 8 of matrices of up to 56 rows, through the
+    pair and triple walks): every d equals the stored oracle value."""
+    from codes import load_oracle_table
+    _, table = load_oracle_table("batch4096_oracle.txt")
+    gens = synth.batch_codes(256)
+    for i, g in enumerate(gens):
+        n, K, d, lo, hi = table[i]
+        assert (n, K) == (g.shape[1] // 2, g.shape[0])
+        r = iso(g)
+        if d is not None:
+            assert r["d"] == d, i
+        else:
+            assert lo <= r["d"] <= hi, i
+        valid(g, r)

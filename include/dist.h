@@ -189,7 +189,10 @@ typedef struct {
 
 typedef struct dist_batch dist_batch;
 
-/* Creates a batch on the current device; opts may be NULL (defaults). */
+/* Creates a batch on the current device; opts may be NULL (defaults).  It
+ * allocates the batch's 32 MB staging arena (pinned host and device memory;
+ * larger slices grow it) and captures its slice graph, so that the first
+ * slices allocate nothing. */
 int dist_batch_create(dist_batch **b, const dist_batch_opts *opts);
 /* Queues count codes (initialised with dist_init on the same device) as one ticket. */
 int dist_batch_submit(dist_batch *b, dist_code *const *codes, int count, uint64_t *ticket);

@@ -35,6 +35,7 @@
 #include "../../include/dist.h"
 #include "code.h"
 #include "plan.h"
+#include "pool.h"
 #include "solve.h"
 
 namespace dist {
@@ -51,25 +52,16 @@ namespace {
 // A code with at most this many chunks is served entirely from the order list.
 const unsigned long long kSmallChunks = 64;
 // Host threads that plan, re-chunk and post-process a large slice.
-const size_t kPlanThreads = 8;
-
-// fn(a, b) over [0, n) cut into ranges of at least `grain` items, on up to
-// kPlanThreads host threads (this one included); every item is touched by
-// exactly one thread.
+// fn(a, b) over [0, n) on the process's host pool (this thread included),
+// in ranges of `grain` items; every item is touched by exactly one thread.
 template <class F>
 void par_ranges(size_t n, size_t grain, const F& fn) {
-    const size_t nthreads = std::max<size_t>(1, std::min(kPlanThreads, n / std::max<size_t>(1, grain)));
-    if (nthreads <= 1) {
-        fn((size_t)0, n);
-        return;
-    }
-    std::vector<std::thread> pool;
-    const size_t per = (n + nthreads - 1) / nthreads;
-    for (size_t t = 1; t < nthreads; t++)
-        pool.emplace_back([&fn, t, per, n] { fn(std::min(n, t * per), std::min(n, (t + 1) * per)); });
-    fn(0, std::min(n, per));
-    for (std::thread& th : pool) th.join();
+    HostPool::get().run(n, grain, fn);
 }
+
+// Initial size of a batch's staging arena (pinned host and device): the
+// slice of a few thousand small codes, with their tables, fits.
+constexpr size_t kArenaInitialBytes = 32ull << 20;
 
 struct Item {
     dist_code* c = nullptr;
@@ -204,7 +196,7 @@ int dist_batch::slice() {
     // plans are independent: large admissions are planned on several host
     // threads (each writes only its own items)
     std::vector<int> prc(todo.size(), P_OK);
-    par_ranges(todo.size(), 128, [&](size_t a, size_t b) {
+    par_ranges(todo.size(), 32, [&](size_t a, size_t b) {
         for (size_t k = a; k < b; k++) {
             Item* it = todo[k];
             const Plan& p = it->c->plan;
@@ -227,7 +219,7 @@ int dist_batch::slice() {
         double all = 0;
         for (Item* it : active)
             if (!it->done) all += estimated_work(it);
-        par_ranges(fresh.size(), 128, [&](size_t a, size_t b) {
+        par_ranges(fresh.size(), 32, [&](size_t a, size_t b) {
             for (size_t k = a; k < b; k++) {
                 Item* it = fresh[k];
                 const double share = estimated_work(it) / std::max(all, 1.0);
@@ -243,12 +235,17 @@ int dist_batch::slice() {
     const int n = (int)run.size();
     // the slice's arrays, packed one after another into the arena behind
     // its header (offsets 256-byte aligned)
-    size_t nseg = 0, ngam = 0;
+    size_t nseg = 0, ngam = 0, tab_bytes = 0;
     int ninit = 0;
+    std::vector<Item*> inits_of;  // the items set up on the device in this slice
     for (Item* it : run) {
         nseg += it->lp.segs.size();
         ngam += it->lp.g.size();
-        if (it->init_mode) ninit++;
+        if (it->init_mode) {
+            ninit++;
+            inits_of.push_back(it);
+            if (!it->c->tables_on_device) tab_bytes += (it->c->plan.tables.size() * 4 + 15) & ~(size_t)15;
+        }
     }
     std::vector<double> work(n);
     double total = 0;
@@ -293,6 +290,10 @@ int dist_batch::slice() {
     place(&hd.off_ring, rng.size() * sizeof(int32_t));
     place(&hd.off_sched, 2 * sizeof(unsigned long long));
     place(&hd.off_scrs, (size_t)n * sizeof(Scratch*));
+    // tables of codes on their first slice (the init kernel copies them to
+    // the codes' device blocks)
+    unsigned long long off_tabs = 0;
+    place(&off_tabs, tab_bytes);
     const size_t up_bytes = off;
     place(&hd.off_outs, (size_t)n * sizeof(BatchOut));
     if (off > arena.cap) {  // a new allocation: the graph is captured again
@@ -306,21 +307,40 @@ int dist_batch::slice() {
     hd.nring = (int32_t)rng.size();
     hd.budget_ns = opts.slice_ms > 0 ? (unsigned long long)(opts.slice_ms * 1e6) : 0ull;
     memcpy(h, &hd, sizeof hd);
-    // scratch set-up of new and re-planned codes
+    // scratch set-up of new and re-planned codes, with the tables of the
+    // new ones (staged on the host threads)
     BatchInit* inits = reinterpret_cast<BatchInit*>(h + hd.off_inits);
-    int k_init = 0;
-    for (Item* it : run) {
-        if (!it->init_mode) continue;
-        BatchInit& bi = inits[k_init++];
-        memset(&bi, 0, sizeof bi);
-        bi.scr = it->c->d_scr;
-        bi.mode = (uint32_t)it->init_mode;
-        const Plan& p = it->c->plan;
-        const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
-        bi.U0 = (uint32_t)std::min<int>(u0, DIST_WINF);
-        bi.slot = p.n_stab > 0 ? p.u0_excl_slot : p.u0_slot;
-        it->init_mode = 0;
+    std::vector<unsigned long long> tab_at(inits_of.size(), 0);
+    {
+        unsigned long long o = off_tabs;
+        for (size_t k = 0; k < inits_of.size(); k++) {
+            const dist_code* c = inits_of[k]->c;
+            if (c->tables_on_device) continue;
+            tab_at[k] = o;
+            o += (c->plan.tables.size() * 4 + 15) & ~(size_t)15;
+        }
     }
+    par_ranges(inits_of.size(), 64, [&](size_t a, size_t b) {
+        for (size_t k = a; k < b; k++) {
+            Item* it = inits_of[k];
+            BatchInit& bi = inits[k];
+            memset(&bi, 0, sizeof bi);
+            bi.scr = it->c->d_scr;
+            bi.mode = (uint32_t)it->init_mode;
+            const Plan& p = it->c->plan;
+            const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
+            bi.U0 = (uint32_t)std::min<int>(u0, DIST_WINF);
+            bi.slot = p.n_stab > 0 ? p.u0_excl_slot : p.u0_slot;
+            if (!it->c->tables_on_device) {
+                bi.tab_dst = it->c->d_tables;
+                bi.tab_off = tab_at[k];
+                bi.tab_words = (uint32_t)p.tables.size();
+                memcpy(h + tab_at[k], p.tables.data(), p.tables.size() * 4);
+                it->c->tables_on_device = true;
+            }
+            it->init_mode = 0;
+        }
+    });
     BatchCode* codes = reinterpret_cast<BatchCode*>(h + hd.off_codes);
     SegDesc* segs = reinterpret_cast<SegDesc*>(h + hd.off_segs);
     GammaDesc* gammas = reinterpret_cast<GammaDesc*>(h + hd.off_gammas);
@@ -374,7 +394,7 @@ int dist_batch::slice() {
     // per code: certify, resume, or plan the next steps (each item is
     // touched by one host thread only)
     const double t_now = wall_now();
-    par_ranges((size_t)n, 128, [&](size_t a, size_t b) {
+    par_ranges((size_t)n, 32, [&](size_t a, size_t b) {
     for (size_t i = a; i < b; i++) {
         Item* it = run[i];
         it->slices++;
@@ -495,6 +515,21 @@ int dist_batch_create(dist_batch** out, const dist_batch_opts* opts) {
         delete b;
         return DIST_ECUDA;
     }
+    // the staging arena at its initial size and the slice graph on it, so
+    // that the first slices allocate and capture nothing
+    auto fail = [b](int rc) {
+        b->drop_graph();
+        b->arena.release();
+        cudaEventDestroy(b->e0);
+        cudaEventDestroy(b->e1);
+        cudaStreamDestroy(b->st);
+        delete b;
+        return rc;
+    };
+    if (!b->arena.ensure(kArenaInitialBytes)) return fail(DIST_ENOMEM);
+    if (slice_graph_build(b->arena.d, b->arena.h, dev->d_binom, dev->sms * dev->batch_blocks_per_sm, 2 * dev->sms,
+                          b->e0, b->e1, b->st, &b->graph, &b->gexec, &b->n_h2d, &b->n_d2h) != cudaSuccess)
+        return fail(DIST_ECUDA);
     b->worker = std::thread([b] { b->run(); });
     *out = b;
     return DIST_OK;
@@ -502,13 +537,6 @@ int dist_batch_create(dist_batch** out, const dist_batch_opts* opts) {
 
 int dist_batch_submit(dist_batch* b, dist_code* const* codes, int count, uint64_t* ticket) {
     if (!b || !codes || count < 1 || !ticket) return DIST_EINVAL;
-    // the multi-code kernel reads every code's tables from the device
-    for (int i = 0; i < count; i++)
-        if (codes[i] && !codes[i]->in_batch && codes[i]->dev == b->dev) {
-            DeviceGuard g(b->dev->device);
-            const int rc = upload_tables(codes[i]);
-            if (rc) return rc;
-        }
     std::lock_guard<std::mutex> lk(b->mu);
     if (b->fatal) return b->fatal;
     for (int i = 0; i < count; i++) {

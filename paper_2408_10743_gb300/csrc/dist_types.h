@@ -197,12 +197,18 @@ struct SliceHeader {
         off_outs;
 };
 
-// Per-code scratch set-up before a multi-code launch.
+// Per-code scratch set-up before a multi-code launch, and the copy of a
+// code's tables from the slice's upload to its device block on its first
+// slice (tab_words = 0: nothing to copy).
 struct BatchInit {
     Scratch* scr;
     uint32_t mode;                      // 1 = full reset + seed, 2 = restart the chunk counter
     uint32_t U0;                        // seeded upper bound (DIST_WINF = none)
     WitnessSlot slot;                   // witness of U0
+    uint32_t* tab_dst;                  // the code's Plan::tables on the device
+    unsigned long long tab_off;         // byte offset of the staged tables in the arena
+    uint32_t tab_words;
+    uint32_t pad;
 };
 
 // Per-code state read back after a multi-code launch.

@@ -95,14 +95,18 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         C.proj = P.proj;
         C.exclude = P.exclude;
     }
-    // stage: representatives and flags of every matrix in the launch, the
-    // binomials and the segment table
+    // stage: representatives, flags and the word-0 and word-1 tables of every
+    // matrix in the launch, the binomials and the segment table
     for (int gi = 0; gi < P.ng; gi++) {
         const GammaDesc& g = P.g[gi];
         const uint32_t* src = P.tables + g.rep_off;
         const int nw = (g.a + g.b) * 6 * P.W;
         for (int t = threadIdx.x; t < nw; t += blockDim.x) cp_async4(&sm[g.s_rep + t], &src[t]);
         for (int t = threadIdx.x; t < g.a + g.b; t += blockDim.x) cp_async4(&sm[g.s_flag + t], &P.tables[g.flag_off + t]);
+        for (int t = threadIdx.x; t < g.a * 3; t += blockDim.x) {
+            cp_async8(&sm[g.s_r0 + 2 * t], &P.tables[g.r0_off + 2 * t]);
+            cp_async8(&sm[g.s_r1 + 2 * t], &P.tables[g.r1_off + 2 * t]);
+        }
     }
     for (int t = threadIdx.x; t < P.brows * P.bcols; t += blockDim.x) {
         const int n = t / P.bcols, k = t - n * P.bcols;
@@ -116,20 +120,6 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         for (int t = threadIdx.x; t < nw; t += blockDim.x) cp_async4(&dst[t], &src[t]);
     }
     cp_async_wait_all();
-    __syncthreads();
-    // word-0 and word-1 tables of the A-units, from the staged representatives
-    for (int gi = 0; gi < P.ng; gi++) {
-        const GammaDesc& g = P.g[gi];
-        const uint32_t* rep = sm + g.s_rep;
-        U2* r0 = reinterpret_cast<U2*>(sm + g.s_r0);
-        U2* r1 = reinterpret_cast<U2*>(sm + g.s_r1);
-        for (int t = threadIdx.x; t < g.a * 3; t += blockDim.x) {
-            r0[t].x = rep[(t * 2 + 0) * P.W];
-            r0[t].z = rep[(t * 2 + 1) * P.W];
-            r1[t].x = P.W >= 2 ? rep[(t * 2 + 0) * P.W + 1] : 0u;
-            r1[t].z = P.W >= 2 ? rep[(t * 2 + 1) * P.W + 1] : 0u;
-        }
-    }
     __syncthreads();
 
     DevSink sink{P.scr};
@@ -192,13 +182,15 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
     if (lane == 0) {
         if (done) atomicAdd(&P.scr->codewords, done);
         atomicMax(&P.scr->t_last, global_ns());
+        // the warp's updates are visible to the whole GPU before its block
+        // counts itself done
+        if (P.out) __threadfence();
     }
     if (P.out) {
         // the last block to finish publishes the launch's result; its loads
-        // bypass L1 (the other blocks' updates are in L2 after their fences)
+        // bypass L1 (every block's updates are in L2 after its fences)
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
             if (atomicAdd(&P.scr->warps_done, 1u) == gridDim.x - 1u) {
                 __threadfence();
                 const Scratch* s = P.scr;
@@ -385,6 +377,10 @@ __global__ void batch_init_kernel(const unsigned char* __restrict__ arena) {
     const int n = H->ninit;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const BatchInit it = items[i];
+        if (it.tab_words) {  // the code's tables, staged in this slice's upload
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(arena + it.tab_off);
+            for (uint32_t t = threadIdx.x; t < it.tab_words; t += blockDim.x) it.tab_dst[t] = src[t];
+        }
         if (it.mode == 1) {
             uint32_t* w = reinterpret_cast<uint32_t*>(it.scr);
             for (int t = threadIdx.x; t < (int)(sizeof(Scratch) / 4); t += blockDim.x) w[t] = 0u;

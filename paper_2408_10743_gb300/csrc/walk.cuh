@@ -555,6 +555,11 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
     uint32_t vbx[2], vbz[2], PB1, PB2;
     b_words(C, nb, sB, vbx, vbz, PB1, PB2);
     const bool fast = use_fast(C, i);
+    // per-segment and per-matrix constants of the subset loop, read once
+    // (as references into shared memory they would be read every subset)
+    const int L_before = sg.L_before, a = C.a;
+    const unsigned long long codes = sg.codes, NA = sg.NA;
+    const bool all_outside = (C.a_all & 1u) && (!kTwo || (C.a_all & 2u));
     unsigned long long done = 0;
     // The running bound is read one subset ahead: a stale (larger) value is
     // still a valid threshold, and the load's latency overlaps the work.
@@ -563,12 +568,12 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
         const uint32_t u = u_next;
         u_next = sink.peek();
         thr = u < thr ? u : thr;
-        if ((int)u <= sg.L_before) break;
+        if ((int)u <= L_before) break;
         if (fast) {
             // packages with a pivot outside the filtered words each add one
             // (P2 is read by the two-word filter only)
             uint32_t P1 = PB1, P2 = PB2;
-            if ((C.a_all & 1u) && (!kTwo || (C.a_all & 2u))) {
+            if (all_outside) {
                 // every A-unit's pivot lies beyond the filtered words
                 P1 += (uint32_t)i;
                 P2 += (uint32_t)i;
@@ -590,15 +595,15 @@ DIST_HD unsigned long long walk_range(const LaneCtx& C, Sink& sink, uint32_t& th
         } else {
             thr = eval_generic(C, sink, thr, i, sA, nb, sB);
         }
-        done += sg.codes;
+        done += codes;
         if (idx + 1 < hi) {
-            if (++tA == sg.NA) {
+            if (++tA == NA) {
                 tA = 0;
                 rd_next(sB, nb, C.b);
                 b_words(C, nb, sB, vbx, vbz, PB1, PB2);
                 for (int p = 0; p < i; p++) sA[p] = (uint8_t)p;
             } else {
-                rd_next(sA, i, C.a);
+                rd_next(sA, i, a);
             }
         }
     }

@@ -73,6 +73,7 @@ struct Item {
     int init_mode = 1;         // 1 = reset and seed, 2 = restart the counter, 0 = none
     int last_round = 0;
     int slices = 0;
+    double work = 1.0;         // estimated_work of lp, set when it is planned
     bool done = false;
     dist_result res{};
     double t_submit = 0, t_admit = 0, t_done = 0;
@@ -202,6 +203,7 @@ int dist_batch::slice() {
             const Plan& p = it->c->plan;
             const int u0 = p.n_stab > 0 ? p.u0_excl : p.u0;
             prc[k] = plan_launch(p, it->r_next, it->j_next, it->L, u0, tw, 1e300, &it->lp);
+            if (prc[k] == P_OK) it->work = estimated_work(it);  // re-chunking leaves it unchanged
         }
     });
     for (size_t k = 0; k < todo.size(); k++) {
@@ -218,11 +220,11 @@ int dist_batch::slice() {
     if (!fresh.empty() && opts.slice_ms <= 0) {
         double all = 0;
         for (Item* it : active)
-            if (!it->done) all += estimated_work(it);
+            if (!it->done) all += it->work;
         par_ranges(fresh.size(), 32, [&](size_t a, size_t b) {
             for (size_t k = a; k < b; k++) {
                 Item* it = fresh[k];
-                const double share = estimated_work(it) / std::max(all, 1.0);
+                const double share = it->work / std::max(all, 1.0);
                 const int twi = (int)std::min<double>(tw, std::max(32.0, std::ceil(4.0 * share * tw)));
                 if (twi < tw) plan_rechunk(&it->lp, twi);
             }
@@ -250,7 +252,7 @@ int dist_batch::slice() {
     std::vector<double> work(n);
     double total = 0;
     for (int i = 0; i < n; i++) {
-        work[i] = estimated_work(run[i]);
+        work[i] = run[i]->work;
         total += work[i];
     }
     // Order list (phase 1, one chunk per entry), shortest job first so that
@@ -345,30 +347,41 @@ int dist_batch::slice() {
     SegDesc* segs = reinterpret_cast<SegDesc*>(h + hd.off_segs);
     GammaDesc* gammas = reinterpret_cast<GammaDesc*>(h + hd.off_gammas);
     Scratch** scrs = reinterpret_cast<Scratch**>(h + hd.off_scrs);
-    size_t so = 0, go = 0;
-    for (int i = 0; i < n; i++) {
-        Item* it = run[i];
-        const Plan& p = it->c->plan;
-        BatchCode& bc = codes[i];
-        memset(&bc, 0, sizeof bc);
-        bc.tables = it->c->d_tables;
-        bc.scr = it->c->d_scr;
-        for (int w = 0; w < DIST_MAXCW; w++) bc.outside[w] = p.outside[w];
-        bc.W = p.W;
-        bc.CW = p.CW;
-        bc.proj = p.field == 4 ? 1 : 0;
-        bc.exclude = p.n_stab > 0 ? 1 : 0;
-        bc.seg0 = (uint32_t)so;
-        bc.nseg = (uint32_t)it->lp.segs.size();
-        bc.g0 = (uint32_t)go;
-        bc.ng = (uint32_t)it->lp.g.size();
-        bc.nchunks = it->lp.nchunks;
-        memcpy(segs + so, it->lp.segs.data(), it->lp.segs.size() * sizeof(SegDesc));
-        memcpy(gammas + go, it->lp.g.data(), it->lp.g.size() * sizeof(GammaDesc));
-        so += it->lp.segs.size();
-        go += it->lp.g.size();
-        scrs[i] = it->c->d_scr;
+    // each code's segments and matrices at offsets fixed first, then packed
+    // on the host threads
+    std::vector<uint32_t> seg_at(n), gam_at(n);
+    {
+        size_t so = 0, go = 0;
+        for (int i = 0; i < n; i++) {
+            seg_at[i] = (uint32_t)so;
+            gam_at[i] = (uint32_t)go;
+            so += run[i]->lp.segs.size();
+            go += run[i]->lp.g.size();
+        }
     }
+    par_ranges((size_t)n, 64, [&](size_t a, size_t b) {
+        for (size_t i = a; i < b; i++) {
+            Item* it = run[i];
+            const Plan& p = it->c->plan;
+            BatchCode& bc = codes[i];
+            memset(&bc, 0, sizeof bc);
+            bc.tables = it->c->d_tables;
+            bc.scr = it->c->d_scr;
+            for (int w = 0; w < DIST_MAXCW; w++) bc.outside[w] = p.outside[w];
+            bc.W = p.W;
+            bc.CW = p.CW;
+            bc.proj = p.field == 4 ? 1 : 0;
+            bc.exclude = p.n_stab > 0 ? 1 : 0;
+            bc.seg0 = seg_at[i];
+            bc.nseg = (uint32_t)it->lp.segs.size();
+            bc.g0 = gam_at[i];
+            bc.ng = (uint32_t)it->lp.g.size();
+            bc.nchunks = it->lp.nchunks;
+            memcpy(segs + seg_at[i], it->lp.segs.data(), it->lp.segs.size() * sizeof(SegDesc));
+            memcpy(gammas + gam_at[i], it->lp.g.data(), it->lp.g.size() * sizeof(GammaDesc));
+            scrs[i] = it->c->d_scr;
+        }
+    });
     memcpy(h + hd.off_order, ord.data(), ord.size() * sizeof(int32_t));
     memcpy(h + hd.off_ring, rng.data(), rng.size() * sizeof(int32_t));
     memset(h + hd.off_sched, 0, 2 * sizeof(unsigned long long));

@@ -148,6 +148,8 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         if (!P.first_static) claimed = atomicAdd(&P.scr->next_chunk, 1ull);
         u_claim = *reinterpret_cast<volatile uint32_t*>(&P.scr->U);
     }
+    // certification work (first_static) reads U at every eighth subset
+    const unsigned long long peek_mask = P.first_static ? 7ull : 0ull;
     int seg = 0;                  // chunks are claimed in increasing order
     unsigned long long done = 0;  // this lane's codewords over all its chunks
     for (;;) {
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB) enum_kernel
         }
         const LaneCtx& C = s_ctx[sg.g];
         unsigned long long lo, hi;
-        if (seg_lane_range(sg, chunk, lane, lo, hi)) done += walk_range<DevSink, kTwo>(C, sink, thr, sg, lo, hi, u_now);
+        if (seg_lane_range(sg, chunk, lane, lo, hi)) done += walk_range<DevSink, kTwo>(C, sink, thr, sg, lo, hi, u_now, peek_mask);
         if (P.budget_ns) {
             int stop = 0;
             if (lane == 0 && global_ns() - t_start > P.budget_ns) {

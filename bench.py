@@ -146,7 +146,15 @@ def cpu_baseline(g, field, budget_s):
                       % (budget_s, r["codewords"], r["rounds"],
                          "complete" if r["complete"] else "stopped by the budget"),
             "complete": bool(r["complete"]), "seconds": r["seconds"],
-            "time_to_d_s": r["seconds"] if r["complete"] else None}
+            "time_to_d_s": r["seconds"] if r["complete"] else None,
+            "one_core": one_core_rate(oracle, g, field, min(3.0, budget_s))}
+
+
+def one_core_rate(oracle, g, field, budget_s):
+    """The oracle on a single host thread, a bounded sample of the same code."""
+    r = oracle.bz(g, field=field, threads=1, time_budget=budget_s, allow_incomplete=True)
+    return {"value": r["codewords"] / max(r["seconds"], 1e-9), "unit": METRIC, "cores": 1,
+            "sample": "first %.0f s of the same enumeration on one thread (%d codewords)" % (budget_s, r["codewords"])}
 
 
 def hist10(ns):

@@ -416,6 +416,8 @@ static void diag_f2_t(const Plan& p, const std::vector<int>& qorder, std::vector
         if (!piv[i]) units.push_back({UNIT_FREE, -1, i, -1});
     G.A.clear();
     G.B.clear();
+    G.A.reserve(units.size());
+    G.B.reserve(units.size());
     G.f = 0;
     G.npack = 0;
     for (const U& u : units) {

@@ -4,6 +4,7 @@
 
 #include <math.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
@@ -867,6 +868,9 @@ namespace {
 class Helper {
    public:
     bool try_run(std::function<void()> job) {
+        // a child process made by fork() has no helper thread (and its lock
+        // may have been held at the fork): the caller does the work
+        if (getpid() != owner_) return false;
         std::lock_guard<std::mutex> lk(mu_);
         if (busy_.load(std::memory_order_relaxed)) return false;
         job_ = std::move(job);
@@ -898,7 +902,7 @@ class Helper {
                 return false;
         }
     }
-    Helper() { std::thread([this] { loop(); }).detach(); }
+    Helper() : owner_(getpid()) { std::thread([this] { loop(); }).detach(); }
     void loop() {
         for (;;) {
             spin_until([this] { return pending_.load(std::memory_order_acquire); }, kIdleSpin);
@@ -922,6 +926,7 @@ class Helper {
     std::condition_variable cv_, done_;
     std::function<void()> job_;
     std::atomic<bool> busy_{false}, pending_{false};
+    const pid_t owner_;
 };
 
 // Fisher-Yates with xorshift64* on qorder, advancing the generator x.

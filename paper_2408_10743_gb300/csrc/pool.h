@@ -6,7 +6,8 @@
 // sleeping thread takes from a few to tens of microseconds, so workers spin
 // for kIdleSpin after each region before they sleep (the slices of a batch
 // follow one another).  One region runs at a time; a caller that finds one
-// running does its items itself.
+// running, or that runs in a child process made by fork() (which has none of
+// the workers), does its items itself.
 #pragma once
 #include <algorithm>
 #include <atomic>
@@ -16,6 +17,8 @@
 #include <mutex>
 #include <thread>
 #include <vector>
+
+#include <unistd.h>
 
 namespace dist {
 
@@ -30,8 +33,12 @@ class HostPool {
     template <class F>
     void run(size_t n, size_t grain, const F& fn) {
         grain = std::max<size_t>(1, grain);
+        if (getpid() != owner_ || workers_.empty() || n <= grain) {
+            fn((size_t)0, n);
+            return;
+        }
         std::unique_lock<std::mutex> region(region_mu_, std::try_to_lock);
-        if (!region.owns_lock() || workers_.empty() || n <= grain) {
+        if (!region.owns_lock()) {
             fn((size_t)0, n);
             return;
         }
@@ -70,7 +77,7 @@ class HostPool {
                 return false;
         }
     }
-    HostPool() {
+    HostPool() : owner_(getpid()) {
         const unsigned hw = std::thread::hardware_concurrency();
         const unsigned nw = hw > 1 ? std::min(hw - 1, 15u) : 0u;
         for (unsigned t = 0; t < nw; t++) workers_.emplace_back([this] { loop(); });
@@ -107,6 +114,7 @@ class HostPool {
     std::atomic<int> pending_{0};
     const std::function<void(size_t, size_t)>* job_ = nullptr;
     size_t n_ = 0, grain_ = 1;
+    const pid_t owner_;
 };
 
 }  // namespace dist

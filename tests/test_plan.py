@@ -282,3 +282,34 @@ def test_dependent_rows_fall_back_to_the_kept_basis():
                 a = dist.dist_plan_info_get(g)
                 assert list(a.a[:a.n_gamma_built]) == list(info.a[:info.n_gamma_built])
                 assert list(a.f[:a.n_gamma_built]) == list(info.f[:info.n_gamma_built])
+
+
+def test_planner_after_fork():
+    """A child process made by fork() after the planner's helper thread has
+    started (a 72-qubit plan uses it) plans on its own thread: the same plan,
+    no wait on a thread the child does not have."""
+    import os
+    import time
+    g = synth.single_qc(0)
+    parent = dist.dist_plan_info_get(g)
+    pid = os.fork()
+    if pid == 0:  # child: plan again and report through the exit status
+        ok = 0
+        try:
+            c = dist.dist_plan_info_get(g)
+            ok = int(c.u0 == parent.u0 and c.d_est == parent.d_est
+                     and list(c.f[:c.n_gamma_built]) == list(parent.f[:parent.n_gamma_built]))
+        finally:
+            os._exit(0 if ok else 3)
+    t0 = time.time()
+    status = None
+    while time.time() - t0 < 60:
+        done, status = os.waitpid(pid, os.WNOHANG)
+        if done:
+            break
+        time.sleep(0.05)
+    else:
+        os.kill(pid, 9)
+        os.waitpid(pid, 0)
+        pytest.fail("the forked child did not finish planning")
+    assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0

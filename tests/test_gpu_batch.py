@@ -230,3 +230,28 @@ def test_wait_array_matches_wait():
         assert np.array_equal(np.bitwise_xor.reduce(g[row["coeffs"][:g.shape[0]].astype(bool)], axis=0), w)
     for c in codes:
         c.close()
+
+
+def test_slice_larger_than_the_initial_arena():
+    """3000 codes of 80 qubits and 80 rows, each with a weight-1 row (d = 1),
+    submitted together: their first slice stages about 45 MB of tables (two
+    matrices of about 40 units, 15 KB per code), more than the batch's
+    initial 32 MB arena, so the arena grows and the slice graph is captured
+    again; every d is 1 with a valid witness."""
+    rng = synth.Xoshiro256ss(4242)
+    gens = []
+    for i in range(3000):
+        g = synth.random_f2_code(80, 80, rng)
+        g[0, :] = 0
+        g[0, i % 80] = 1  # x on one qubit
+        gens.append(g)
+    codes = [dist.Code(g) for g in gens]
+    with dist.Batch() as b:
+        res = b.wait_array(b.submit(codes), timeout_s=600)
+    for g, row in zip(gens, res):
+        assert int(row["status"]) == 0 and int(row["d"]) == 1
+        w = row["witness"][:160]
+        assert sym_weight_bits(w, 80) == 1
+        assert np.array_equal(np.bitwise_xor.reduce(g[row["coeffs"][:80].astype(bool)], axis=0), w)
+    for c in codes:
+        c.close()

@@ -345,20 +345,29 @@ __global__ void __launch_bounds__(256) iso_pair_kernel(const __grid_constant__ I
             }
             const uint32_t nh = min(cm - p0, left);
             passes += (nh + 31u) >> 5;
+            // the lightest words-0-1 bound of this lane's pairs of the top,
+            // with a three-way min instead of a branch per pair; the pairs
+            // are weighed against thr one by one only if it beats thr (rare)
+            uint32_t m = 0xFFFFu;
             uint32_t q = (uint32_t)lane;
             for (; q + 32u < nh; q += 64u) {  // two pairs per pass: two table loads in flight
                 const uint32_t p = p0 + q;
                 const uint4 e0 = spt[p], e1 = spt[p + 32u];
-                const uint32_t w0 = npb + e0.z + (uint32_t)__popc(bx ^ e0.x) + (uint32_t)__popc(by ^ e0.y);
-                const uint32_t w1 = npb + e1.z + (uint32_t)__popc(bx ^ e1.x) + (uint32_t)__popc(by ^ e1.y);
-                if (w0 < thr) thr = iso_pair_slow<WORDS>(P, srow, spiv, T, m2, p, thr);
-                if (w1 < thr) thr = iso_pair_slow<WORDS>(P, srow, spiv, T, m2, p + 32u, thr);
+                const uint32_t w0 = e0.z + (uint32_t)__popc(bx ^ e0.x) + (uint32_t)__popc(by ^ e0.y);
+                const uint32_t w1 = e1.z + (uint32_t)__popc(bx ^ e1.x) + (uint32_t)__popc(by ^ e1.y);
+                m = __vimin3_u32(m, w0, w1);
             }
             if (q < nh) {
-                const uint32_t p = p0 + q;
-                const uint4 e = spt[p];
-                const uint32_t w = npb + e.z + (uint32_t)__popc(bx ^ e.x) + (uint32_t)__popc(by ^ e.y);
-                if (w < thr) thr = iso_pair_slow<WORDS>(P, srow, spiv, T, m2, p, thr);
+                const uint4 e = spt[p0 + q];
+                m = min(m, e.z + (uint32_t)__popc(bx ^ e.x) + (uint32_t)__popc(by ^ e.y));
+            }
+            if (npb + m < thr) {
+                for (uint32_t q2 = (uint32_t)lane; q2 < nh; q2 += 32u) {
+                    const uint32_t p = p0 + q2;
+                    const uint4 e = spt[p];
+                    const uint32_t w = npb + e.z + (uint32_t)__popc(bx ^ e.x) + (uint32_t)__popc(by ^ e.y);
+                    if (w < thr) thr = iso_pair_slow<WORDS>(P, srow, spiv, T, m2, p, thr);
+                }
             }
             left -= nh;
             if (left == 0) break;

@@ -114,6 +114,8 @@ SIGNATURES = {
     "dist_get_gamma_limit": (ctypes.c_int, []),
     "dist_set_event_timing": (ctypes.c_int, [ctypes.c_int]),
     "dist_get_event_timing": (ctypes.c_int, []),
+    "dist_set_iso_walk": (ctypes.c_int, [ctypes.c_int]),
+    "dist_get_iso_walk": (ctypes.c_int, []),
     "dist_autotune_codes": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_double,
                                            ctypes.POINTER(Tuning)]),
     "dist_version": (ctypes.c_char_p, []),
@@ -351,6 +353,16 @@ def dist_set_event_timing(on):
 
 def dist_get_event_timing() -> int:
     return lib().dist_get_event_timing()
+
+
+def dist_set_iso_walk(mode):
+    """Walk of dist_solve_isometry on rounds r >= 2: 0 automatic, 1 the split
+    walk wherever it applies (r <= 8), 2 never the split walk."""
+    return _check(lib().dist_set_iso_walk(int(mode)), "dist_set_iso_walk")
+
+
+def dist_get_iso_walk() -> int:
+    return lib().dist_get_iso_walk()
 
 
 def dist_get_tuning() -> dict:

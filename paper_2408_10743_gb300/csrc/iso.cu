@@ -14,12 +14,14 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "../../include/dist.h"
 #include "code.h"
 #include "iso.h"
 #include "solve.h"
+#include "isosplit.cuh"
 #include "packed.cuh"
 #include "rdorder.cuh"
 #include "walk.cuh"
@@ -53,6 +55,10 @@ struct IsoParams {
     uint32_t spl;
     int K, words, CW, r, gamma, exclude;
     uint32_t outside[DIST_MAXCW];
+    // split walk (iso_split_kernel): the terms of round r and their units
+    SplitTerm split[kSplitMaxTerms];
+    unsigned long long split_units;
+    int split_nterms;
 };
 
 __device__ __noinline__ void iso_record(const IsoParams& P, uint32_t w, const uint8_t* s, uint32_t& thr) {
@@ -448,6 +454,234 @@ cudaError_t iso_pair_launch(const IsoParams& P, int words, int sms, size_t optin
     }
 }
 
+// ---------------------------------------------------------------------------
+// Split walk (rounds r >= 2 of large matrices).  The rows are cut into two
+// halves and round r into the products of an i-subset of one half and an
+// (r - i)-subset of the other (isosplit.cuh).  A block claims a unit, stages
+// the sums of its tile-side subsets in shared memory and gives each thread
+// kSplitNB consecutive lane-side sums in registers; each broadcast tile
+// entry is then weighed against all kSplitNB register values.
+//
+// The weight bound of the inner loop takes one popcount per codeword: with
+// c_q = a_q XOR b_q the codeword on filter word q, popc(c_0 | c_1 | c_2) is
+// at most popc(c_0) + popc(c_1) + popc(c_2), so pivot count + popc of the OR
+// of words 0-2 is a lower bound on the weight.  It is tight enough to reject
+// nearly every codeword (on 96 random bits it is about 28 +- 1.9 where the
+// exact sum is 48 +- 4.9), and popcounts, not the XORs, are what the SM
+// runs out of.  A thread keeps the lightest bound over its kSplitNB values;
+// when it beats thr (rare) the values are weighed again one by one with the
+// exact words-0-2 sum, and a codeword that still beats thr in full.
+// ---------------------------------------------------------------------------
+
+// Full Hamming weight of the subset s (r rows) from rows staged with
+// `words` words each (run-time count: only the rare full weighing uses it).
+__device__ __forceinline__ uint32_t iso_full_rt(const uint32_t* srow, int words, const uint8_t* spiv, const uint8_t* s,
+                                                int r) {
+    uint32_t w = 0;
+    for (int t = 0; t < r; t++) w += spiv[s[t]];
+    for (int q = 0; q < words; q++) {
+        uint32_t v = 0;
+        for (int t = 0; t < r; t++) v ^= srow[s[t] * words + q];
+        w += (uint32_t)__popc(v);
+    }
+    return w;
+}
+
+// Full weight of the codeword (tile-side subset of rank tr, lane-side subset
+// of rank lr) and, when it beats thr, its record; returns the new threshold.
+// Called out of line: none of the walk's register values is live across it.
+__device__ __noinline__ uint32_t iso_split_slow(const IsoParams& P, const uint32_t* srow, const uint8_t* spiv,
+                                                const SplitTerm& S, unsigned long long tr, unsigned long long lr,
+                                                uint32_t thr) {
+    uint8_t s[DIST_MAXR];
+    split_rows(P.binom, S.tile_off, S.tile_kh, S.tile_t, tr, s);
+    split_rows(P.binom, S.lane_off, S.lane_kh, S.lane_t, lr, s + S.tile_t);
+    const uint32_t w = iso_full_rt(srow, P.words, spiv, s, P.r);
+    if (w < thr) iso_record(P, w, s, thr);
+    return thr;
+}
+
+// kNp: the matrix has rows without a pivot, so a sum's pivot count depends
+// on its rows and each register value carries its own; otherwise every
+// r-subset has r pivots and the count is folded into the threshold.
+template <bool kNp>
+__global__ void __launch_bounds__(kSplitThreads, 4) iso_split_kernel(const __grid_constant__ IsoParams P) {
+    extern __shared__ __align__(16) uint32_t iso_smem[];
+    __shared__ unsigned long long s_unit;
+    const int K = P.K, words = P.words;
+    SplitRow* stile = reinterpret_cast<SplitRow*>(iso_smem);  // [kSplitTile]: tile-side sums
+    SplitRow* srt = stile + kSplitTile;                       // [K]: words 0-2 of each row, pivot
+    SplitRow* sdt = srt + K;                                  // [K]: rows c and c + 1 XORed, pivot change
+    SplitRow* sval = sdt + K;                                 // [kSplitNB][kSplitThreads]: register sets
+    uint32_t* srow = reinterpret_cast<uint32_t*>(sval + kSplitNB * kSplitThreads);  // [K][words]
+    uint8_t* spiv = reinterpret_cast<uint8_t*>(srow + K * words);
+    const int tid = (int)threadIdx.x;
+    for (int t = tid; t < K * words; t += kSplitThreads) srow[t] = P.rows[t];
+    for (int t = tid; t < K; t += kSplitThreads) spiv[t] = P.piv[t];
+    __syncthreads();
+    for (int t = tid; t < K; t += kSplitThreads) {
+        SplitRow q;
+        q.x = srow[t * words];
+        q.y = words > 1 ? srow[t * words + 1] : 0u;
+        q.z = words > 2 ? srow[t * words + 2] : 0u;
+        q.np = spiv[t];
+        srt[t] = q;
+    }
+    __syncthreads();
+    for (int t = tid; t < K; t += kSplitThreads) {
+        const SplitRow a = srt[t];
+        SplitRow b = {0u, 0u, 0u, 0u};
+        if (t + 1 < K) b = srt[t + 1];
+        SplitRow d;
+        d.x = a.x ^ b.x;
+        d.y = a.y ^ b.y;
+        d.z = a.z ^ b.z;
+        d.np = b.np - a.np;
+        sdt[t] = d;
+    }
+    volatile uint32_t* Up = &P.scr->U;
+    uint32_t thr = DIST_WINF, u_next = *Up;
+    for (;;) {
+        __syncthreads();  // the last unit's tile is read; s_unit is free
+        if (tid == 0) s_unit = atomicAdd(&P.scr->next_chunk, 1ull);
+        __syncthreads();
+        const unsigned long long u = s_unit;
+        if (u >= P.split_units) break;
+        const SplitUnit W = split_unit(P.split, P.split_nterms, u);
+        const SplitTerm& S = P.split[W.term];
+        const unsigned long long t_lo = W.t_lo, t_hi = W.t_hi, l_lo = W.l_lo, l_hi = W.l_hi;
+        unsigned long long q = l_lo + (unsigned long long)tid * W.per;
+        const unsigned long long q_end = min(l_hi, q + W.per);
+        uint64_t T = 0;
+        SplitRow lv = {0u, 0u, 0u, 0u};
+        if (q < q_end) split_unrank(P.binom, srt, S.lane_off, S.lane_kh, S.lane_t, q, &T, &lv);
+        const int ntiles = (int)((t_hi - t_lo + kSplitTile - 1) / kSplitTile);
+        if (ntiles == 1) {  // a short tile side: staged once for all register sets
+            const unsigned long long tr = t_lo + (unsigned long long)tid;
+            if (tr < t_hi) {
+                uint64_t TT;
+                split_unrank(P.binom, srt, S.tile_off, S.tile_kh, S.tile_t, tr, &TT, &stile[tid]);
+            }
+            __syncthreads();
+        }
+        for (uint32_t gi = 0; gi < S.groups; ++gi) {
+            // this thread's next kSplitNB lane-side sums, stepped in a loop
+            // through its own slots of shared memory (the step's registers
+            // are not live beside the register set)
+            const unsigned long long qg = q;  // rank of register value 0
+            for (int j = 0; j < kSplitNB; j++) {
+                SplitRow v = lv;
+                if (q < q_end) {
+                    ++q;
+                    if (q < q_end) split_next(srt, sdt, S.lane_off, S.lane_t, &T, &lv);
+                } else {  // no value: all-zero words, and a pivot count no threshold accepts
+                    v.x = v.y = v.z = 0u;
+                    v.np = DIST_WINF;
+                }
+                sval[j * kSplitThreads + tid] = v;
+            }
+            for (int tt = 0; tt < ntiles; ++tt) {
+                const unsigned long long base = t_lo + (unsigned long long)tt * kSplitTile;
+                const int len = (int)min((unsigned long long)kSplitTile, t_hi - base);
+                if (ntiles > 1) {  // one register set per thread; the tile range staged piece by piece
+                    __syncthreads();
+                    if (tid < len) {
+                        uint64_t TT;
+                        split_unrank(P.binom, srt, S.tile_off, S.tile_kh, S.tile_t, base + (unsigned long long)tid,
+                                     &TT, &stile[tid]);
+                    }
+                    __syncthreads();
+                }
+                // the running bound, read one piece ahead (a stale, larger U
+                // is still a valid threshold)
+                thr = min(thr, u_next);
+                u_next = *Up;
+                // without free rows every codeword has r pivots: the bound
+                // on words 0-2 must stay below thr - r
+                const uint32_t thr_w = kNp ? thr : (thr > (uint32_t)P.r ? thr - (uint32_t)P.r : 0u);
+                int k = 0;
+                for (;;) {
+                    // the register set, (re)loaded from its slots: it is not
+                    // live across the rare weighing below
+                    uint32_t vx[kSplitNB], vy[kSplitNB], vz[kSplitNB], vn[kSplitNB];
+#pragma unroll
+                    for (int j = 0; j < kSplitNB; j++) {
+                        const SplitRow v = sval[j * kSplitThreads + tid];
+                        vx[j] = v.x;
+                        vy[j] = v.y;
+                        vz[j] = v.z;
+                        vn[j] = kNp ? v.np : 0u;
+                    }
+                    for (; k < len; ++k) {
+                        const SplitRow a = stile[k];
+                        uint32_t m = DIST_WINF;
+#pragma unroll
+                        for (int j = 0; j < kSplitNB; j += 2) {
+                            uint32_t w0 = (uint32_t)__popc((a.x ^ vx[j]) | (a.y ^ vy[j]) | (a.z ^ vz[j]));
+                            uint32_t w1 =
+                                (uint32_t)__popc((a.x ^ vx[j + 1]) | (a.y ^ vy[j + 1]) | (a.z ^ vz[j + 1]));
+                            if (kNp) {
+                                w0 += vn[j];
+                                w1 += vn[j + 1];
+                            }
+                            m = __vimin3_u32(m, w0, w1);
+                        }
+                        if (kNp) m += a.np;
+                        if (m < thr_w) break;
+                    }
+                    if (k >= len) break;
+                    // entry k meets a register value whose bound beats thr
+                    // (rare): the exact words-0-2 weight of each, and the
+                    // full weight of any that still beats it
+                    const SplitRow a = stile[k];
+#pragma unroll 1
+                    for (int j = 0; j < kSplitNB; j++) {
+                        const SplitRow v = sval[j * kSplitThreads + tid];
+                        const uint32_t w = a.np + v.np + (uint32_t)__popc(a.x ^ v.x) + (uint32_t)__popc(a.y ^ v.y) +
+                                           (uint32_t)__popc(a.z ^ v.z);
+                        if (w < thr && qg + (unsigned long long)j < q_end)
+                            thr = iso_split_slow(P, srow, spiv, S, base + (unsigned long long)k,
+                                                 qg + (unsigned long long)j, thr);
+                    }
+                    ++k;
+                }
+            }
+        }
+        if (tid == 0) atomicAdd(&P.scr->codewords, (t_hi - t_lo) * (l_hi - l_lo));
+    }
+}
+
+size_t iso_split_smem(int K, int words) {
+    return (size_t)kSplitTile * 16 + (size_t)K * 32 + (size_t)kSplitNB * kSplitThreads * 16 + (size_t)K * words * 4 +
+           (size_t)K + 16;
+}
+
+template <bool kNp>
+cudaError_t iso_split_launch_t(const IsoParams& P, int sms, size_t optin, cudaStream_t st, bool* used) {
+    *used = false;
+    const size_t smem = iso_split_smem(P.K, P.words);
+    if (smem > optin || P.split_units == 0) return cudaSuccess;  // the caller takes another walk
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(iso_split_kernel<kNp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return cudaErrorUnknown;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, iso_split_kernel<kNp>, kSplitThreads, smem) !=
+        cudaSuccess)
+        return cudaErrorUnknown;
+    bps = std::max(1, bps);
+    const int grid = (int)std::min<unsigned long long>(P.split_units, (unsigned long long)sms * bps);
+    iso_split_kernel<kNp><<<std::max(1, grid), kSplitThreads, smem, st>>>(P);
+    *used = true;
+    return cudaGetLastError();
+}
+
+// free_rows: the matrix has rows without a pivot.
+cudaError_t iso_split_launch(const IsoParams& P, bool free_rows, int sms, size_t optin, cudaStream_t st, bool* used) {
+    return free_rows ? iso_split_launch_t<true>(P, sms, optin, st, used)
+                     : iso_split_launch_t<false>(P, sms, optin, st, used);
+}
+
 template <int WORDS>
 cudaError_t iso_rd_launch_w(const IsoParams& P, int sms, cudaStream_t st) {
     const size_t smem = (size_t)P.K * 40 + (size_t)P.K * WORDS * 4 + (size_t)P.K + 16;
@@ -494,6 +728,19 @@ unsigned long long binom_u64(int n, int k) {
 }  // namespace dist
 
 using namespace dist;
+
+namespace {
+std::atomic<int> g_iso_walk{0};
+constexpr unsigned long long kSplitMinCombinations = 1ull << 20;
+}  // namespace
+
+extern "C" int dist_set_iso_walk(int mode) {
+    if (mode < 0 || mode > 2) return DIST_EINVAL;
+    g_iso_walk.store(mode);
+    return DIST_OK;
+}
+
+extern "C" int dist_get_iso_walk(void) { return g_iso_walk.load(); }
 
 extern "C" int dist_solve_isometry(dist_code* c, dist_result* out, void* cuda_stream) {
     if (!c || !out) return DIST_EINVAL;
@@ -570,9 +817,19 @@ extern "C" int dist_solve_isometry(dist_code* c, dist_result* out, void* cuda_st
     int L = iso_lower_bound(ip, 0, m - 1), rounds = 0;
     if (cudaMemcpyAsync(db, img.data(), bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) status = DIST_ECUDA;
     const unsigned long long tw = (unsigned long long)c->dev->sms * 32ull;  // resident warps (4 x 8 per SM)
-    // rounds r >= 2 take the pair-table walk where its table fits in shared
-    // memory, round 1 and larger matrices the revolving-door walk
+    const int walk = g_iso_walk.load(std::memory_order_relaxed);
+    std::vector<unsigned long long> hbinom((DIST_MAXU + 1) * (DIST_MAXR + 1));
+    binom_table(hbinom.data());
+    // rounds r >= 2 take the split walk where it applies, else the pair-table
+    // walk where its table fits in shared memory; round 1 and the rest the
+    // revolving-door walk
     auto launch_step = [&](const IsoParams& P) -> cudaError_t {
+        if (P.split_units) {
+            bool used = false;
+            const cudaError_t e =
+                iso_split_launch(P, ip.G[P.gamma].f > 0, c->dev->sms, c->dev->smem_optin, st, &used);
+            if (e != cudaSuccess || used) return e;
+        }
         if (P.r >= 2) {
             bool used = false;
             const cudaError_t e = iso_pair_launch(P, ip.words, c->dev->sms, c->dev->smem_optin, st, &used);
@@ -610,6 +867,17 @@ extern "C" int dist_solve_isometry(dist_code* c, dist_result* out, void* cuda_st
             P.gamma = j;
             P.exclude = p.n_stab > 0 ? 1 : 0;
             for (int w = 0; w < DIST_MAXCW; w++) P.outside[w] = p.outside[w];
+            if (r >= 2 && walk != 2 && (walk == 1 || nsub >= kSplitMinCombinations)) {
+                // units of about 1/16 of a resident block's share of the round
+                unsigned long long target = nsub / ((unsigned long long)c->dev->sms * 4ull * 16ull);
+                target = std::max(1ull << 15, std::min(target, 1ull << 21));
+                SplitPlan sp;
+                if (split_plan(K, r, target, hbinom.data(), &sp)) {
+                    for (int e = 0; e < sp.nterms; e++) P.split[e] = sp.term[e];
+                    P.split_nterms = sp.nterms;
+                    P.split_units = sp.units;
+                }
+            }
             if (cudaMemsetAsync(&dscr->next_chunk, 0, sizeof(unsigned long long), st) != cudaSuccess ||
                 cudaEventRecord(kit->e0, st) != cudaSuccess ||
                 launch_step(P) != cudaSuccess ||

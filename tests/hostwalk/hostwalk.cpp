@@ -10,6 +10,7 @@
 
 #include "plan.h"
 #include "solve.h"
+#include "isosplit.cuh"
 #include "rdorder.cuh"
 #include "walk.cuh"
 
@@ -484,4 +485,88 @@ extern "C" void hw_rd_delta_walk(int n, int t, unsigned long long rank0, int cou
         memcpy(out + (size_t)k * t, s, t);
         if (k + 1 < count) rd_next_delta(s, t, n, &moves[2 * k], &moves[2 * k + 1]);
     }
+}
+
+// Runs the split walk of the isometry kernel (isosplit.cuh) on the CPU for
+// round r of K rows, unit by unit and thread by thread as the kernel does:
+// each thread's lane-side sums stepped with split_next from one
+// split_unrank, each tile entry by split_unrank.  Every (tile entry, lane
+// value) pair is mapped back to its r-subset, whose colexicographic rank over
+// all K rows is counted in hits[] (C(K, r) entries).  Also checks every sum
+// the walk carries against the sum of the subset's rows (rows: K x 3 words,
+// piv: K flags).  out[0] = units, out[1] = codewords counted per unit as the
+// kernel counts them, out[2] = sums that differ, out[3] = lane values outside
+// their thread's range.  Returns -1 if the split walk does not apply.
+extern "C" int hw_split_cover(int K, int r, unsigned long long target, const uint32_t* rows, const uint8_t* piv,
+                              uint32_t* hits, unsigned long long* out) {
+    std::vector<unsigned long long> B((DIST_MAXU + 1) * (DIST_MAXR + 1));
+    binom_table(B.data());
+    SplitPlan sp;
+    if (!split_plan(K, r, target, B.data(), &sp)) return -1;
+    std::vector<SplitRow> srt(K), sdt(K);
+    for (int t = 0; t < K; t++) srt[t] = SplitRow{rows[3 * t], rows[3 * t + 1], rows[3 * t + 2], piv[t]};
+    for (int t = 0; t < K; t++) {
+        const SplitRow a = srt[t], b = t + 1 < K ? srt[t + 1] : SplitRow{0u, 0u, 0u, 0u};
+        sdt[t] = SplitRow{a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, b.np - a.np};
+    }
+    auto direct = [&](const uint8_t* s, int n) {
+        SplitRow v{0u, 0u, 0u, 0u};
+        for (int t = 0; t < n; t++) split_add(&v, srt[s[t]]);
+        return v;
+    };
+    auto same = [](const SplitRow& a, const SplitRow& b) {
+        return a.x == b.x && a.y == b.y && a.z == b.z && a.np == b.np;
+    };
+    unsigned long long counted = 0, bad = 0, outside = 0;
+    for (unsigned long long u = 0; u < sp.units; u++) {
+        const SplitUnit W = split_unit(sp.term, sp.nterms, u);
+        const SplitTerm& S = sp.term[W.term];
+        counted += (W.t_hi - W.t_lo) * (W.l_hi - W.l_lo);
+        // tile entries of the unit
+        std::vector<SplitRow> tile;
+        std::vector<unsigned long long> trank;
+        for (unsigned long long tr = W.t_lo; tr < W.t_hi; tr++) {
+            SplitRow a;
+            uint64_t TT;
+            split_unrank(B.data(), srt.data(), S.tile_off, S.tile_kh, S.tile_t, tr, &TT, &a);
+            uint8_t st[kSplitMaxT];
+            split_rows(B.data(), S.tile_off, S.tile_kh, S.tile_t, tr, st);
+            if (!same(direct(st, S.tile_t), a)) bad++;
+            tile.push_back(a);
+            trank.push_back(tr);
+        }
+        for (int tid = 0; tid < kSplitThreads; tid++) {
+            unsigned long long q = W.l_lo + (unsigned long long)tid * W.per;
+            const unsigned long long q_end = std::min(W.l_hi, q + W.per);
+            uint64_t T = 0;
+            SplitRow lv = {0u, 0u, 0u, 0u};
+            if (q < q_end) split_unrank(B.data(), srt.data(), S.lane_off, S.lane_kh, S.lane_t, q, &T, &lv);
+            for (uint32_t gi = 0; gi < S.groups; ++gi) {
+                for (int j = 0; j < kSplitNB; j++) {
+                    if (q >= q_end) break;
+                    const unsigned long long lr = q;
+                    if (lr < W.l_lo || lr >= W.l_hi) outside++;
+                    uint8_t sl[kSplitMaxT];
+                    split_rows(B.data(), S.lane_off, S.lane_kh, S.lane_t, lr, sl);
+                    if (!same(direct(sl, S.lane_t), lv)) bad++;
+                    for (size_t k = 0; k < tile.size(); k++) {
+                        uint8_t s[2 * kSplitMaxT];
+                        split_rows(B.data(), S.tile_off, S.tile_kh, S.tile_t, trank[k], s);
+                        memcpy(s + S.tile_t, sl, S.lane_t);
+                        std::sort(s, s + r);
+                        unsigned long long rank = 0;
+                        for (int t = 0; t < r; t++) rank += B[(size_t)s[t] * (DIST_MAXR + 1) + t + 1];
+                        hits[rank]++;
+                    }
+                    ++q;
+                    if (q < q_end) split_next(srt.data(), sdt.data(), S.lane_off, S.lane_t, &T, &lv);
+                }
+            }
+        }
+    }
+    out[0] = sp.units;
+    out[1] = counted;
+    out[2] = bad;
+    out[3] = outside;
+    return 0;
 }

@@ -91,7 +91,7 @@ def test_qc72_and_work_comparison():
 def test_batch_codes_vs_oracle_table():
     """The isometry method on 256 of the batch workload's random codes
     (n 16-56, so rounds up to 8 of matrices of up to 56 rows, through the
-    pair and triple walks): every d equals the stored oracle value."""
+    split, pair and lane walks): every d equals the stored oracle value."""
     from codes import load_oracle_table
     _, table = load_oracle_table("batch4096_oracle.txt")
     gens = synth.batch_codes(256)
@@ -104,3 +104,49 @@ def test_batch_codes_vs_oracle_table():
         else:
             assert lo <= r["d"] <= hi, i
         valid(g, r)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_every_walk_vs_oracle(mode):
+    """The split walk on every round r in [2, 8] (mode 1), and never (mode
+    2): the same distances as the oracle and valid witnesses, on tiny codes
+    (rounds up to the whole matrix, halves of one or two rows), medium
+    codes, F4 inputs and exclusion."""
+    dist.dist_set_iso_walk(mode)
+    try:
+        rng = np.random.default_rng(4100 + mode)
+        for t in range(80):
+            n = int(rng.integers(1, 9))
+            K = int(rng.integers(1, min(2 * n, 12) + 1))
+            g = tiny_random_code(rng, n, K, ["iid", "css", "yheavy", "sparse"][t % 4])
+            if not g.any():
+                continue
+            r = iso(g)
+            assert r["d"] == oracle.bz(g)["d"], (mode, t)
+            valid(g, r)
+        for t in range(8):
+            rs = synth.Xoshiro256ss(8100 + t)
+            n = 16 + rs.below(25)
+            K = (n + 1) // 2 + rs.below(n - (n + 1) // 2 + 1)
+            g = synth.random_f2_code(n, K, rs)
+            r = iso(g)
+            assert r["d"] == oracle.bz(g)["d"], (mode, n, K)
+            valid(g, r)
+        g4 = synth.single_f4(0)
+        r = iso(g4, field=4)
+        assert r["d"] == oracle.bz(g4, field=4)["d"]
+        valid(g4, r, field=4)
+        for L in (3, 4):
+            N, s_ = toric(L)
+            r = iso(N, n_stab=s_)
+            assert r["d"] == L
+            valid(N, r)
+    finally:
+        dist.dist_set_iso_walk(0)
+    assert dist.dist_get_iso_walk() == 0
+
+
+def test_iso_walk_setting():
+    with pytest.raises(dist.DistError):
+        dist.dist_set_iso_walk(3)
+    assert dist.dist_get_iso_walk() == 0

@@ -68,6 +68,10 @@ def hw():
     L.hw_launch_digest.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)]
     L.hw_set_tuning.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hw_split_cover.restype = ctypes.c_int
+    L.hw_split_cover.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_uint32),
+                                 ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_uint32),
+                                 ctypes.POINTER(ctypes.c_ulonglong)]
     L.hw_solve_sliced.restype = ctypes.c_int
     L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -389,6 +393,47 @@ def test_rd_delta_walk(hw):
             for k in range(cnt - 1):
                 a, b = set(got[k]), set(got[k + 1])
                 assert a - b == {mv[2 * k]} and b - a == {mv[2 * k + 1]}, (n, t, k)
+
+
+@pytest.mark.parametrize("K,r,target", [
+    (2, 1, 1 << 15), (2, 2, 1 << 15), (3, 2, 1 << 15), (7, 3, 1 << 15), (8, 8, 1 << 15), (9, 8, 1 << 15),
+    (13, 5, 1 << 15), (17, 8, 1 << 15), (20, 4, 1 << 21), (24, 6, 1 << 15), (24, 6, 1 << 21),
+    (30, 6, 1 << 15), (30, 6, 1 << 21), (31, 7, 1 << 15), (256, 2, 1 << 15), (200, 3, 1 << 21),
+    (40, 7, 1 << 15), (48, 6, 1 << 21)])
+def test_split_walk_covers_every_subset_once(hw, K, r, target):
+    """The isometry kernel's split walk (isosplit.cuh), run unit by unit and
+    thread by thread on the CPU: every r-subset of the K rows is one (tile
+    entry, lane value) pair of exactly one unit, the codewords counted per
+    unit add up to C(K, r), no thread steps outside its range, and every sum
+    the walk carries (unranked or stepped, with free rows among the rows)
+    equals the sum of its subset's rows.  Cases with a thin term (one side of
+    a single subset), several register sets per thread, tile ranges of
+    several staged pieces and several tile ranges per term, and one-sided
+    terms split again (K = 40 and 48)."""
+    rng = np.random.default_rng(K * 100 + r)
+    rows = rng.integers(0, 1 << 32, size=3 * K, dtype=np.uint64).astype(np.uint32)
+    piv = (rng.random(K) < 0.8).astype(np.uint8)
+    total = comb(K, r)
+    hits = np.zeros(total, dtype=np.uint32)
+    out = (ctypes.c_ulonglong * 4)()
+    rc = hw.hw_split_cover(K, r, target, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                           piv.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                           hits.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), out)
+    assert rc == 0
+    assert out[1] == total and out[2] == 0 and out[3] == 0, list(out)
+    assert hits.min() == 1 and hits.max() == 1
+
+
+def test_split_plan_limits(hw):
+    """The split walk applies to rounds 1..8 of 2..256 rows only."""
+    out = (ctypes.c_ulonglong * 4)()
+    hits = np.zeros(1, dtype=np.uint32)
+    rows = np.zeros(3 * 300, dtype=np.uint32)
+    piv = np.ones(300, dtype=np.uint8)
+    args = (rows.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), piv.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+            hits.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), out)
+    for K, r in ((1, 1), (20, 9), (20, 0), (257, 2)):
+        assert hw.hw_split_cover(K, r, 1 << 15, *args) == -1
 
 
 def test_rechunk_equals_fresh_plan(hw):

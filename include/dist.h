@@ -157,7 +157,7 @@ int dist_solve_isometry(dist_code *c, dist_result *out, void *cuda_stream);
  * Which walk dist_solve_isometry runs on rounds r >= 2 (process-wide).
  * 0 (the default): the split walk (rows cut into two halves, every r-subset a
  * product of one subset of each) on rounds of at most 8 rows with at least
- * 2^20 combinations, the pair-table walk on the other rounds whose table fits
+ * 2^18 combinations, the pair-table walk on the other rounds whose table fits
  * in shared memory, the revolving-door lane walk elsewhere.  1: the split
  * walk on every round r in [2, 8].  2: never the split walk.  Affects speed,
  * never results.  DIST_EINVAL for other values.

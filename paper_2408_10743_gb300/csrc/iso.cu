@@ -501,11 +501,17 @@ __device__ __noinline__ uint32_t iso_split_slow(const IsoParams& P, const uint32
     return thr;
 }
 
-// kNp: the matrix has rows without a pivot, so a sum's pivot count depends
-// on its rows and each register value carries its own; otherwise every
-// r-subset has r pivots and the count is folded into the threshold.
-template <bool kNp>
+// kMode: 0, every row of the matrix has a pivot, so every r-subset has r
+// pivots and the count is folded into the threshold; 1, some rows have none,
+// so each register value carries its own pivot count; 2, most rows have
+// none, and the pivot count no longer carries most of the bound (a matrix of
+// rank 1 has one pivot row), so the bound takes a second popcount:
+// popc(c_0 | c_1) + popc(c_2), about 40 +- 3.5 on random words (the OR of
+// all three, 28 +- 1.9, let about one codeword in a hundred through to the
+// exact weighing on such a matrix).
+template <int kMode>
 __global__ void __launch_bounds__(kSplitThreads, 4) iso_split_kernel(const __grid_constant__ IsoParams P) {
+    constexpr bool kNp = kMode > 0;
     extern __shared__ __align__(16) uint32_t iso_smem[];
     __shared__ unsigned long long s_unit;
     const int K = P.K, words = P.words;
@@ -617,12 +623,16 @@ __global__ void __launch_bounds__(kSplitThreads, 4) iso_split_kernel(const __gri
                         uint32_t m = DIST_WINF;
 #pragma unroll
                         for (int j = 0; j < kSplitNB; j += 2) {
-                            uint32_t w0 = (uint32_t)__popc((a.x ^ vx[j]) | (a.y ^ vy[j]) | (a.z ^ vz[j]));
-                            uint32_t w1 =
-                                (uint32_t)__popc((a.x ^ vx[j + 1]) | (a.y ^ vy[j + 1]) | (a.z ^ vz[j + 1]));
-                            if (kNp) {
-                                w0 += vn[j];
-                                w1 += vn[j + 1];
+                            uint32_t w0, w1;
+                            if (kMode == 2) {
+                                w0 = (uint32_t)__popc((a.x ^ vx[j]) | (a.y ^ vy[j])) + (uint32_t)__popc(a.z ^ vz[j]) +
+                                     vn[j];
+                                w1 = (uint32_t)__popc((a.x ^ vx[j + 1]) | (a.y ^ vy[j + 1])) +
+                                     (uint32_t)__popc(a.z ^ vz[j + 1]) + vn[j + 1];
+                            } else {
+                                w0 = (uint32_t)__popc((a.x ^ vx[j]) | (a.y ^ vy[j]) | (a.z ^ vz[j])) + vn[j];
+                                w1 = (uint32_t)__popc((a.x ^ vx[j + 1]) | (a.y ^ vy[j + 1]) | (a.z ^ vz[j + 1])) +
+                                     vn[j + 1];
                             }
                             m = __vimin3_u32(m, w0, w1);
                         }
@@ -656,30 +666,31 @@ size_t iso_split_smem(int K, int words) {
            (size_t)K + 16;
 }
 
-template <bool kNp>
+template <int kMode>
 cudaError_t iso_split_launch_t(const IsoParams& P, int sms, size_t optin, cudaStream_t st, bool* used) {
     *used = false;
     const size_t smem = iso_split_smem(P.K, P.words);
     if (smem > optin || P.split_units == 0) return cudaSuccess;  // the caller takes another walk
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(iso_split_kernel<kNp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaFuncSetAttribute(iso_split_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
         return cudaErrorUnknown;
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, iso_split_kernel<kNp>, kSplitThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, iso_split_kernel<kMode>, kSplitThreads, smem) !=
         cudaSuccess)
         return cudaErrorUnknown;
     bps = std::max(1, bps);
     const int grid = (int)std::min<unsigned long long>(P.split_units, (unsigned long long)sms * bps);
-    iso_split_kernel<kNp><<<std::max(1, grid), kSplitThreads, smem, st>>>(P);
+    iso_split_kernel<kMode><<<std::max(1, grid), kSplitThreads, smem, st>>>(P);
     *used = true;
     return cudaGetLastError();
 }
 
-// free_rows: the matrix has rows without a pivot.
-cudaError_t iso_split_launch(const IsoParams& P, bool free_rows, int sms, size_t optin, cudaStream_t st, bool* used) {
-    return free_rows ? iso_split_launch_t<true>(P, sms, optin, st, used)
-                     : iso_split_launch_t<false>(P, sms, optin, st, used);
+// free_rows: rows of the matrix without a pivot, of K.
+cudaError_t iso_split_launch(const IsoParams& P, int free_rows, int sms, size_t optin, cudaStream_t st, bool* used) {
+    if (free_rows == 0) return iso_split_launch_t<0>(P, sms, optin, st, used);
+    if (4 * free_rows <= P.K) return iso_split_launch_t<1>(P, sms, optin, st, used);
+    return iso_split_launch_t<2>(P, sms, optin, st, used);
 }
 
 template <int WORDS>
@@ -731,7 +742,7 @@ using namespace dist;
 
 namespace {
 std::atomic<int> g_iso_walk{0};
-constexpr unsigned long long kSplitMinCombinations = 1ull << 20;
+constexpr unsigned long long kSplitMinCombinations = 1ull << 18;
 }  // namespace
 
 extern "C" int dist_set_iso_walk(int mode) {
@@ -826,8 +837,7 @@ extern "C" int dist_solve_isometry(dist_code* c, dist_result* out, void* cuda_st
     auto launch_step = [&](const IsoParams& P) -> cudaError_t {
         if (P.split_units) {
             bool used = false;
-            const cudaError_t e =
-                iso_split_launch(P, ip.G[P.gamma].f > 0, c->dev->sms, c->dev->smem_optin, st, &used);
+            const cudaError_t e = iso_split_launch(P, ip.G[P.gamma].f, c->dev->sms, c->dev->smem_optin, st, &used);
             if (e != cudaSuccess || used) return e;
         }
         if (P.r >= 2) {

@@ -663,6 +663,11 @@ def run_ours(args):
                    "codewords_per_s": best["codewords"] / max(best["gpu_seconds"], 1e-12),
                    "work_vs_packages": best["codewords"] / (total_cw / args.steps),
                    "time_vs_packages": best["seconds"] / statistics.mean(step_s)}
+        # the split walk's bound takes one popcount per codeword: its ceiling
+        # is the measured popcount rate
+        iso_cmp["popc_ceiling_Gcodewords_per_s"] = peak.popc_per_s / 1e9
+        iso_cmp["frac_of_popc_ceiling"] = (iso_cmp["codewords_per_s"] / peak.popc_per_s
+                                           if peak.popc_per_s else None)
     # the same code planned on the identity qubit order only (no
     # information-set search): a longer enumeration of the same kernel, the
     # single-code roofline on a launch long enough to fill the GPU

@@ -150,3 +150,21 @@ def test_iso_walk_setting():
     with pytest.raises(dist.DistError):
         dist.dist_set_iso_walk(3)
     assert dist.dist_get_iso_walk() == 0
+
+
+def test_split_walk_on_240_rows():
+    """An F4 [I_120 | A] code of length 128: its image has 240 rows, so the
+    split walk's halves hold 120 rows each and its row indices run to 239;
+    rounds 2-5 of two matrices, in the default walk and with the split walk
+    on every round.  d as the oracle."""
+    g4 = synth.f4_systematic(128, 120, synth.Xoshiro256ss(6))
+    want = oracle.bz(g4, field=4)["d"]
+    for mode in (0, 1):
+        dist.dist_set_iso_walk(mode)
+        try:
+            r = iso(g4, field=4)
+        finally:
+            dist.dist_set_iso_walk(0)
+        assert r["d"] == want, mode
+        assert r["rounds"] >= 3
+        valid(g4, r, field=4)

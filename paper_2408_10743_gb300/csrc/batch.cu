@@ -42,7 +42,8 @@ namespace dist {
 cudaError_t slice_graph_build(unsigned char* d_arena, unsigned char* h_arena, const unsigned long long* binom,
                               int grid, int aux_grid, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st,
                               cudaGraph_t* graph, cudaGraphExec_t* exec, cudaGraphNode_t* h2d,
-                              cudaGraphNode_t* d2h);
+                              cudaGraphNode_t* d2h, cudaGraphNode_t* knode);
+cudaError_t slice_graph_set_two(cudaGraphExec_t exec, cudaGraphNode_t knode, int two);
 }  // namespace dist
 
 using namespace dist;
@@ -144,12 +145,14 @@ struct dist_batch {
     DevBuf<unsigned char> arena;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    cudaGraphNode_t n_h2d = nullptr, n_d2h = nullptr;
+    cudaGraphNode_t n_h2d = nullptr, n_d2h = nullptr, n_enum = nullptr;
+    int graph_two = 0;  // the instance the graph's multi-code launch runs
     void drop_graph() {
         if (gexec) cudaGraphExecDestroy(gexec);
         if (graph) cudaGraphDestroy(graph);
         gexec = nullptr;
         graph = nullptr;
+        graph_two = 0;
     }
 
     void run();
@@ -387,8 +390,15 @@ int dist_batch::slice() {
     memset(h + hd.off_sched, 0, 2 * sizeof(unsigned long long));
     const int grid = dev->sms * dev->batch_blocks_per_sm;
     if (!gexec && slice_graph_build(arena.d, arena.h, dev->d_binom, grid, 2 * dev->sms, e0, e1, st, &graph,
-                                    &gexec, &n_h2d, &n_d2h) != cudaSuccess)
+                                    &gexec, &n_h2d, &n_d2h, &n_enum) != cudaSuccess)
         return DIST_ECUDA;
+    // the two-word filter only where a code has three or more words per plane
+    int two = 0;
+    for (int i = 0; i < n && !two; i++) two = run[i]->c->plan.W >= 3 ? 1 : 0;
+    if (two != graph_two) {
+        if (slice_graph_set_two(gexec, n_enum, two) != cudaSuccess) return DIST_ECUDA;
+        graph_two = two;
+    }
     const double t_launch = wall_now();
     plan_seconds += t_launch - t_plan;
     // one upload, the slice graph, one read-back
@@ -541,7 +551,8 @@ int dist_batch_create(dist_batch** out, const dist_batch_opts* opts) {
     };
     if (!b->arena.ensure(kArenaInitialBytes)) return fail(DIST_ENOMEM);
     if (slice_graph_build(b->arena.d, b->arena.h, dev->d_binom, dev->sms * dev->batch_blocks_per_sm, 2 * dev->sms,
-                          b->e0, b->e1, b->st, &b->graph, &b->gexec, &b->n_h2d, &b->n_d2h) != cudaSuccess)
+                          b->e0, b->e1, b->st, &b->graph, &b->gexec, &b->n_h2d, &b->n_d2h, &b->n_enum) !=
+        cudaSuccess)
         return fail(DIST_ECUDA);
     b->worker = std::thread([b] { b->run(); });
     *out = b;

@@ -269,6 +269,11 @@ __device__ __forceinline__ void slice_params(const unsigned char* arena, const u
     P->budget_ns = H->budget_ns;
 }
 
+// kTwo: with the two-word filter (as enum_kernel).  The host takes the
+// instance without it unless a code of the slice has three or more words per
+// plane (for up to two words the filter's registers cost more than it saves:
+// 25.1 against 26.9 ms on 4096 codes of n <= 56).
+template <bool kTwo>
 __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB)
     enum_batch_kernel(const unsigned char* __restrict__ arena, const unsigned long long* binom) {
     __shared__ BatchParams sP;
@@ -358,7 +363,8 @@ __global__ void __launch_bounds__(DIST_ENUM_THREADS, DIST_ENUM_MINB)
         __syncwarp();
         DevSink sink{bc.scr};
         unsigned long long lo, hi, done = 0;
-        if (seg_lane_range(sg, chunk, lane, lo, hi)) done = walk_range(C, sink, thr, sg, lo, hi, sink.peek());
+        if (seg_lane_range(sg, chunk, lane, lo, hi))
+            done = walk_range<DevSink, kTwo>(C, sink, thr, sg, lo, hi, sink.peek());
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) done += __shfl_xor_sync(0xffffffffu, done, off);
         int stop = 0;
@@ -423,11 +429,13 @@ __global__ void batch_gather_kernel(unsigned char* __restrict__ arena) {
 // multi-code launch between the two timing events, the gather and the
 // read-back of the results.  It is captured once per arena allocation (the
 // kernels' arguments are the arena and the binomial table); before each
-// replay the two copies get the slice's sizes (*h2d, *d2h: their nodes).
+// replay the two copies get the slice's sizes (*h2d, *d2h: their nodes).  The
+// multi-code launch (*knode) is captured without the two-word filter;
+// slice_graph_set_two switches it.
 cudaError_t slice_graph_build(unsigned char* d_arena, unsigned char* h_arena, const unsigned long long* binom,
                               int grid, int aux_grid, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st,
                               cudaGraph_t* graph, cudaGraphExec_t* exec, cudaGraphNode_t* h2d,
-                              cudaGraphNode_t* d2h) {
+                              cudaGraphNode_t* d2h, cudaGraphNode_t* knode) {
     *graph = nullptr;
     *exec = nullptr;
     cudaError_t err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -436,7 +444,7 @@ cudaError_t slice_graph_build(unsigned char* d_arena, unsigned char* h_arena, co
     cudaMemcpyAsync(d_arena, h_arena, sizeof(SliceHeader), cudaMemcpyHostToDevice, st);
     batch_init_kernel<<<aux_grid, 128, 0, st>>>(d_arena);
     cudaEventRecordWithFlags(e0, st, cudaEventRecordExternal);
-    enum_batch_kernel<<<grid, DIST_ENUM_THREADS, 0, st>>>(d_arena, binom);
+    enum_batch_kernel<false><<<grid, DIST_ENUM_THREADS, 0, st>>>(d_arena, binom);
     cudaEventRecordWithFlags(e1, st, cudaEventRecordExternal);
     batch_gather_kernel<<<aux_grid, 128, 0, st>>>(d_arena);
     cudaMemcpyAsync(h_arena, d_arena, sizeof(SliceHeader), cudaMemcpyDeviceToHost, st);
@@ -452,16 +460,23 @@ cudaError_t slice_graph_build(unsigned char* d_arena, unsigned char* h_arena, co
     err = cudaGraphGetNodes(*graph, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
     if (err == cudaSuccess) err = cudaGraphGetNodes(*graph, nodes.data(), &nn);
-    *h2d = *d2h = nullptr;
+    *h2d = *d2h = *knode = nullptr;
     for (size_t k = 0; err == cudaSuccess && k < nn; k++) {
         cudaGraphNodeType t;
-        if ((err = cudaGraphNodeGetType(nodes[k], &t)) != cudaSuccess || t != cudaGraphNodeTypeMemcpy) continue;
+        if ((err = cudaGraphNodeGetType(nodes[k], &t)) != cudaSuccess) break;
+        if (t == cudaGraphNodeTypeKernel) {
+            cudaKernelNodeParams kp;
+            if ((err = cudaGraphKernelNodeGetParams(nodes[k], &kp)) != cudaSuccess) break;
+            if (kp.func == reinterpret_cast<void*>(enum_batch_kernel<false>)) *knode = nodes[k];
+            continue;
+        }
+        if (t != cudaGraphNodeTypeMemcpy) continue;
         cudaMemcpy3DParms mp;
         if ((err = cudaGraphMemcpyNodeGetParams(nodes[k], &mp)) != cudaSuccess) break;
         if (mp.dstPtr.ptr == static_cast<void*>(d_arena)) *h2d = nodes[k];
         else if (mp.dstPtr.ptr == static_cast<void*>(h_arena)) *d2h = nodes[k];
     }
-    if (err == cudaSuccess && (!*h2d || !*d2h)) err = cudaErrorUnknown;
+    if (err == cudaSuccess && (!*h2d || !*d2h || !*knode)) err = cudaErrorUnknown;
     if (err == cudaSuccess) err = cudaGraphInstantiate(exec, *graph, 0);
     if (err != cudaSuccess) {
         cudaGraphDestroy(*graph);
@@ -471,10 +486,25 @@ cudaError_t slice_graph_build(unsigned char* d_arena, unsigned char* h_arena, co
     return err;
 }
 
+// The slice graph's multi-code launch with (two != 0) or without the
+// two-word filter, for the replays that follow.
+cudaError_t slice_graph_set_two(cudaGraphExec_t exec, cudaGraphNode_t knode, int two) {
+    cudaKernelNodeParams kp;
+    cudaError_t err = cudaGraphKernelNodeGetParams(knode, &kp);
+    if (err != cudaSuccess) return err;
+    kp.func = two ? reinterpret_cast<void*>(enum_batch_kernel<true>) : reinterpret_cast<void*>(enum_batch_kernel<false>);
+    return cudaGraphExecKernelNodeSetParams(exec, knode, &kp);
+}
+
+// Both instances: the occupancy of the more demanding one.
 int batch_blocks_per_sm() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, enum_batch_kernel, DIST_ENUM_THREADS, 0) != cudaSuccess) return 0;
-    return nb;
+    int n1 = 0, n2 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, enum_batch_kernel<false>, DIST_ENUM_THREADS, 0) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, enum_batch_kernel<true>, DIST_ENUM_THREADS, 0) !=
+            cudaSuccess)
+        return 0;
+    return n1 < n2 ? n1 : n2;
 }
 
 size_t enum_smem_bytes(const EnumParams& P) { return (size_t)P.s_words * 4; }

@@ -82,6 +82,24 @@ typedef struct dist_code dist_code;
 int dist_init(dist_code **out, const uint8_t *generator, int n, int K, int field);
 
 /*
+ * dist_init_many -- dist_init of count codes in one call (steps S1-S2 for a
+ * batch, Sections 2.2-2.3): the codes are ingested and diagonalized on the
+ * library's host threads (one per hardware thread beyond the caller's, at
+ * most 15), and their device blocks are carved from one allocation, which
+ * is freed with the last of its codes.
+ *   out[i]:                      the code (NULL where status[i] < 0).
+ *   generators[i], n[i], K[i], field[i]: as dist_init (host memory, read
+ *                                during the call).
+ *   status[i]:                   DIST_OK or the error dist_init would return.
+ * Every array has count entries; count = 0 is accepted.  Returns DIST_OK if
+ * every code was initialised, else the status of the first that was not
+ * (the others are initialised and must be released with dist_free).
+ * DIST_EINVAL if count < 0 or an array is NULL.
+ */
+int dist_init_many(dist_code **out, int count, const uint8_t *const *generators, const int *n, const int *K,
+                   const int *field, int *status);
+
+/*
  * dist_set_exclude -- take the minimum over C minus S, S = span of the first
  * n_stab input rows (F4: their F4-span).  With a normalizer matrix whose
  * first rows generate the stabilizer this is d(Q) = wt_s(N \ S), the check of

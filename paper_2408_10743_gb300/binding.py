@@ -80,6 +80,9 @@ _U8P = ctypes.POINTER(ctypes.c_uint8)
 _VP = ctypes.c_void_p
 SIGNATURES = {
     "dist_init": (ctypes.c_int, [ctypes.POINTER(_VP), _U8P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "dist_init_many": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_U8P),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "dist_set_exclude": (ctypes.c_int, [_VP, ctypes.c_int]),
     "dist_solve": (ctypes.c_int, [_VP, ctypes.POINTER(DistResult), _VP]),
     "dist_solve_bounded": (ctypes.c_int, [_VP, ctypes.POINTER(DistResult), _VP, ctypes.c_double]),
@@ -186,6 +189,31 @@ def dist_init(generator, n, K, field):
     g = np.ascontiguousarray(np.asarray(generator, dtype=np.uint8))
     _check(lib().dist_init(ctypes.byref(h), _ptr(g), n, K, field), "dist_init")
     return h
+
+
+def dist_init_many(generators, field=None):
+    """dist_init of many codes in one call.  generators: a list of 2-D arrays
+    (field: one value or a list, DIST_F2 by default).  Returns (handles,
+    statuses): a handle per code (None where its status is an error)."""
+    count = len(generators)
+    fields = [DIST_F2] * count if field is None else (list(field) if isinstance(field, (list, tuple)) else [field] * count)
+    arrs, ns, Ks = [], [], []
+    for g, f in zip(generators, fields):
+        a, n, K = _as_gen(g, f)
+        arrs.append(a)
+        ns.append(n)
+        Ks.append(K)
+    ptrs = (_U8P * max(count, 1))(*[_ptr(a) for a in arrs])
+    c_n = (ctypes.c_int * max(count, 1))(*ns)
+    c_K = (ctypes.c_int * max(count, 1))(*Ks)
+    c_f = (ctypes.c_int * max(count, 1))(*fields)
+    c_st = (ctypes.c_int * max(count, 1))()
+    hs = (_VP * max(count, 1))()
+    rc = lib().dist_init_many(hs, count, ptrs, c_n, c_K, c_f, c_st)
+    if rc == DIST_EINVAL and count and all(c_st[i] == 0 for i in range(count)):
+        _check(rc, "dist_init_many")
+    handles = [_VP(hs[i]) if hs[i] else None for i in range(count)]
+    return handles, [int(c_st[i]) for i in range(count)]
 
 
 def dist_set_exclude(handle, n_stab):
@@ -417,6 +445,28 @@ class Code:
         g, n, K = _as_gen(generator, field)
         self.n, self.K, self.field = n, K, field
         self._h = dist_init(g, n, K, field)
+
+    @classmethod
+    def many(cls, generators, field=DIST_F2):
+        """Codes for a list of generator matrices, initialised together
+        (dist_init_many: planning on the library's host threads, one device
+        allocation).  Raises DistError for the first code that fails, after
+        releasing the others."""
+        handles, statuses = dist_init_many(generators, field)
+        bad = [i for i, st in enumerate(statuses) if st != 0]
+        if bad:
+            for h in handles:
+                if h is not None:
+                    dist_free(h)
+            _check(statuses[bad[0]], "dist_init_many (code %d)" % bad[0])
+        codes = []
+        for g, h in zip(generators, handles):
+            self = cls.__new__(cls)
+            _, self.n, self.K = _as_gen(g, field)
+            self.field = field
+            self._h = h
+            codes.append(self)
+        return codes
 
     @classmethod
     def from_stabilizers(cls, stabilizers):

@@ -11,6 +11,7 @@
 
 #include "../../include/dist.h"
 #include "code.h"
+#include "pool.h"
 #include "plan.h"
 #include "solve.h"
 
@@ -199,8 +200,22 @@ namespace {
 
 void release(dist_code* c) {
     if (!c) return;
-    if (c->d_block) block_release(c->dev, c->d_block, c->block_cap);
+    if (c->slab) {
+        if (c->slab->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+            cudaFree(c->slab->base);
+            delete c->slab;
+        }
+    } else if (c->d_block) {
+        block_release(c->dev, c->d_block, c->block_cap);
+    }
     delete c;
+}
+
+// The device block's layout: tables, then scratch, then the segment table.
+void place_block(dist_code* c, size_t tbytes) {
+    c->d_tables = static_cast<uint32_t*>(c->d_block);
+    c->d_scr = reinterpret_cast<Scratch*>(static_cast<unsigned char*>(c->d_block) + tbytes);
+    c->d_segs = reinterpret_cast<SegDesc*>(reinterpret_cast<unsigned char*>(c->d_scr) + align256(sizeof(Scratch)));
 }
 
 // Runs one enumeration launch per call on the GPU (the executor of
@@ -364,9 +379,7 @@ int dist_init(dist_code** out, const uint8_t* generator, int n, int K, int field
         release(c);
         return rc;
     }
-    c->d_tables = static_cast<uint32_t*>(c->d_block);
-    c->d_scr = reinterpret_cast<Scratch*>(static_cast<unsigned char*>(c->d_block) + tbytes);
-    c->d_segs = reinterpret_cast<SegDesc*>(reinterpret_cast<unsigned char*>(c->d_scr) + align256(sizeof(Scratch)));
+    place_block(c, tbytes);
     // Small tables go to the device with the first solve (one copy fewer
     // here); larger ones now.
     if (words * 4 > kKitTableBytes) {
@@ -378,6 +391,94 @@ int dist_init(dist_code** out, const uint8_t* generator, int n, int K, int field
     }
     *out = c;
     return DIST_OK;
+}
+
+int dist_init_many(dist_code** out, int count, const uint8_t* const* generators, const int* n, const int* K,
+                   const int* field, int* status) {
+    if (count < 0 || (count > 0 && (!out || !generators || !n || !K || !field || !status))) return DIST_EINVAL;
+    for (int i = 0; i < count; i++) {
+        out[i] = nullptr;
+        status[i] = DIST_OK;
+    }
+    if (count == 0) return DIST_OK;
+    DeviceCtx* dev = nullptr;
+    int rc = device_ctx(&dev);
+    if (rc) {
+        for (int i = 0; i < count; i++) status[i] = rc;
+        return rc;
+    }
+    // steps S1-S2 of every code on the host threads
+    std::vector<dist_code*> cs((size_t)count, nullptr);
+    HostPool::get().run((size_t)count, 4, [&](size_t a, size_t b) {
+        for (size_t i = a; i < b; i++) {
+            if (!generators[i]) {
+                status[i] = DIST_EINVAL;
+                continue;
+            }
+            dist_code* c = new (std::nothrow) dist_code();
+            if (!c) {
+                status[i] = DIST_ENOMEM;
+                continue;
+            }
+            const int prc = map_plan_rc(plan_build(generators[i], n[i], K[i], field[i], &c->plan));
+            if (prc) {
+                delete c;
+                status[i] = prc;
+                continue;
+            }
+            cs[i] = c;
+        }
+    });
+    // one device allocation for all of them: each code's block holds its
+    // tables, scratch and segment table, 256-byte aligned
+    std::vector<size_t> off((size_t)count, 0);
+    size_t total = 0;
+    int live = 0;
+    for (int i = 0; i < count; i++) {
+        if (!cs[i]) continue;
+        off[i] = total;
+        total += align256(align256(cs[i]->plan.tables.size() * 4) + state_bytes());
+        live++;
+    }
+    DevSlab* slab = nullptr;
+    if (live > 0) {
+        slab = new (std::nothrow) DevSlab();
+        if (!slab || cudaMalloc(&slab->base, total) != cudaSuccess) {
+            delete slab;
+            for (int i = 0; i < count; i++)
+                if (cs[i]) {
+                    delete cs[i];
+                    cs[i] = nullptr;
+                    status[i] = DIST_ENOMEM;
+                }
+            slab = nullptr;
+        } else {
+            slab->refs.store(live);
+        }
+    }
+    int first_err = DIST_OK;
+    for (int i = 0; i < count; i++) {
+        dist_code* c = cs[i];
+        if (c) {
+            const size_t tbytes = align256(c->plan.tables.size() * 4);
+            c->dev = dev;
+            c->slab = slab;
+            c->d_block = static_cast<unsigned char*>(slab->base) + off[i];
+            c->block_cap = align256(tbytes + state_bytes());
+            place_block(c, tbytes);
+            if (c->plan.tables.size() * 4 > kKitTableBytes) {  // as dist_init: larger tables now
+                const int urc = upload_tables(c);
+                if (urc) {
+                    release(c);
+                    c = nullptr;
+                    status[i] = urc;
+                }
+            }
+            out[i] = c;
+        }
+        if (status[i] && first_err == DIST_OK) first_err = status[i];
+    }
+    return first_err;
 }
 
 int dist_normalizer(const uint8_t* stabilizers, int n, int m, uint8_t* generator_out, int* K_out,

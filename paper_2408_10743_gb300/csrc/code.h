@@ -85,11 +85,21 @@ struct DeviceGuard {
 
 // A code resident on one device: its plan and one device block holding its
 // tables, its scratch and its launch segment table.
+namespace dist {
+// One device allocation shared by the codes of a dist_init_many call; freed
+// when the last of them is.
+struct DevSlab {
+    void* base = nullptr;
+    std::atomic<int> refs{0};
+};
+}  // namespace dist
+
 struct dist_code {
     dist::Plan plan;
     dist::DeviceCtx* dev = nullptr;
     void* d_block = nullptr;
     size_t block_cap = 0;
+    dist::DevSlab* slab = nullptr;            // d_block lies in a shared allocation (dist_init_many)
     uint32_t* d_tables = nullptr;             // Plan::tables on the device
     Scratch* d_scr = nullptr;                 // bound, counters, witness slots
     SegDesc* d_segs = nullptr;                // segment table of the current launch (after d_scr)

@@ -255,3 +255,39 @@ def test_slice_larger_than_the_initial_arena():
         assert np.array_equal(np.bitwise_xor.reduce(g[row["coeffs"][:80].astype(bool)], axis=0), w)
     for c in codes:
         c.close()
+
+
+def test_init_many_vs_oracle_table():
+    """dist_init_many: 1024 codes of the batched workload initialised in one
+    call (planning on the host threads, one device allocation), solved
+    together and one by one, against the CPU oracle's stored distances; the
+    codes are freed in an interleaved order, the allocation with the last.
+    Entries that dist_init rejects get its error and no handle, and the
+    call's other codes are still initialised."""
+    _, table = load_oracle_table("batch4096_oracle.txt")
+    gens = synth.batch_codes(1024)
+    codes = dist.Code.many(gens)
+    with dist.Batch() as b:
+        res = b.wait(b.submit(codes), timeout_s=300)
+    bad = [(i, r["d"], table[i][2]) for i, r in enumerate(res) if r["d"] != table[i][2]]
+    assert not bad, bad[:10]
+    for g, r in zip(gens, res):
+        valid(g, r)
+    for i in range(0, 1024, 2):  # every other code freed first
+        codes[i].close()
+    for i in range(1, 1024, 64):
+        r = dist.dist_solve(codes[i]._h)
+        assert r.d == table[i][2], i
+    for i in range(1, 1024, 2):
+        codes[i].close()
+    zero = np.zeros((3, 20), dtype=np.uint8)          # the zero code
+    wide = np.ones((2, 2 * 129), dtype=np.uint8)      # 129 qubits
+    handles, status = dist.dist_init_many([gens[0], zero, gens[1], wide])
+    assert status[0] == 0 and status[2] == 0
+    assert status[1] == dist.binding.DIST_EZERO and status[3] < 0
+    assert handles[1] is None and handles[3] is None
+    for i in (0, 2):
+        r = dist.dist_solve(handles[i])
+        assert r.d == table[i // 2][2]
+        dist.dist_free(handles[i])
+    assert dist.dist_init_many([]) == ([], [])

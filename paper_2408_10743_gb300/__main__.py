@@ -52,7 +52,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.batch:
         gens = synth.batch_codes(args.batch)
-        codes = [binding.Code(g) for g in gens]
+        codes = binding.Code.many(gens)
         with binding.Batch() as b:
             res = b.wait(b.submit(codes))
             st = b.stats()

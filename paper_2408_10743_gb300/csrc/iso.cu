@@ -5,11 +5,13 @@
 //
 // One launch per step (round r of matrix j).  Each block stages the matrix's
 // rows, restricted to the columns outside its information set (a pivot row
-// adds exactly 1 on the set, a free row 0), in shared memory.  Rounds r >= 2
-// walk the subsets in colexicographic order over a shared-memory table of
-// all row pairs (iso_pair_kernel, below); round 1 and matrices whose pair
-// table does not fit have each lane walk its own rank range in
-// revolving-door order (iso_rd_kernel).
+// adds exactly 1 on the set, a free row 0), in shared memory.  Large rounds
+// (at most 8 rows, at least 2^18 combinations) take the split walk
+// (iso_split_kernel, isosplit.cuh): the rows in two halves, every r-subset a
+// product of one subset of each.  The other rounds r >= 2 walk the subsets
+// in colexicographic order over a shared-memory table of all row pairs
+// (iso_pair_kernel); round 1 and matrices whose pair table does not fit have
+// each lane walk its own rank range in revolving-door order (iso_rd_kernel).
 #include <cuda_runtime.h>
 #include <string.h>
 

@@ -455,7 +455,8 @@ def serve_measure(dist, rate, duration, slice_ms, drain_s, time_limit_s, one_per
            "oracle_source": "tests/golden/stream_oracle.txt (CPU oracle, Algorithm 3; %s entries)" % (
                len(table) if table is not None else "no"),
            "served": serve_summary(reqs, recs, wall, table)}
-    out["served"].update({"gpu_s": st["gpu_seconds"], "slices": st["slices"]})
+    out["served"].update({"gpu_s": st["gpu_seconds"], "slices": st["slices"],
+                          "host_plan_s": st["plan_seconds"], "host_post_s": st["post_seconds"]})
     if one_per_launch:
         prec, pwall = serve_one_per_launch(dist, reqs, drain_s if plain_drain_s is None else plain_drain_s,
                                            time_limit_s)

@@ -570,3 +570,25 @@ extern "C" int hw_split_cover(int K, int r, unsigned long long target, const uin
     out[3] = outside;
     return 0;
 }
+
+// The split plan of round r of K rows for unit target `target` (isosplit.cuh):
+// its terms (at most kSplitMaxTerms) and unit count.  Returns the number of
+// terms, or -1 if the split walk does not apply.
+extern "C" int hw_split_plan(int K, int r, unsigned long long target, SplitTerm* terms, unsigned long long* units) {
+    std::vector<unsigned long long> B((DIST_MAXU + 1) * (DIST_MAXR + 1));
+    binom_table(B.data());
+    SplitPlan sp;
+    if (!split_plan(K, r, target, B.data(), &sp)) return -1;
+    for (int e = 0; e < sp.nterms; e++) terms[e] = sp.term[e];
+    *units = sp.units;
+    return sp.nterms;
+}
+
+extern "C" int hw_split_sizes(int* term_bytes, int* max_terms, int* threads, int* nb, int* tile) {
+    *term_bytes = (int)sizeof(SplitTerm);
+    *max_terms = kSplitMaxTerms;
+    *threads = kSplitThreads;
+    *nb = kSplitNB;
+    *tile = kSplitTile;
+    return 0;
+}

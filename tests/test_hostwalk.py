@@ -72,6 +72,10 @@ def hw():
     L.hw_split_cover.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_uint32),
                                  ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_uint32),
                                  ctypes.POINTER(ctypes.c_ulonglong)]
+    L.hw_split_plan.restype = ctypes.c_int
+    L.hw_split_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p,
+                                ctypes.POINTER(ctypes.c_ulonglong)]
+    L.hw_split_sizes.argtypes = [ctypes.POINTER(ctypes.c_int)] * 5
     L.hw_solve_sliced.restype = ctypes.c_int
     L.hw_solve_sliced.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
@@ -422,6 +426,58 @@ def test_split_walk_covers_every_subset_once(hw, K, r, target):
     assert rc == 0
     assert out[1] == total and out[2] == 0 and out[3] == 0, list(out)
     assert hits.min() == 1 and hits.max() == 1
+
+
+class SplitTerm(ctypes.Structure):
+    _fields_ = [("n_tile", ctypes.c_ulonglong), ("n_lane", ctypes.c_ulonglong),
+                ("unit0", ctypes.c_ulonglong), ("units", ctypes.c_ulonglong),
+                ("nh", ctypes.c_uint32), ("tile_span", ctypes.c_uint32), ("groups", ctypes.c_uint32),
+                ("tile_off", ctypes.c_uint8), ("tile_kh", ctypes.c_uint8), ("tile_t", ctypes.c_uint8),
+                ("lane_off", ctypes.c_uint8), ("lane_kh", ctypes.c_uint8), ("lane_t", ctypes.c_uint8),
+                ("pad", ctypes.c_uint8 * 2)]
+
+
+def test_split_plan_invariants(hw):
+    """The split plan of every round r in [1, 8] of every K in [2, 256] rows,
+    at the smallest, a middle and the largest unit target the solver uses:
+    the terms' products add up to C(K, r) with every side a subset count of
+    its own half; tile sides are the shorter side, within 8 rows and inside
+    the K rows; each term's units are its tile ranges times its lane ranges,
+    laid end to end; a unit's tile range stays within a 2^20-entry span and
+    its thread ranges within 32-bit sizes the kernel's fields hold."""
+    sizes = [ctypes.c_int() for _ in range(5)]
+    hw.hw_split_sizes(*[ctypes.byref(x) for x in sizes])
+    term_bytes, max_terms, threads, nb, tile = (x.value for x in sizes)
+    assert term_bytes == ctypes.sizeof(SplitTerm)
+    terms = (SplitTerm * max_terms)()
+    units = ctypes.c_ulonglong()
+    for K in range(2, 257):
+        for r in range(1, 9):
+            for target in (1 << 15, 1 << 18, 1 << 21):
+                nt = hw.hw_split_plan(K, r, target, terms, ctypes.byref(units))
+                if r > K:  # no r-subsets: no terms, no units
+                    assert nt == 0 and units.value == 0
+                    continue
+                assert 0 < nt <= max_terms, (K, r)
+                total, u0 = 0, 0
+                for e in range(nt):
+                    T = terms[e]
+                    for off, kh, t, cnt in ((T.tile_off, T.tile_kh, T.tile_t, T.n_tile),
+                                            (T.lane_off, T.lane_kh, T.lane_t, T.n_lane)):
+                        assert t <= 8 and off + kh <= K and cnt == comb(kh, t), (K, r, e)
+                    assert T.n_tile <= T.n_lane
+                    assert {T.tile_off, T.lane_off} & {T.tile_off + T.tile_kh, T.lane_off + T.lane_kh}, (K, r, e)
+                    assert T.tile_t + T.lane_t == r
+                    assert 1 <= T.tile_span <= min(T.n_tile, 1 << 20) and T.groups >= 1
+                    assert T.nh == -(-T.n_tile // T.tile_span)
+                    lane_span = threads * nb * T.groups
+                    assert T.units == T.nh * -(-T.n_lane // lane_span)
+                    assert T.unit0 == u0
+                    u0 += T.units
+                    total += T.n_tile * T.n_lane
+                    if T.groups > 1:
+                        assert T.n_tile <= tile
+                assert total == comb(K, r) and units.value == u0, (K, r, target)
 
 
 def test_split_plan_limits(hw):

@@ -74,3 +74,37 @@ def test_tuning_get_set_clamps():
     finally:
         dist.dist_set_tuning(saved["chunks_per_warp"], saved["lane_cap_log2"],
                              saved["lane_floor_log2"])
+
+
+def test_init_many_rejects_bad_arguments_without_device():
+    """dist_init_many checks its arguments before it touches a device: a
+    negative count or a missing array is DIST_EINVAL, and count 0 is accepted
+    with nothing to do."""
+    L = dist.lib()
+    n = (ctypes.c_int * 1)(4)
+    K = (ctypes.c_int * 1)(2)
+    f = (ctypes.c_int * 1)(dist.DIST_F2)
+    st = (ctypes.c_int * 1)()
+    out = (ctypes.c_void_p * 1)()
+    g = (ctypes.c_uint8 * 16)()
+    gens = (ctypes.POINTER(ctypes.c_uint8) * 1)(ctypes.cast(g, ctypes.POINTER(ctypes.c_uint8)))
+    assert L.dist_init_many(out, -1, gens, n, K, f, st) == -1
+    assert L.dist_init_many(out, 1, None, n, K, f, st) == -1
+    assert L.dist_init_many(out, 1, gens, n, K, f, None) == -1
+    assert L.dist_init_many(None, 0, None, None, None, None, None) == 0
+    assert dist.dist_init_many([]) == ([], [])
+
+
+def test_iso_walk_setting_without_device():
+    saved = dist.dist_get_iso_walk()
+    try:
+        for mode in (1, 2, 0):
+            dist.dist_set_iso_walk(mode)
+            assert dist.dist_get_iso_walk() == mode
+        with pytest.raises(dist.DistError) as e:
+            dist.dist_set_iso_walk(3)
+        assert e.value.code == -1
+        with pytest.raises(dist.DistError):
+            dist.dist_set_iso_walk(-1)
+    finally:
+        dist.dist_set_iso_walk(saved)
